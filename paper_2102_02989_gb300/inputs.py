@@ -1,0 +1,221 @@
+"""Seeded synthetic inputs: cells, AO and auxiliary shells, k-meshes.
+
+This module holds no arithmetic of the method (no normalisation, no integrals,
+no screening, no parameter rules); it only draws the geometry and the shell
+data that both the CUDA library and the CPU oracle consume.  The paper's own
+workloads (diamond/cc-pVDZ with cc-pVDZ-jkfit; MgO and LiF with GTH-DZVP and an
+even-tempered auxiliary basis of progression 2.0) are not available here; the
+shapes below stand in for them: an FCC two-atom cell at diamond's lattice
+constant, 3s2p1d AO shells per atom, and an even-tempered auxiliary basis of
+about three times the AO count.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2102_02989
+
+
+@dataclass
+class Basis:
+    """Contracted Cartesian shells.  ``coeffs`` are raw contraction coefficients
+    of the primitives; the libraries apply the normalisation themselves."""
+    l: np.ndarray          # [nshell] int32
+    nprim: np.ndarray      # [nshell] int32
+    prim_off: np.ndarray   # [nshell] int32
+    center: np.ndarray     # [nshell, 3] float64, Bohr
+    exps: np.ndarray       # [nprim_total] float64
+    coeffs: np.ndarray     # [nprim_total] float64
+
+    @property
+    def nshell(self) -> int:
+        return int(len(self.l))
+
+    @property
+    def nfunc(self) -> int:
+        return int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in self.l))
+
+    def subset(self, shells) -> "Basis":
+        shells = list(shells)
+        l, npr, off, cen, ex, co = [], [], [], [], [], []
+        o = 0
+        for s in shells:
+            n = int(self.nprim[s])
+            p0 = int(self.prim_off[s])
+            l.append(int(self.l[s])); npr.append(n); off.append(o); cen.append(self.center[s])
+            ex.extend(self.exps[p0:p0 + n]); co.extend(self.coeffs[p0:p0 + n])
+            o += n
+        return Basis(np.array(l, np.int32), np.array(npr, np.int32), np.array(off, np.int32),
+                     np.array(cen, np.float64).reshape(-1, 3), np.array(ex, np.float64),
+                     np.array(co, np.float64))
+
+
+def make_basis(shells) -> Basis:
+    """shells: iterable of (l, centre[3], exps[], coeffs[])."""
+    l, npr, off, cen, ex, co = [], [], [], [], [], []
+    o = 0
+    for (ll, c, e, cf) in shells:
+        e = list(map(float, e)); cf = list(map(float, cf))
+        assert len(e) == len(cf) and len(e) > 0
+        l.append(int(ll)); npr.append(len(e)); off.append(o); cen.append(list(map(float, c)))
+        ex.extend(e); co.extend(cf); o += len(e)
+    return Basis(np.array(l, np.int32), np.array(npr, np.int32), np.array(off, np.int32),
+                 np.array(cen, np.float64).reshape(-1, 3), np.array(ex, np.float64),
+                 np.array(co, np.float64))
+
+
+@dataclass
+class Problem:
+    name: str
+    a: np.ndarray            # [3,3] lattice vectors as rows, Bohr
+    kmesh: tuple             # Gamma-including mesh
+    ao: Basis
+    aux: Basis
+    omega: float | None      # None: derive from gmesh and eps_lr
+    gmesh: tuple | None      # None: derive from omega and eps_lr
+    eps_sr: float
+    eps_lr: float
+    atoms: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+
+    @property
+    def nk(self) -> int:
+        return int(np.prod(self.kmesh))
+
+
+def even_tempered(l: int, center, alpha0: float, beta: float, n: int):
+    return [(l, center, [alpha0 * beta ** i], [1.0]) for i in range(n)]
+
+
+def fcc_cell(a: float) -> np.ndarray:
+    return 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+
+
+def _random_ao_atom(rng, center, spec=((0, (3, 2, 1)), (1, (2, 1)), (2, (1,))),
+                    lo=0.1, hi=7000.0):
+    shells = []
+    for l, nprims in spec:
+        for npr in nprims:
+            e = np.sort(np.exp(rng.uniform(np.log(lo), np.log(hi), size=npr)))[::-1]
+            c = rng.uniform(0.2, 1.0, size=npr)
+            shells.append((l, center, e, c))
+    return shells
+
+
+def _etb_atom(center, counts=(8, 5, 2, 1), alpha0=0.2, beta=2.0):
+    shells = []
+    for l, n in enumerate(counts):
+        shells += even_tempered(l, center, alpha0, beta, n)
+    return shells
+
+
+def config1() -> Problem:
+    """Gamma-only cubic cell a = 4.0 Bohr, atoms at (0,0,0) and (2,2,2);
+    per atom uncontracted AO s {13.0, 1.96, 0.44} and p {0.8}; aux s, p, d
+    even-tempered 0.2*2.5^n, n = 0..5; omega = 0.5; eps = 1e-10."""
+    a = 4.0 * np.eye(3)
+    atoms = np.array([[0.0, 0.0, 0.0], [2.0, 2.0, 2.0]])
+    ao, aux = [], []
+    for c in atoms:
+        for e in (13.0, 1.96, 0.44):
+            ao.append((0, c, [e], [1.0]))
+        ao.append((1, c, [0.8], [1.0]))
+        for l in range(3):
+            aux += even_tempered(l, c, 0.2, 2.5, 6)
+    return Problem("cubic a=4.0 2-atom Gamma (12 AO, 120 aux)", a, (1, 1, 1), make_basis(ao),
+                   make_basis(aux), 0.5, None, 1e-10, 1e-10, atoms)
+
+
+def config2(kmesh=(2, 2, 2), seed_offset=2) -> Problem:
+    """FCC two-atom cell a = 6.74 Bohr; per atom 3s2p1d AO shells with
+    log-uniform random exponents in [0.1, 7000] and random contraction
+    coefficients in [0.2, 1]; even-tempered aux (beta = 2, from 0.2) s x8,
+    p x5, d x2, f x1 per atom; eps = 1e-8; G mesh 7^3, omega from the LR cutoff."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    A = 6.74
+    a = fcc_cell(A)
+    atoms = np.array([[0.0, 0.0, 0.0], [A / 4, A / 4, A / 4]])
+    ao, aux = [], []
+    for c in atoms:
+        ao += _random_ao_atom(rng, c)
+        aux += _etb_atom(c)
+    name = "FCC a=6.74 2-atom k=%dx%dx%d (30 AO, 90 aux)" % tuple(kmesh)
+    return Problem(name, a, tuple(kmesh), make_basis(ao), make_basis(aux), None, (7, 7, 7),
+                   1e-8, 1e-8, atoms)
+
+
+def config3(kmesh=(4, 4, 4)) -> Problem:
+    p = config2(kmesh, seed_offset=2)
+    p.name = p.name.replace("k=", "mixed k=")
+    return p
+
+
+def config5() -> Problem:
+    """Rocksalt conventional cubic cell a = 8.0 Bohr, 8 atoms, 4x4x4 mesh;
+    every atom draws its AO shells like config 2 and carries the same ETB aux."""
+    rng = np.random.default_rng(SEED_BASE + 5)
+    A = 8.0
+    a = A * np.eye(3)
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]]) * A
+    atoms = np.concatenate([fcc, fcc + np.array([A / 2, 0, 0])])
+    ao, aux = [], []
+    for c in atoms:
+        ao += _random_ao_atom(rng, c)
+        aux += _etb_atom(c)
+    return Problem("rocksalt a=8.0 8-atom k=4x4x4 (120 AO, 360 aux)", a, (4, 4, 4),
+                   make_basis(ao), make_basis(aux), None, (7, 7, 7), 1e-8, 1e-8, atoms)
+
+
+def config4(ncell=32) -> list:
+    """32 heterogeneous cells: 1-8 atoms, cubic or FCC lattices with a in
+    U[5, 10] Bohr, 1-3 random AO shells per l <= 3 per atom, an ETB aux of
+    about 3x the AO count with l <= 3, k-meshes from 1x1x1 to 3x3x3."""
+    rng = np.random.default_rng(SEED_BASE + 4)
+    probs = []
+    for ic in range(ncell):
+        natm = int(rng.integers(1, 9))
+        A = float(rng.uniform(5.0, 10.0))
+        fcc = bool(rng.integers(0, 2))
+        a = fcc_cell(A) if fcc else A * np.eye(3)
+        frac = rng.uniform(0, 1, size=(natm, 3))
+        atoms = frac @ a
+        ao, aux = [], []
+        for c in atoms:
+            spec = tuple((l, tuple([1] * int(rng.integers(1, 4)))) for l in range(4))
+            ao += _random_ao_atom(rng, c, spec=spec, lo=0.15, hi=50.0)
+        nao = sum((s[0] + 1) * (s[0] + 2) // 2 for s in ao)
+        per_atom = max(1, int(round(3 * nao / natm)))
+        for c in atoms:
+            counts = [0, 0, 0, 0]
+            tot, l = 0, 0
+            while tot < per_atom:
+                counts[l] += 1
+                tot += (l + 1) * (l + 2) // 2
+                l = (l + 1) % 4
+            aux += _etb_atom(c, counts=tuple(counts), alpha0=0.25, beta=2.0)
+        n = int(rng.integers(1, 4))
+        probs.append(Problem("batch cell %d" % ic, a, (n, n, n), make_basis(ao), make_basis(aux),
+                             None, (7, 7, 7), 1e-8, 1e-8, atoms))
+    return probs
+
+
+def tiny(kmesh=(1, 1, 1), lmax_ao=1, lmax_aux=2, seed=7, a=3.2, natm=1) -> Problem:
+    """A tiny cubic cell for brute-force checks: few compact shells."""
+    rng = np.random.default_rng(SEED_BASE + 100 + seed)
+    cell = a * np.eye(3)
+    atoms = rng.uniform(0, a, size=(natm, 3))
+    ao, aux = [], []
+    for c in atoms:
+        for l in range(lmax_ao + 1):
+            npr = 2 if l == 0 else 1
+            e = np.sort(rng.uniform(0.8, 4.0, size=npr))[::-1]
+            ao.append((l, c, e, rng.uniform(0.3, 1.0, size=npr)))
+        for l in range(lmax_aux + 1):
+            aux.append((l, c, [float(rng.uniform(1.0, 3.0))], [1.0]))
+    return Problem("tiny", cell, tuple(kmesh), make_basis(ao), make_basis(aux), 0.9, None,
+                   1e-12, 1e-12, atoms)
+
+
+def kpairs_all(nk: int) -> np.ndarray:
+    return np.array([(i, j) for i in range(nk) for j in range(nk)], dtype=np.int32)
