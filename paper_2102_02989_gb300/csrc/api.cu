@@ -1,0 +1,638 @@
+// C ABI of the RSGDF library: argument checks, the host planner, device
+// uploads, the launch sequence of the j3c / j2c / kphase paths and the error
+// and statistics reporting.  Scratch memory is allocated stream-ordered on
+// the caller's stream and released before each call returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "k_common.cuh"
+#include "rsgdf_internal.h"
+
+namespace rsgdf {
+
+static thread_local std::string t_err;
+static thread_local rsgdf_stats t_stats;
+static thread_local cudaStream_t t_stats_stream = nullptr;
+static thread_local unsigned long long *t_count_host = nullptr;   // pinned [LTOT_MAX+1]
+static thread_local bool t_count_valid = false;
+
+static int fail(int code, const std::string &msg)
+{
+    t_err = msg;
+    return code;
+}
+
+#define CU(x)                                                                           \
+    do {                                                                                \
+        cudaError_t e_ = (x);                                                           \
+        if (e_ != cudaSuccess) return fail(RSGDF_EDEVICE, std::string(#x ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RC(x)                                   \
+    do {                                        \
+        int r_ = (x);                           \
+        if (r_ != RSGDF_OK) {                   \
+            if (t_err.empty()) t_err = #x;      \
+            return r_;                          \
+        }                                       \
+    } while (0)
+
+// Stream-ordered device scratch released on scope exit.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    ~Scratch()
+    {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <class T>
+    int alloc(T *&p, size_t n)
+    {
+        p = nullptr;
+        if (n == 0) n = 1;
+        void *q = nullptr;
+        if (cudaMallocAsync(&q, n * sizeof(T), st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RSGDF_ENOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
+        }
+        ptrs.push_back(q);
+        p = (T *)q;
+        return RSGDF_OK;
+    }
+    template <class T>
+    int upload(T *&p, const std::vector<T> &v)
+    {
+        RC(alloc(p, v.size()));
+        if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(RSGDF_EDEVICE, "host-to-device copy failed");
+        return RSGDF_OK;
+    }
+};
+
+static int check_device()
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(RSGDF_EDEVICE, "no CUDA device");
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major * 10 + minor != 103) return fail(RSGDF_EDEVICE, "library built for sm_103a only");
+    return RSGDF_OK;
+}
+
+static int upload_shells(Scratch &S, const HBasis &h, DevShells &d)
+{
+    int *l, *np, *po, *fo;
+    double *c, *e, *cn;
+    RC(S.upload(l, h.l));
+    RC(S.upload(np, h.nprim));
+    RC(S.upload(po, h.poff));
+    RC(S.upload(fo, h.foff));
+    RC(S.upload(c, h.center));
+    RC(S.upload(e, h.exps));
+    RC(S.upload(cn, h.cn));
+    d.l = l; d.nprim = np; d.poff = po; d.foff = fo; d.cen = c; d.exps = e; d.cn = cn;
+    return RSGDF_OK;
+}
+
+static int ensure_boys(cudaStream_t st)
+{
+    static std::vector<double> tab;
+    static bool built = false;
+    if (!built) {
+        boys_table(tab);
+        built = true;
+    }
+    return upload_boys_table(tab.data(), st);
+}
+
+// e^{i k.cell} for every mesh k and BvK cell, exact integer angle reduction
+static void phase_table(const Lattice &L, std::vector<double> &ph)
+{
+    ph.assign((size_t)2 * L.Nk * L.Nk, 0.0);
+    for (int k = 0; k < L.Nk; k++) {
+        int n[3] = {k / (L.nk[1] * L.nk[2]), (k / L.nk[2]) % L.nk[1], k % L.nk[2]};
+        for (int c = 0; c < L.Nk; c++) {
+            int j[3] = {c / (L.nk[1] * L.nk[2]), (c / L.nk[2]) % L.nk[1], c % L.nk[2]};
+            long double f = 0.0L;
+            for (int i = 0; i < 3; i++) f += (long double)((n[i] * j[i]) % L.nk[i]) / L.nk[i];
+            long double ang = 2.0L * 3.141592653589793238462643383279502884L * f;
+            ph[2 * ((size_t)k * L.Nk + c)] = (double)cosl(ang);
+            ph[2 * ((size_t)k * L.Nk + c) + 1] = (double)sinl(ang);
+        }
+    }
+}
+
+static int k12_of(const Lattice &L, int k1, int k2)
+{
+    int a[3] = {k1 / (L.nk[1] * L.nk[2]), (k1 / L.nk[2]) % L.nk[1], k1 % L.nk[2]};
+    int b[3] = {k2 / (L.nk[1] * L.nk[2]), (k2 / L.nk[2]) % L.nk[1], k2 % L.nk[2]};
+    int d[3];
+    for (int i = 0; i < 3; i++) d[i] = ((b[i] - a[i]) % L.nk[i] + L.nk[i]) % L.nk[i];
+    return (d[0] * L.nk[1] + d[1]) * L.nk[2] + d[2];
+}
+
+static void k12_frac(const Lattice &L, int k12, double f[3])
+{
+    int d[3] = {k12 / (L.nk[1] * L.nk[2]), (k12 / L.nk[2]) % L.nk[1], k12 % L.nk[2]};
+    for (int i = 0; i < 3; i++) {
+        double x = (double)d[i] / L.nk[i];
+        if (x >= 0.5) x -= 1.0;
+        f[i] = x;
+    }
+}
+
+static void gbox(const int gm[3], std::vector<int> &g)
+{
+    g.clear();
+    for (int i = -(gm[0] - 1) / 2; i <= (gm[0] - 1) / 2; i++)
+        for (int j = -(gm[1] - 1) / 2; j <= (gm[1] - 1) / 2; j++)
+            for (int k = -(gm[2] - 1) / 2; k <= (gm[2] - 1) / 2; k++) {
+                g.push_back(i);
+                g.push_back(j);
+                g.push_back(k);
+            }
+}
+
+static void fill_lattice(const Lattice &L, double a9[9], double bq[9], int nk[3])
+{
+    for (int i = 0; i < 3; i++)
+        for (int x = 0; x < 3; x++) {
+            a9[3 * i + x] = L.a[i][x];
+            bq[3 * i + x] = L.b[i][x] / (2.0 * 3.141592653589793238462643383279502884);
+        }
+    for (int i = 0; i < 3; i++) nk[i] = L.nk[i];
+}
+
+static int check_opts(const rsgdf_opts *o)
+{
+    if (!o) return fail(RSGDF_EINVAL, "opts is NULL");
+    if (!(o->eps_screen > 0.0 && o->eps_screen < 1.0)) return fail(RSGDF_EINVAL, "eps_screen must be in (0, 1)");
+    if (o->precision != RSGDF_FP64 && o->precision != RSGDF_MIXED) return fail(RSGDF_EINVAL, "unknown precision mode");
+    if (o->precision == RSGDF_MIXED) return fail(RSGDF_ENOTIMPL, "mixed precision path not built in this library");
+    if (o->screening != RSGDF_SCREEN_BOUND && o->screening != RSGDF_SCREEN_LEARNED)
+        return fail(RSGDF_EINVAL, "unknown screening mode");
+    if (o->screening == RSGDF_SCREEN_LEARNED) return fail(RSGDF_ENOTIMPL, "learned screening not built in this library");
+    return RSGDF_OK;
+}
+
+// Launch the SR kernels of a plan into X.
+static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShells &ao, const DevShells &ax,
+                  const HBasis &hao, const HBasis &hax, double omega, double *X, long long s_lt, long long s_dt,
+                  long long s_P, long long s_mu, long long s_nu, int pfunc0, unsigned long long *counts,
+                  cudaStream_t st, int &nlaunch)
+{
+    if (plan.tri.empty()) return RSGDF_OK;
+    std::vector<SRTripleDev> td(plan.tri.size());
+    for (size_t i = 0; i < plan.tri.size(); i++) {
+        const SRTriple &t = plan.tri[i];
+        td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, t.Rc_cut, t.amu, t.anu, t.item_off};
+    }
+    SRTripleDev *dtri;
+    double *dwin;
+    int *dpoff, *dl, *dsph;
+    RC(S.upload(dtri, td));
+    RC(S.upload(dwin, plan.win));
+    RC(S.upload(dpoff, plan.pair_doff));
+    RC(S.upload(dl, plan.dlist));
+    RC(S.upload(dsph, plan.sph));
+    SRArgs A;
+    memset(&A, 0, sizeof(A));
+    A.ao = ao;
+    A.ax = ax;
+    A.tri = dtri;
+    A.win = dwin;
+    A.pair_doff = dpoff;
+    A.dlist = dl;
+    A.sph = dsph;
+    fill_lattice(L, A.a, A.bq, A.nk);
+    A.Nk = L.Nk;
+    A.omega = omega;
+    A.X = X;
+    A.s_lt = s_lt; A.s_dt = s_dt; A.s_P = s_P; A.s_mu = s_mu; A.s_nu = s_nu;
+    A.pfunc0 = pfunc0;
+    A.term_count = counts;
+    for (int c = 0; c <= LTOT_MAX; c++) {
+        int b = plan.class_tri_begin[c], e = plan.class_tri_begin[c + 1];
+        if (b >= e) continue;
+        int ncmax = 0;
+        for (int i = b; i < e; i++) {
+            const SRTriple &t = plan.tri[i];
+            ncmax = std::max(ncmax, ncart(hax.l[t.P]) * ncart(hao.l[t.mu]) * ncart(hao.l[t.nu]));
+        }
+        A.tri_begin = b;
+        A.tri_end = e;
+        A.item_begin = plan.tri[b].item_off;
+        A.item_end = (e < (int)plan.tri.size()) ? plan.tri[e].item_off : plan.n_items;
+        RC(launch_sr(c, A, ncmax, st));
+        nlaunch++;
+    }
+    return RSGDF_OK;
+}
+
+enum { MODE_SR = 1, MODE_LR = 2 };
+
+static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in,
+                    const rsgdf_opts *opts, int npair, const int *kpairs, int s0, int s1, double *V, int mode)
+{
+    t_err.clear();
+    memset(&t_stats, 0, sizeof(t_stats));
+    t_count_valid = false;
+    RC(check_opts(opts));
+    Lattice L;
+    HBasis ao, ax;
+    RC(make_lattice(cell, L, t_err));
+    RC(load_basis(ao_in, ao, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
+    for (int i = 0; i < 2 * npair; i++)
+        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    if (s0 < 0 || s1 > ax.nshell || s0 >= s1) return fail(RSGDF_EINVAL, "aux shell range is empty or out of bounds");
+    if (!V) return fail(RSGDF_EINVAL, "V_out is NULL");
+    double omega;
+    int gm[3];
+    RC(derive_params(L, opts, omega, gm, t_err));
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    RC(ensure_boys(st));
+    Scratch S(st);
+    const int nao = ao.nfunc;
+    const int pfunc0 = ax.foff[s0];
+    const int nP = (s1 < ax.nshell ? ax.foff[s1] : ax.nfunc) - pfunc0;
+    const long long m = (long long)nP * nao * nao;
+    const int Nk = L.Nk;
+    int nlaunch = 0;
+    DevShells dao, dax;
+    RC(upload_shells(S, ao, dao));
+    RC(upload_shells(S, ax, dax));
+    double a9[9], bq[9];
+    int nk3[3];
+    fill_lattice(L, a9, bq, nk3);
+    double *da9;
+    int *dnk;
+    RC(S.upload(da9, std::vector<double>(a9, a9 + 9)));
+    RC(S.upload(dnk, std::vector<int>(nk3, nk3 + 3)));
+    std::vector<double> ph;
+    phase_table(L, ph);
+    double *dph;
+    RC(S.upload(dph, ph));
+    // k12 groups
+    std::map<int, std::vector<int>> groups;
+    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
+    std::vector<int> plist, pk2, goff;
+    std::vector<int> gkey;
+    for (auto &kv : groups) {
+        goff.push_back((int)plist.size());
+        gkey.push_back(kv.first);
+        for (int p : kv.second) {
+            plist.push_back(p);
+            pk2.push_back(kpairs[2 * p + 1]);
+        }
+    }
+    goff.push_back((int)plist.size());
+    int *dplist, *dpk2;
+    RC(S.upload(dplist, plist));
+    RC(S.upload(dpk2, pk2));
+    unsigned long long *dcnt;
+    RC(S.alloc(dcnt, LTOT_MAX + 1));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 1), st));
+
+    // SR folded sums X[lt][dt][P][mu][nu]
+    double *X = nullptr;
+    SRPlan plan;
+    if (mode & MODE_SR) {
+        plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
+        RC(S.alloc(X, (size_t)Nk * Nk * m));
+        CU(cudaMemsetAsync(X, 0, sizeof(double) * Nk * Nk * m, st));
+        RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
+                  dcnt, st, nlaunch));
+    }
+    // AFT pair lists (also the overlaps of the G = 0 correction)
+    std::vector<int> apoff, alist;
+    plan_pairs(L, ao, opts->eps_lr, apoff, alist);
+    int *dapoff, *dalist;
+    RC(S.upload(dapoff, apoff));
+    RC(S.upload(dalist, alist));
+    double *SP = nullptr, *Sf = nullptr;
+    const double g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
+    if ((mode & MODE_SR) && groups.count(0)) {
+        RC(S.alloc(SP, nP));
+        RC(S.alloc(Sf, (size_t)Nk * nao * nao));
+        k_aux_charge<<<(s1 - s0 + 63) / 64, 64, 0, st>>>(dax, s0, s1, pfunc0, SP);
+        int nth = ao.nshell * ao.nshell * Nk;
+        k_ovlp_fold<<<(nth + 127) / 128, 128, 0, st>>>(dao, ao.nshell, nao, dapoff, dalist, da9, dnk, Nk, Sf);
+        CU(cudaGetLastError());
+        nlaunch += 2;
+    }
+    // G-space data
+    std::vector<int> gl;
+    gbox(gm, gl);
+    const int NG = (int)(gl.size() / 3);
+    int *dg = nullptr;
+    double *W = nullptr, *Y = nullptr;
+    if (mode & MODE_LR) {
+        RC(S.upload(dg, gl));
+        RC(S.alloc(W, (size_t)2 * NG * nP));
+        RC(S.alloc(Y, (size_t)2 * Nk * NG * nao * nao));
+    }
+    double *T;
+    RC(S.alloc(T, (size_t)2 * Nk * m));
+    long long aft_units = 0;
+    for (size_t gi = 0; gi < gkey.size(); gi++) {
+        const int k12 = gkey[gi];
+        bool have = false;
+        if (mode & MODE_SR) {
+            RC(launch_phase1(X, m, Nk, Nk, k12, dph, T, 0, st));
+            nlaunch++;
+            have = true;
+            if (k12 == 0) {
+                RC(launch_g0_fold(T, m, Nk, nP, nao, SP, Sf, g0fac, st));
+                nlaunch++;
+            }
+        }
+        if (mode & MODE_LR) {
+            if (!have) CU(cudaMemsetAsync(T, 0, sizeof(double) * 2 * Nk * m, st));
+            GArgs G;
+            memset(&G, 0, sizeof(G));
+            G.g = dg;
+            G.NG = NG;
+            for (int i = 0; i < 3; i++)
+                for (int x = 0; x < 3; x++) G.b[3 * i + x] = L.b[i][x];
+            k12_frac(L, k12, G.f12);
+            G.vol = L.vol;
+            G.omega = omega;
+            RC(launch_aux_ft(G, dax, s0, s1, pfunc0, nP, W, nullptr, st));
+            RC(launch_aft(G, dao, ao.nshell, nao, dapoff, dalist, da9, dnk, Nk, Y, st));
+            RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, T, 2 * m, st));
+            nlaunch += 3;
+        }
+        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V,
+                         (mode == MODE_LR) ? 1 : 0, st));
+        nlaunch++;
+    }
+    if (mode & MODE_LR) {
+        for (int mu = 0; mu < ao.nshell; mu++)
+            for (int nu = 0; nu < ao.nshell; nu++) {
+                int pr = mu * ao.nshell + nu;
+                aft_units += (long long)(apoff[pr + 1] - apoff[pr]) * ao.nprim[mu] * ao.nprim[nu];
+            }
+        aft_units *= (long long)NG * (long long)gkey.size();
+    }
+    CU(cudaGetLastError());
+    // statistics
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 1)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 1), cudaMemcpyDeviceToHost, st));
+    t_count_valid = true;
+    t_stats_stream = st;
+    t_stats.omega = omega;
+    for (int i = 0; i < 3; i++) t_stats.gmesh[i] = gm[i];
+    t_stats.aft_units = aft_units;
+    t_stats.lr_flops = (mode & MODE_LR) ? 8LL * nP * nao * nao * NG * Nk * (long long)gkey.size() : 0;
+    t_stats.n_launch = nlaunch;
+    return RSGDF_OK;
+}
+
+}  // namespace rsgdf
+
+using namespace rsgdf;
+
+extern "C" {
+
+int rsgdf_j3c_sr(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux, const rsgdf_opts *opts,
+                 int npair, const int *kpairs, int s0, int s1, double *V_out)
+{
+    return j3c_impl(cell, ao, aux, opts, npair, kpairs, s0, s1, V_out, MODE_SR);
+}
+
+int rsgdf_j3c_lr(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux, const rsgdf_opts *opts,
+                 int npair, const int *kpairs, int s0, int s1, double *V_out)
+{
+    return j3c_impl(cell, ao, aux, opts, npair, kpairs, s0, s1, V_out, MODE_LR);
+}
+
+int rsgdf_j3c(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux, const rsgdf_opts *opts,
+              int npair, const int *kpairs, int s0, int s1, double *V_out)
+{
+    return j3c_impl(cell, ao, aux, opts, npair, kpairs, s0, s1, V_out, MODE_SR | MODE_LR);
+}
+
+int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opts *opts, int nk, const int *kidx,
+              double *J_out, double *L_out, int *info_out)
+{
+    t_err.clear();
+    memset(&t_stats, 0, sizeof(t_stats));
+    t_count_valid = false;
+    RC(check_opts(opts));
+    Lattice L;
+    HBasis ax, axu;
+    RC(make_lattice(cell, L, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    if (nk < 1 || !kidx) return fail(RSGDF_EINVAL, "need at least one k");
+    for (int i = 0; i < nk; i++)
+        if (kidx[i] < 0 || kidx[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    if (!J_out) return fail(RSGDF_EINVAL, "J_out is NULL");
+    double omega;
+    int gm[3];
+    RC(derive_params(L, opts, omega, gm, t_err));
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    RC(ensure_boys(st));
+    Scratch S(st);
+    unit_partner_basis(ax, axu);
+    const int naux = ax.nfunc, Nk = L.Nk;
+    int nlaunch = 0;
+    DevShells dax, daxu;
+    RC(upload_shells(S, ax, dax));
+    RC(upload_shells(S, axu, daxu));
+    std::vector<double> ph;
+    phase_table(L, ph);
+    double *dph;
+    RC(S.upload(dph, ph));
+    unsigned long long *dcnt;
+    RC(S.alloc(dcnt, LTOT_MAX + 1));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 1), st));
+    // SR: X2[lt][P][Q] = sum_{l -> lt} (chi_P^l | erfc | chi_Q^0), the
+    // three-center kernel with the unit function as the second pair member
+    SRPlan plan;
+    plan_sr2c(L, ax, axu, omega, opts->eps_screen, plan);
+    const long long m = (long long)naux * naux;
+    double *X2;
+    RC(S.alloc(X2, (size_t)Nk * m));
+    CU(cudaMemsetAsync(X2, 0, sizeof(double) * Nk * m, st));
+    RC(run_sr(S, L, plan, daxu, dax, axu, ax, omega, X2, m, 0, naux, 1, 0, 0, dcnt, st, nlaunch));
+    double *SP;
+    RC(S.alloc(SP, naux));
+    k_aux_charge<<<(ax.nshell + 63) / 64, 64, 0, st>>>(dax, 0, ax.nshell, 0, SP);
+    CU(cudaGetLastError());
+    nlaunch++;
+    std::vector<int> gl;
+    gbox(gm, gl);
+    const int NG = (int)(gl.size() / 3);
+    int *dg;
+    double *W, *F;
+    RC(S.upload(dg, gl));
+    RC(S.alloc(W, (size_t)2 * NG * naux));
+    RC(S.alloc(F, (size_t)2 * NG * naux));
+    const double g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
+    // J^k = sum_lt e^{-i k.lt} X2[lt] - [k = 0] fac S_P S_Q + W^T F
+    for (int i = 0; i < nk; i++) {
+        const int k = kidx[i];
+        double *Jk = J_out + (size_t)2 * i * m;
+        RC(launch_phase1(X2, m, Nk, 1, k, dph, Jk, 0, st));
+        nlaunch++;
+        if (k == 0) {
+            RC(launch_g0_outer(Jk, naux, SP, g0fac, st));
+            nlaunch++;
+        }
+        GArgs G;
+        memset(&G, 0, sizeof(G));
+        G.g = dg;
+        G.NG = NG;
+        for (int a = 0; a < 3; a++)
+            for (int x = 0; x < 3; x++) G.b[3 * a + x] = L.b[a][x];
+        k12_frac(L, k, G.f12);
+        G.vol = L.vol;
+        G.omega = omega;
+        RC(launch_aux_ft(G, dax, 0, ax.nshell, 0, naux, W, F, st));
+        RC(launch_zgemm_tn(naux, naux, NG, 1, W, F, 0, Jk, 0, st));
+        nlaunch += 2;
+    }
+    if (L_out) {
+        RC(launch_cholesky(naux, nk, J_out, L_out, info_out, st));
+        nlaunch++;
+    } else if (info_out) {
+        CU(cudaMemsetAsync(info_out, 0xff, sizeof(int) * nk, st));
+    }
+    CU(cudaGetLastError());
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 1)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 1), cudaMemcpyDeviceToHost, st));
+    t_count_valid = true;
+    t_stats_stream = st;
+    t_stats.omega = omega;
+    for (int i = 0; i < 3; i++) t_stats.gmesh[i] = gm[i];
+    t_stats.lr_flops = 8LL * naux * naux * NG * nk;
+    t_stats.n_launch = nlaunch;
+    return RSGDF_OK;
+}
+
+int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair, const int *kpairs, double *V_out,
+                 void *stream)
+{
+    t_err.clear();
+    Lattice L;
+    RC(make_lattice(cell, L, t_err));
+    if (!X || !V_out || m < 1) return fail(RSGDF_EINVAL, "X, V_out and m >= 1 are required");
+    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
+    for (int i = 0; i < 2 * npair; i++)
+        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    const int Nk = L.Nk;
+    std::vector<double> ph;
+    phase_table(L, ph);
+    double *dph;
+    RC(S.upload(dph, ph));
+    std::map<int, std::vector<int>> groups;
+    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
+    std::vector<int> plist, pk2, goff, gkey;
+    for (auto &kv : groups) {
+        goff.push_back((int)plist.size());
+        gkey.push_back(kv.first);
+        for (int p : kv.second) {
+            plist.push_back(p);
+            pk2.push_back(kpairs[2 * p + 1]);
+        }
+    }
+    goff.push_back((int)plist.size());
+    int *dplist, *dpk2;
+    RC(S.upload(dplist, plist));
+    RC(S.upload(dpk2, pk2));
+    double *T;
+    RC(S.alloc(T, (size_t)2 * Nk * m));
+    for (size_t gi = 0; gi < gkey.size(); gi++) {
+        RC(launch_phase1(X, m, Nk, Nk, gkey[gi], dph, T, 0, st));
+        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V_out, 0, st));
+    }
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+int rsgdf_last_stats(rsgdf_stats *out)
+{
+    if (!out) return fail(RSGDF_EINVAL, "out is NULL");
+    if (t_count_valid) {
+        if (cudaStreamSynchronize(t_stats_stream) != cudaSuccess) return fail(RSGDF_EDEVICE, "stream sync failed");
+        t_stats.sr_terms = 0;
+        t_stats.sr_flops = 0;
+        for (int L = 0; L <= LTOT_MAX; L++) {
+            t_stats.sr_terms += (long long)t_count_host[L];
+            t_stats.sr_flops += (long long)t_count_host[L] * sr_term_flops(L);
+        }
+    }
+    *out = t_stats;
+    return RSGDF_OK;
+}
+
+int rsgdf_params(const rsgdf_cell *cell, const rsgdf_opts *opts, double *omega_out, int *gmesh_out)
+{
+    t_err.clear();
+    if (!opts || !omega_out || !gmesh_out) return fail(RSGDF_EINVAL, "NULL argument");
+    Lattice L;
+    RC(make_lattice(cell, L, t_err));
+    double w;
+    int g[3];
+    RC(derive_params(L, opts, w, g, t_err));
+    *omega_out = w;
+    for (int i = 0; i < 3; i++) gmesh_out[i] = g[i];
+    return RSGDF_OK;
+}
+
+const char *rsgdf_last_error(void) { return t_err.c_str(); }
+
+int rsgdf_probe_fp64(double *tflops_out, void *stream)
+{
+    t_err.clear();
+    if (!tflops_out) return fail(RSGDF_EINVAL, "NULL argument");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    Scratch S(st);
+    double *buf;
+    RC(S.alloc(buf, (size_t)nsm * 8 * 256));
+    const int iters = 2000;
+    RC(launch_probe_fp64(buf, iters, st));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; rep++) {
+        CU(cudaEventRecord(e0, st));
+        RC(launch_probe_fp64(buf, iters, st));
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    double flops = 2.0 * 8 * iters * (double)nsm * 8 * 256;
+    *tflops_out = flops / (best * 1e-3) / 1e12;
+    return RSGDF_OK;
+}
+
+}  // extern "C"

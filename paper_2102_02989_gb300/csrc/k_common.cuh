@@ -1,0 +1,107 @@
+// Device-side declarations shared by the library's CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "rsgdf_internal.h"
+
+namespace rsgdf {
+
+constexpr double KPI = 3.141592653589793238462643383279502884;
+constexpr double KPI2_5 = 17.493418327624862846262821679872;  // pi^{5/2}
+
+// Cartesian exponents (lx, ly, lz) of each component, lexicographic order
+static __constant__ const signed char c_cart[LMAX + 1][NC_MAX][3] = {
+    {{0, 0, 0}},
+    {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},
+    {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}},
+    {{3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}},
+};
+
+struct DevShells {
+    const int *l, *nprim, *poff, *foff;
+    const double *cen, *exps, *cn;
+};
+
+struct SRTripleDev {
+    int P, mu, nu, pair;
+    int nwin, win_off, nd, nsph;
+    double Rc_cut, amu, anu;
+    long long item_off;
+};
+
+struct SRArgs {
+    DevShells ao, ax;
+    const SRTripleDev *tri;
+    int tri_begin, tri_end;
+    long long item_begin, item_end;
+    const double *win;
+    const int *pair_doff, *dlist, *sph;
+    double a[9];    // lattice vectors (rows)
+    double bq[9];   // b_i / 2 pi: fractional coordinates
+    int nk[3];
+    int Nk;
+    double omega;
+    double *X;
+    long long s_lt, s_dt, s_P, s_mu, s_nu;
+    int pfunc0;
+    int bc;
+    int warp_bytes;
+    unsigned long long *term_count;   // [LTOT_MAX+1] or NULL
+};
+
+// BvK cell (mesh order, last index fastest) of an integer lattice vector
+__host__ __device__ __forceinline__ int bvk_bin(int i, int j, int k, const int *nk)
+{
+    int a = i % nk[0]; if (a < 0) a += nk[0];
+    int b = j % nk[1]; if (b < 0) b += nk[1];
+    int c = k % nk[2]; if (c < 0) c += nk[2];
+    return (a * nk[1] + b) * nk[2] + c;
+}
+
+// e^{sign i k.R} for k-mesh index k and BvK cell index R (both mesh order):
+// angle = 2 pi sum_i (n_i j_i mod N_i)/N_i, reduced in integers.
+__device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int sign, double &c, double &s)
+{
+    int n2 = k % nk[2], n1 = (k / nk[2]) % nk[1], n0 = k / (nk[1] * nk[2]);
+    int j2 = cell % nk[2], j1 = (cell / nk[2]) % nk[1], j0 = cell / (nk[1] * nk[2]);
+    double f = (double)((n0 * j0) % nk[0]) / nk[0] + (double)((n1 * j1) % nk[1]) / nk[1] +
+               (double)((n2 * j2) % nk[2]) / nk[2];
+    sincospi(2.0 * f, &s, &c);
+    s *= sign;
+}
+
+int upload_boys_table(const double *tab, cudaStream_t st);
+int launch_sr(int L, SRArgs args, int ncomp_max, cudaStream_t st);
+__global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S);
+__global__ void k_ovlp_fold(DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist, const double *a9,
+                            const int *nk3, int Nk, double *Sf);
+__global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,
+                             const double *Sf, const int *nk3, int Nk, double fac);
+
+// G-space and phase kernels (k_gspace.cu)
+struct GArgs {
+    const int *g;          // [NG][3] integer G coordinates
+    int NG;
+    double b[9];           // reciprocal vectors (rows)
+    double f12[3];         // fractional coordinates of k12, in [-1/2, 1/2)
+    double vol, omega;
+    int full_coulomb;      // 1: no erf damping (route used only for checks)
+};
+
+int launch_aux_ft(const GArgs &G, DevShells ax, int s0, int s1, int pfunc0, int nP, double *W, double *F,
+                  cudaStream_t st);
+int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist,
+               const double *a9, const int *nk3, int Nk, double *Y, cudaStream_t st);
+int launch_zgemm_tn(int M, int N, int K, int batch, const double *A, const double *B, long long strideB,
+                    double *C, long long strideC, cudaStream_t st);
+int launch_phase1(const double *X, long long m, int Nk, int ndt, int k12, const double *ph, double *T, int accumulate,
+                  cudaStream_t st);
+int launch_g0_outer(double *J, int n, const double *S, double fac, cudaStream_t st);
+int launch_g0_fold(double *T, long long m, int Nk, int nP, int nao, const double *SP, const double *Sf, double fac,
+                   cudaStream_t st);
+int launch_phase2(const double *T, long long m, int Nk, const int *pair_list, const int *pair_k2, int npl,
+                  const double *ph, double *V, int accumulate, cudaStream_t st);
+int launch_cholesky(int n, int nk, const double *J, double *Lo, int *info, cudaStream_t st);
+int launch_probe_fp64(double *out, int iters, cudaStream_t st);
+
+}  // namespace rsgdf

@@ -1,0 +1,489 @@
+// Reciprocal-space part of RSGDF (Eqs. VPmunu_LR and AFT_pairden), the Bloch
+// phase contractions of folded lattice sums (Eq. BvK_latsum_LR), the FP64
+// Cholesky factorisation of j2c, and the FP64 throughput probe.
+#include <cuda_runtime.h>
+
+#include "k_common.cuh"
+
+namespace rsgdf {
+
+constexpr int EMT = 2 * LMAX + 1;
+constexpr int EAB_SZ = (LMAX + 1) * (LMAX + 1) * EMT;
+
+__device__ static void pair_E_g(int la, int lb, double a, double b, double Ax, double Bx, double *E)
+{
+    double p = a + b;
+    double Px = (a * Ax + b * Bx) / p;
+    double XPA = Px - Ax, XPB = Px - Bx, XAB = Ax - Bx;
+    double h = 0.5 / p;
+    for (int k = 0; k < EAB_SZ; k++) E[k] = 0.0;
+#define EE(i, j, t) E[((i) * (LMAX + 1) + (j)) * EMT + (t)]
+    EE(0, 0, 0) = exp(-(a * b / p) * XAB * XAB);
+    for (int i = 0; i <= la; i++)
+        for (int j = 0; j <= lb; j++) {
+            if (i == 0 && j == 0) continue;
+            for (int t = 0; t <= i + j; t++) {
+                double v;
+                if (i > 0) {
+                    v = XPA * EE(i - 1, j, t);
+                    if (t > 0) v += h * EE(i - 1, j, t - 1);
+                    if (t + 1 <= i - 1 + j) v += (t + 1) * EE(i - 1, j, t + 1);
+                } else {
+                    v = XPB * EE(i, j - 1, t);
+                    if (t > 0) v += h * EE(i, j - 1, t - 1);
+                    if (t + 1 <= i + j - 1) v += (t + 1) * EE(i, j - 1, t + 1);
+                }
+                EE(i, j, t) = v;
+            }
+        }
+#undef EE
+}
+
+__device__ __forceinline__ void qvec(const GArgs &G, int ig, double q[3])
+{
+    double n0 = G.g[3 * ig] + G.f12[0], n1 = G.g[3 * ig + 1] + G.f12[1], n2 = G.g[3 * ig + 2] + G.f12[2];
+#pragma unroll
+    for (int x = 0; x < 3; x++) q[x] = n0 * G.b[x] + n1 * G.b[3 + x] + n2 * G.b[6 + x];
+}
+
+// W[G][P] = 4 pi/Omega e^{-q^2/4w^2}/q^2 conj(chi^_P(q)) (0 at q = 0) and,
+// when F != NULL, F[G][P] = chi^_P(q).  chi^ of x^c e^{-g r^2} at C:
+// (pi/g)^{3/2} e^{-q^2/4g} e^{-iq.C} prod_x sum_tau E^{c_x}_tau (-i q_x)^tau.
+__global__ void k_aux_ft(GArgs G, DevShells ax, int s0, int s1, int pfunc0, int nP, double *W, double *F)
+{
+    int ig = blockIdx.x * blockDim.x + threadIdx.x;
+    int P = s0 + blockIdx.y;
+    if (ig >= G.NG || P >= s1) return;
+    double q[3];
+    qvec(G, ig, q);
+    double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    double w = 0.0;
+    if (q2 >= 1e-14) {
+        w = 4.0 * KPI / G.vol / q2;
+        if (!G.full_coulomb) w *= exp(-q2 / (4.0 * G.omega * G.omega));
+    }
+    int l = ax.l[P], nc = (l + 1) * (l + 2) / 2;
+    double re[NC_MAX], im[NC_MAX];
+    for (int c = 0; c < nc; c++) { re[c] = 0.0; im[c] = 0.0; }
+    const double *C = ax.cen + 3 * P;
+    double qC = q[0] * C[0] + q[1] * C[1] + q[2] * C[2];
+    double sc, cc;
+    sincos(qC, &sc, &cc);
+    for (int k = 0; k < ax.nprim[P]; k++) {
+        int o = ax.poff[P] + k;
+        double g = ax.exps[o];
+        double E[(LMAX + 1) * (LMAX + 1)];
+        double h = 0.5 / g;
+        for (int z = 0; z < (LMAX + 1) * (LMAX + 1); z++) E[z] = 0.0;
+        E[0] = 1.0;
+        for (int c = 1; c <= l; c++)
+            for (int t = 0; t <= c; t++) {
+                double v = 0.0;
+                if (t > 0) v += h * E[(c - 1) * (LMAX + 1) + t - 1];
+                if (t + 1 <= c - 1) v += (t + 1) * E[(c - 1) * (LMAX + 1) + t + 1];
+                E[c * (LMAX + 1) + t] = v;
+            }
+        // 1D polynomials f_x(c) = sum_tau E^c_tau (-i q_x)^tau
+        double pr[3][LMAX + 1], pi[3][LMAX + 1];
+        for (int x = 0; x < 3; x++)
+            for (int c = 0; c <= l; c++) {
+                double ar = 0.0, ai = 0.0, wr = 1.0, wi = 0.0;
+                for (int t = 0; t <= c; t++) {
+                    double e = E[c * (LMAX + 1) + t];
+                    ar += e * wr;
+                    ai += e * wi;
+                    double nr = wi * q[x], ni = -wr * q[x];   // times (-i q)
+                    wr = nr;
+                    wi = ni;
+                }
+                pr[x][c] = ar;
+                pi[x][c] = ai;
+            }
+        double base = ax.cn[o] * pow(KPI / g, 1.5) * exp(-q2 / (4.0 * g));
+        for (int ic = 0; ic < nc; ic++) {
+            const signed char *c = c_cart[l][ic];
+            double ar = pr[0][c[0]], ai = pi[0][c[0]];
+            double br = ar * pr[1][c[1]] - ai * pi[1][c[1]], bi = ar * pi[1][c[1]] + ai * pr[1][c[1]];
+            double cr = br * pr[2][c[2]] - bi * pi[2][c[2]], ci = br * pi[2][c[2]] + bi * pr[2][c[2]];
+            re[ic] += base * cr;
+            im[ic] += base * ci;
+        }
+    }
+    int pf = ax.foff[P] - pfunc0;
+    for (int ic = 0; ic < nc; ic++) {
+        // times e^{-i q.C}
+        double vr = re[ic] * cc + im[ic] * sc, vi = im[ic] * cc - re[ic] * sc;
+        long long o = (long long)ig * nP + pf + ic;
+        W[2 * o] = w * vr;
+        W[2 * o + 1] = -w * vi;
+        if (F) {
+            F[2 * o] = vr;
+            F[2 * o + 1] = vi;
+        }
+    }
+}
+
+int launch_aux_ft(const GArgs &G, DevShells ax, int s0, int s1, int pfunc0, int nP, double *W, double *F,
+                  cudaStream_t st)
+{
+    (void)nP;
+    dim3 grid((G.NG + 127) / 128, s1 - s0);
+    k_aux_ft<<<grid, 128, 0, st>>>(G, ax, s0, s1, pfunc0, nP, W, F);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// Y[dt][G][mu][nu] = sum_{d -> dt} int phi_mu^0 phi_nu^d e^{-i q.r} dr (Eq.
+// AFT_pairden folded on the BvK cells of d).  Block = (G chunk, dt, shell
+// pair); the Hermite coefficients of each (d, primitive pair) are shared
+// through shared memory by the block's threads (one G each).
+constexpr int AFT_THREADS = 128;
+
+__global__ void __launch_bounds__(AFT_THREADS) k_aft(GArgs G, DevShells ao, int nshell, int nao, const int *pair_doff,
+                                                     const int *dlist, const double *a9, const int *nk3, int Nk,
+                                                     double *Y)
+{
+    __shared__ double E[3][EAB_SZ];
+    const int ig = blockIdx.x * AFT_THREADS + threadIdx.x;
+    const int dt = blockIdx.y, pr = blockIdx.z;
+    const int mu = pr / nshell, nu = pr % nshell;
+    const int lm = ao.l[mu], ln = ao.l[nu];
+    const int ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
+    int nk[3] = {nk3[0], nk3[1], nk3[2]};
+    double q[3] = {0, 0, 0}, q2 = 0.0;
+    const bool on = ig < G.NG;
+    if (on) {
+        qvec(G, ig, q);
+        q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    }
+    double accr[NC_MAX * NC_MAX], acci[NC_MAX * NC_MAX];
+    for (int z = 0; z < ncm * ncn; z++) { accr[z] = 0.0; acci[z] = 0.0; }
+    const double *Av = ao.cen + 3 * mu;
+    for (int di = pair_doff[pr]; di < pair_doff[pr + 1]; di++) {
+        const int d0 = dlist[3 * di], d1 = dlist[3 * di + 1], d2 = dlist[3 * di + 2];
+        if (bvk_bin(d0, d1, d2, nk) != dt) continue;
+        double Bv[3];
+        for (int x = 0; x < 3; x++) Bv[x] = ao.cen[3 * nu + x] + d0 * a9[x] + d1 * a9[3 + x] + d2 * a9[6 + x];
+        for (int i = 0; i < ao.nprim[mu]; i++)
+            for (int j = 0; j < ao.nprim[nu]; j++) {
+                const int oi = ao.poff[mu] + i, oj = ao.poff[nu] + j;
+                const double ea = ao.exps[oi], eb = ao.exps[oj], p = ea + eb;
+                __syncthreads();
+                if (threadIdx.x < 3) pair_E_g(lm, ln, ea, eb, Av[threadIdx.x], Bv[threadIdx.x], E[threadIdx.x]);
+                __syncthreads();
+                if (!on) continue;
+                double Pc[3];
+                for (int x = 0; x < 3; x++) Pc[x] = (ea * Av[x] + eb * Bv[x]) / p;
+                const double base = ao.cn[oi] * ao.cn[oj] * pow(KPI / p, 1.5) * exp(-q2 / (4.0 * p));
+                double sp, cp;
+                sincos(q[0] * Pc[0] + q[1] * Pc[1] + q[2] * Pc[2], &sp, &cp);
+                const double br = base * cp, bi = -base * sp;   // base e^{-i q.P}
+                double fr[3][(LMAX + 1) * (LMAX + 1)], fi[3][(LMAX + 1) * (LMAX + 1)];
+                for (int x = 0; x < 3; x++)
+                    for (int a = 0; a <= lm; a++)
+                        for (int b = 0; b <= ln; b++) {
+                            double ar = 0.0, ai = 0.0, wr = 1.0, wi = 0.0;
+                            for (int t = 0; t <= a + b; t++) {
+                                double e = E[x][(a * (LMAX + 1) + b) * EMT + t];
+                                ar += e * wr;
+                                ai += e * wi;
+                                double nr = wi * q[x], ni = -wr * q[x];
+                                wr = nr;
+                                wi = ni;
+                            }
+                            fr[x][a * (LMAX + 1) + b] = ar;
+                            fi[x][a * (LMAX + 1) + b] = ai;
+                        }
+                for (int ia = 0; ia < ncm; ia++)
+                    for (int ib = 0; ib < ncn; ib++) {
+                        const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
+                        int i0 = ca[0] * (LMAX + 1) + cb[0], i1 = ca[1] * (LMAX + 1) + cb[1], i2 = ca[2] * (LMAX + 1) + cb[2];
+                        double xr = fr[0][i0] * fr[1][i1] - fi[0][i0] * fi[1][i1];
+                        double xi = fr[0][i0] * fi[1][i1] + fi[0][i0] * fr[1][i1];
+                        double yr = xr * fr[2][i2] - xi * fi[2][i2];
+                        double yi = xr * fi[2][i2] + xi * fr[2][i2];
+                        accr[ia * ncn + ib] += yr * br - yi * bi;
+                        acci[ia * ncn + ib] += yr * bi + yi * br;
+                    }
+            }
+    }
+    if (!on) return;
+    const int mf = ao.foff[mu], nf = ao.foff[nu];
+    for (int ia = 0; ia < ncm; ia++)
+        for (int ib = 0; ib < ncn; ib++) {
+            long long o = (((long long)dt * G.NG + ig) * nao + mf + ia) * nao + nf + ib;
+            Y[2 * o] = accr[ia * ncn + ib];
+            Y[2 * o + 1] = acci[ia * ncn + ib];
+        }
+}
+
+int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist,
+               const double *a9, const int *nk3, int Nk, double *Y, cudaStream_t st)
+{
+    dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
+    k_aft<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, pair_doff, dlist, a9, nk3, Nk, Y);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// C[b][m][n] += sum_k A[k][m] B[b][k][n], complex FP64 (interleaved).
+constexpr int GB_M = 32, GB_N = 32, GB_K = 16;
+
+__global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const double2 *A, const double2 *B,
+                                                  long long strideB, double2 *C, long long strideC)
+{
+    __shared__ double2 As[GB_K][GB_M];
+    __shared__ double2 Bs[GB_K][GB_N];
+    const int b = blockIdx.z;
+    const double2 *Bb = B + b * strideB;
+    double2 *Cb = C + b * strideC;
+    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double cr[2][2] = {{0, 0}, {0, 0}}, ci[2][2] = {{0, 0}, {0, 0}};
+    for (int k0 = 0; k0 < K; k0 += GB_K) {
+        for (int e = threadIdx.x; e < GB_K * GB_M; e += 256) {
+            int kk = e / GB_M, mm = e % GB_M;
+            int gk = k0 + kk, gm = m0 + mm;
+            As[kk][mm] = (gk < K && gm < M) ? A[(long long)gk * M + gm] : make_double2(0.0, 0.0);
+        }
+        for (int e = threadIdx.x; e < GB_K * GB_N; e += 256) {
+            int kk = e / GB_N, nn = e % GB_N;
+            int gk = k0 + kk, gn = n0 + nn;
+            Bs[kk][nn] = (gk < K && gn < N) ? Bb[(long long)gk * N + gn] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; kk++) {
+            double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+            double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+            double2 av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    cr[i][j] = fma(av[i].x, bv[j].x, fma(-av[i].y, bv[j].y, cr[i][j]));
+                    ci[i][j] = fma(av[i].x, bv[j].y, fma(av[i].y, bv[j].x, ci[i][j]));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            int gm = m0 + ty * 2 + i, gn = n0 + tx * 2 + j;
+            if (gm < M && gn < N) {
+                double2 c = Cb[(long long)gm * N + gn];
+                c.x += cr[i][j];
+                c.y += ci[i][j];
+                Cb[(long long)gm * N + gn] = c;
+            }
+        }
+}
+
+int launch_zgemm_tn(int M, int N, int K, int batch, const double *A, const double *B, long long strideB, double *C,
+                    long long strideC, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return RSGDF_OK;
+    dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, batch);
+    k_zgemm_tn<<<grid, 256, 0, st>>>(M, N, K, (const double2 *)A, (const double2 *)B, strideB / 2, (double2 *)C,
+                                     strideC / 2);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// T[dt][i] (=|+=) sum_lt conj(ph[k12][lt]) X[lt][dt][i] for dt < ndt;
+// ph[k][cell] = e^{i k.cell}
+__global__ void k_phase1(const double *X, long long m, int Nk, int ndt, int k12, const double2 *ph, double2 *T,
+                         int accumulate)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)ndt * m) return;
+    int dt = (int)(id / m);
+    long long i = id - (long long)dt * m;
+    double re = 0.0, im = 0.0;
+    for (int lt = 0; lt < Nk; lt++) {
+        double2 p = ph[(long long)k12 * Nk + lt];
+        double x = X[((long long)lt * ndt + dt) * m + i];
+        re = fma(p.x, x, re);
+        im = fma(-p.y, x, im);
+    }
+    if (accumulate) {
+        double2 t = T[id];
+        t.x += re;
+        t.y += im;
+        T[id] = t;
+    } else {
+        T[id] = make_double2(re, im);
+    }
+}
+
+int launch_phase1(const double *X, long long m, int Nk, int ndt, int k12, const double *ph, double *T, int accumulate,
+                  cudaStream_t st)
+{
+    long long n = (long long)ndt * m;
+    k_phase1<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, m, Nk, ndt, k12, (const double2 *)ph, (double2 *)T,
+                                                         accumulate);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// J[P][Q] -= fac S_P S_Q  (the q = 0 term of the SR kernel at k = 0)
+__global__ void k_g0_outer(double2 *J, int n, const double *S, double fac)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)n * n) return;
+    int P = (int)(id / n), Q = (int)(id % n);
+    J[id].x -= fac * S[P] * S[Q];
+}
+
+int launch_g0_outer(double *J, int n, const double *S, double fac, cudaStream_t st)
+{
+    long long tot = (long long)n * n;
+    k_g0_outer<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((double2 *)J, n, S, fac);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// T[dt][P][mu][nu] -= fac S_P Sf[dt][mu][nu]  (k12 = 0 only)
+__global__ void k_g0_fold(double2 *T, long long m, int Nk, int nP, int nao, const double *SP, const double *Sf,
+                          double fac)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)Nk * m) return;
+    int dt = (int)(id / m);
+    long long i = id - (long long)dt * m;
+    long long nn = (long long)nao * nao;
+    int P = (int)(i / nn);
+    long long mn = i - (long long)P * nn;
+    T[id].x -= fac * SP[P] * Sf[(long long)dt * nn + mn];
+}
+
+int launch_g0_fold(double *T, long long m, int Nk, int nP, int nao, const double *SP, const double *Sf, double fac,
+                   cudaStream_t st)
+{
+    long long n = (long long)Nk * m;
+    k_g0_fold<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double2 *)T, m, Nk, nP, nao, SP, Sf, fac);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// V[pair][i] (=|+=) sum_dt ph[k2][dt] T[dt][i] for the pairs of one k12
+__global__ void k_phase2(const double2 *T, long long m, int Nk, const int *pair_list, const int *pair_k2, int npl,
+                         const double2 *ph, double2 *V, int accumulate)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)npl * m) return;
+    int j = (int)(id / m);
+    long long i = id - (long long)j * m;
+    int k2 = pair_k2[j];
+    double re = 0.0, im = 0.0;
+    for (int dt = 0; dt < Nk; dt++) {
+        double2 p = ph[(long long)k2 * Nk + dt];
+        double2 t = T[(long long)dt * m + i];
+        re = fma(p.x, t.x, fma(-p.y, t.y, re));
+        im = fma(p.x, t.y, fma(p.y, t.x, im));
+    }
+    long long o = (long long)pair_list[j] * m + i;
+    if (accumulate) {
+        double2 v = V[o];
+        v.x += re;
+        v.y += im;
+        V[o] = v;
+    } else {
+        V[o] = make_double2(re, im);
+    }
+}
+
+int launch_phase2(const double *T, long long m, int Nk, const int *pair_list, const int *pair_k2, int npl,
+                  const double *ph, double *V, int accumulate, cudaStream_t st)
+{
+    long long n = (long long)npl * m;
+    if (n <= 0) return RSGDF_OK;
+    k_phase2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)T, m, Nk, pair_list, pair_k2, npl,
+                                                         (const double2 *)ph, (double2 *)V, accumulate);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// Right-looking Cholesky J = L L^H of one Hermitian matrix per block (lower
+// triangle used).  info[k] = -1 on success, else the first pivot whose
+// Schur complement is not positive.
+__global__ void __launch_bounds__(1024) k_cholesky(int n, const double2 *J, double2 *Lo, int *info)
+{
+    const int kk = blockIdx.x;
+    const double2 *A = J + (long long)kk * n * n;
+    double2 *Lk = Lo + (long long)kk * n * n;
+    __shared__ int bad;
+    __shared__ double piv;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+        int i = (int)(e / n), j = (int)(e % n);
+        Lk[e] = (j <= i) ? A[e] : make_double2(0.0, 0.0);
+    }
+    if (threadIdx.x == 0) bad = -1;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        if (threadIdx.x == 0) {
+            double d = Lk[(long long)j * n + j].x;
+            if (!(d > 0.0)) {
+                bad = j;
+                piv = 1.0;
+            } else {
+                piv = sqrt(d);
+                Lk[(long long)j * n + j] = make_double2(piv, 0.0);
+            }
+        }
+        __syncthreads();
+        if (bad >= 0) break;
+        const double inv = 1.0 / piv;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double2 v = Lk[(long long)i * n + j];
+            Lk[(long long)i * n + j] = make_double2(v.x * inv, v.y * inv);
+        }
+        __syncthreads();
+        // trailing update of the lower triangle: L[i][c] -= L[i][j] conj(L[c][j]), j < c <= i
+        const int m = n - j - 1;
+        const long long tot = (long long)m * (m + 1) / 2;
+        for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+            // e -> (r, c) with 0 <= c <= r < m
+            int r = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+            while ((long long)(r + 1) * (r + 2) / 2 <= e) r++;
+            while ((long long)r * (r + 1) / 2 > e) r--;
+            int c = (int)(e - (long long)r * (r + 1) / 2);
+            int i = j + 1 + r, cc = j + 1 + c;
+            double2 a = Lk[(long long)i * n + j], b = Lk[(long long)cc * n + j];
+            double2 t = Lk[(long long)i * n + cc];
+            t.x -= a.x * b.x + a.y * b.y;
+            t.y -= a.y * b.x - a.x * b.y;
+            Lk[(long long)i * n + cc] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && info) info[kk] = bad;
+}
+
+int launch_cholesky(int n, int nk, const double *J, double *Lo, int *info, cudaStream_t st)
+{
+    k_cholesky<<<nk, 1024, 0, st>>>(n, (const double2 *)J, (double2 *)Lo, info);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// FP64 FMA throughput probe: independent chains, no memory traffic.
+__global__ void k_probe_fp64(double *out, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = threadIdx.x * 1e-3 + i;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = fma(x[i], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s += x[i];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int launch_probe_fp64(double *out, int iters, cudaStream_t st)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_probe_fp64<<<nsm * 8, 256, 0, st>>>(out, iters, 0.999999, 1e-7);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+}  // namespace rsgdf

@@ -1,0 +1,90 @@
+// Internal declarations of the RSGDF library (host planner <-> CUDA kernels).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rsgdf.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
+namespace rsgdf {
+
+constexpr int LMAX = RSGDF_LMAX;
+constexpr int LTOT_MAX = 3 * LMAX;              // highest total angular momentum of a triple
+constexpr int NC_MAX = (LMAX + 1) * (LMAX + 2) / 2;
+constexpr int NBIN_MAX = 128;                    // largest k-mesh (BvK cells) supported
+constexpr double SCREEN_DR = 1.0;                // window width of the R12 cutoffs (Bohr)
+constexpr double SCREEN_EPS_PRIME = 1e-4;        // truncation of S_h (Supplementary Material)
+
+// Boys table: F_m(T_i), T_i = i * BOYS_H, i = 0..BOYS_NT-1, m = 0..BOYS_NM-1
+constexpr double BOYS_H = 0.1;
+constexpr int BOYS_NT = 401;
+constexpr double BOYS_TMAX = 40.0;
+constexpr int BOYS_TAYLOR = 8;
+constexpr int BOYS_NM = LTOT_MAX + BOYS_TAYLOR + 2;
+
+__host__ __device__ constexpr inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr inline int ntuv(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+
+struct Lattice {
+    double a[3][3];
+    double b[3][3];
+    double vol;
+    int nk[3];
+    int Nk;
+    double r_round;   // max distance of a point to the lattice point of its rounded coordinates
+    int nnf;          // lattice points within 3 Omega^{1/3}
+};
+
+struct HBasis {
+    int nshell = 0;
+    std::vector<int> l, nprim, poff, foff;
+    std::vector<double> center, exps, cn;  // cn: normalised contraction coefficients
+    int nfunc = 0;
+};
+
+// One screened SR triple (aux shell P, "AO" shells mu, nu).
+struct SRTriple {
+    int P, mu, nu, pair;
+    int L;
+    int nwin, win_off;
+    int nd;           // leading entries of the pair's sorted d list with R12 <= R12_max
+    int nsph;         // leading entries of the sphere list with |l| <= Rc_cut + r_round
+    double Rc_cut, amu, anu;
+    long long item_off;
+};
+
+struct SRPlan {
+    std::vector<SRTriple> tri;           // sorted by L
+    std::vector<double> win;             // R12 cutoffs per window
+    std::vector<int> pair_doff;          // [npair+1]
+    std::vector<int> dlist;              // int3 per d, sorted by R12 per pair
+    std::vector<int> sph;                // int3 per lattice vector sorted by length
+    std::vector<double> sph_len;
+    std::vector<int> class_tri_begin;    // per L: first triple index, size LTOT_MAX+2
+    long long n_items = 0;
+};
+
+// Host planner entry points (planner.cpp)
+int make_lattice(const rsgdf_cell *cell, Lattice &L, std::string &err);
+int load_basis(const rsgdf_basis *b, HBasis &h, std::string &err, bool allow_empty = false);
+// basis made of the aux shells followed by one unit s function (exponent 0)
+void unit_partner_basis(const HBasis &aux, HBasis &out);
+int derive_params(const Lattice &L, const rsgdf_opts *o, double &omega, int gmesh[3], std::string &err);
+// j3c SR plan for aux shells [s0, s1)
+void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, int s1, double omega,
+               double eps, SRPlan &plan);
+// j2c SR plan: "AO" basis = aux + unit partner, pairs (Q, unit)
+void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double omega, double eps,
+               SRPlan &plan);
+void boys_table(std::vector<double> &tab);  // [BOYS_NT][BOYS_NM]
+// AFT pair screening: list of d per AO shell pair with some primitive pair above eps
+void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int> &pair_doff,
+                std::vector<int> &dlist);
+long long sr_term_flops(int L);   // algorithmic FP64 flops of one SR term of total angular momentum L
+
+}  // namespace rsgdf

@@ -1,0 +1,245 @@
+"""Thin Python binding of the C ABI in ``include/rsgdf.h`` (ctypes).
+
+Argument marshalling only: every step of the j3c / j2c / k-phase paths runs in
+the CUDA library ``_build/librsgdf.so``.  PyTorch supplies device memory and the
+current CUDA stream.  There is no CPU fallback: if the library cannot be loaded
+or no sm_103a device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "librsgdf.so")
+_lock = threading.Lock()
+_lib = None
+
+RSGDF_OK, RSGDF_EINVAL, RSGDF_ENOMEM, RSGDF_ENOTPD, RSGDF_ETIMEOUT, RSGDF_EDEVICE, RSGDF_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+RSGDF_FP64, RSGDF_MIXED = 0, 1
+RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
+
+# names exported by the library (every declaration of include/rsgdf.h)
+EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase",
+           "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64")
+
+
+class RsgdfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("rsgdf error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Basis(C.Structure):
+    _fields_ = [("nshell", C.c_int), ("l", C.c_void_p), ("nprim", C.c_void_p),
+                ("prim_off", C.c_void_p), ("center", C.c_void_p), ("exps", C.c_void_p),
+                ("coeffs", C.c_void_p)]
+
+
+class _Cell(C.Structure):
+    _fields_ = [("a", C.c_double * 9), ("kmesh", C.c_int * 3)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("omega", C.c_double), ("gmesh", C.c_int * 3), ("eps_screen", C.c_double),
+                ("eps_lr", C.c_double), ("precision", C.c_int), ("screening", C.c_int),
+                ("mlp", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sr_terms", C.c_longlong), ("sr_integrals", C.c_longlong),
+                ("sr_flops", C.c_longlong), ("aft_units", C.c_longlong),
+                ("lr_flops", C.c_longlong), ("omega", C.c_double), ("gmesh", C.c_int * 3),
+                ("n_launch", C.c_int)]
+
+    def asdict(self):
+        return {"sr_terms": self.sr_terms, "sr_integrals": self.sr_integrals,
+                "sr_flops": self.sr_flops, "aft_units": self.aft_units, "lr_flops": self.lr_flops,
+                "omega": self.omega, "gmesh": tuple(self.gmesh), "n_launch": self.n_launch}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load the CUDA library (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _b
+        if _b.needs_build():
+            _b.build()
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("librsgdf.so is missing: run paper_2102_02989_gb300.build.build()")
+        lib = C.CDLL(_LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        lib.rsgdf_j2c.argtypes = [vp, vp, vp, i, vp, vp, vp, vp]
+        for n in ("rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c"):
+            getattr(lib, n).argtypes = [vp, vp, vp, vp, i, vp, i, i, vp]
+        lib.rsgdf_kphase.argtypes = [vp, vp, C.c_longlong, i, vp, vp, vp]
+        lib.rsgdf_last_stats.argtypes = [vp]
+        lib.rsgdf_params.argtypes = [vp, vp, vp, vp]
+        lib.rsgdf_last_error.restype = C.c_char_p
+        lib.rsgdf_probe_fp64.argtypes = [vp, vp]
+        for n in EXPORTS:
+            if n != "rsgdf_last_error":
+                getattr(lib, n).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != RSGDF_OK:
+        raise RsgdfError(rc, load().rsgdf_last_error().decode())
+
+
+class _BasisRef:
+    def __init__(self, b):
+        self.l = np.ascontiguousarray(b.l, dtype=np.int32)
+        self.nprim = np.ascontiguousarray(b.nprim, dtype=np.int32)
+        self.prim_off = np.ascontiguousarray(b.prim_off, dtype=np.int32)
+        self.center = np.ascontiguousarray(b.center, dtype=np.float64)
+        self.exps = np.ascontiguousarray(b.exps, dtype=np.float64)
+        self.coeffs = np.ascontiguousarray(b.coeffs, dtype=np.float64)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        self.s = _Basis(len(self.l), p(self.l), p(self.nprim), p(self.prim_off), p(self.center),
+                        p(self.exps), p(self.coeffs))
+        self.nfunc = int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in self.l))
+
+    def ref(self):
+        return C.byref(self.s)
+
+
+def _cell(a, kmesh):
+    c = _Cell()
+    av = np.asarray(a, dtype=np.float64).reshape(9)
+    for k in range(9):
+        c.a[k] = float(av[k])
+    for k in range(3):
+        c.kmesh[k] = int(kmesh[k])
+    return c
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _opts(omega=None, gmesh=None, eps_screen=1e-8, eps_lr=1e-8, precision=RSGDF_FP64,
+          screening=RSGDF_SCREEN_BOUND, mlp=None, stream=None):
+    o = _Opts()
+    o.omega = float(omega) if omega else 0.0
+    for k in range(3):
+        o.gmesh[k] = int(gmesh[k]) if gmesh is not None else 0
+    o.eps_screen, o.eps_lr = float(eps_screen), float(eps_lr)
+    o.precision, o.screening = int(precision), int(screening)
+    o.mlp = mlp
+    o.stream = _stream_ptr(stream)
+    return o
+
+
+def _nfunc(b, s0, s1):
+    return int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in np.asarray(b.l)[s0:s1]))
+
+
+def rsgdf_params(a, kmesh, omega=None, gmesh=None, eps_lr=1e-8):
+    lib = load()
+    c = _cell(a, kmesh)
+    o = _Opts()
+    o.omega = float(omega) if omega else 0.0
+    for k in range(3):
+        o.gmesh[k] = int(gmesh[k]) if gmesh is not None else 0
+    o.eps_screen, o.eps_lr = 1e-8, float(eps_lr)
+    w = C.c_double()
+    g = (C.c_int * 3)()
+    _check(lib.rsgdf_params(C.byref(c), C.byref(o), C.byref(w), g))
+    return float(w.value), tuple(int(x) for x in g)
+
+
+def _j3c_call(name, a, kmesh, ao, aux, kpairs, shells=None, out=None, **opt):
+    import torch
+    lib = load()
+    ra, rx = _BasisRef(ao), _BasisRef(aux)
+    s0, s1 = shells if shells is not None else (0, len(rx.l))
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    nP = _nfunc(aux, s0, s1)
+    shape = (len(kp), nP, ra.nfunc, ra.nfunc)
+    if out is None:
+        out = torch.zeros(shape, dtype=torch.complex128, device="cuda")
+    assert out.is_cuda and out.dtype == torch.complex128 and tuple(out.shape) == shape and out.is_contiguous()
+    c = _cell(a, kmesh)
+    o = _opts(**opt)
+    rc = getattr(lib, name)(C.byref(c), ra.ref(), rx.ref(), C.byref(o), len(kp),
+                            kp.ctypes.data_as(C.c_void_p), s0, s1, C.c_void_p(out.data_ptr()))
+    _check(rc)
+    return out
+
+
+def rsgdf_j3c_sr(a, kmesh, ao, aux, kpairs, shells=None, out=None, **opt):
+    """SR part incl. the G = 0 correction; overwrites ``out`` [pair][P][mu][nu] (complex128, cuda)."""
+    return _j3c_call("rsgdf_j3c_sr", a, kmesh, ao, aux, kpairs, shells, out, **opt)
+
+
+def rsgdf_j3c_lr(a, kmesh, ao, aux, kpairs, shells=None, out=None, **opt):
+    """LR part; ADDED to ``out``."""
+    return _j3c_call("rsgdf_j3c_lr", a, kmesh, ao, aux, kpairs, shells, out, **opt)
+
+
+def rsgdf_j3c(a, kmesh, ao, aux, kpairs, shells=None, out=None, **opt):
+    """SR + G = 0 + LR; overwrites ``out``."""
+    return _j3c_call("rsgdf_j3c", a, kmesh, ao, aux, kpairs, shells, out, **opt)
+
+
+def rsgdf_j2c(a, kmesh, aux, klist, cholesky=True, **opt):
+    import torch
+    lib = load()
+    rx = _BasisRef(aux)
+    kl = np.ascontiguousarray(np.asarray(klist, dtype=np.int32).reshape(-1))
+    J = torch.zeros((len(kl), rx.nfunc, rx.nfunc), dtype=torch.complex128, device="cuda")
+    L = torch.zeros_like(J) if cholesky else None
+    info = torch.full((len(kl),), -2, dtype=torch.int32, device="cuda")
+    c = _cell(a, kmesh)
+    o = _opts(**opt)
+    _check(lib.rsgdf_j2c(C.byref(c), rx.ref(), C.byref(o), len(kl), kl.ctypes.data_as(C.c_void_p),
+                         C.c_void_p(J.data_ptr()), C.c_void_p(L.data_ptr()) if L is not None else None,
+                         C.c_void_p(info.data_ptr())))
+    return J, L, info
+
+
+def rsgdf_kphase(a, kmesh, X, kpairs, out=None, stream=None):
+    """V[pair][i] = sum_{lt,dt} e^{-i k12.lt} e^{i k2.dt} X[lt][dt][i]; X float64 cuda [Nk][Nk][m]."""
+    import torch
+    lib = load()
+    assert X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()
+    nk = int(np.prod(kmesh))
+    m = X.numel() // (nk * nk)
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    if out is None:
+        out = torch.empty((len(kp), m), dtype=torch.complex128, device="cuda")
+    c = _cell(a, kmesh)
+    _check(lib.rsgdf_kphase(C.byref(c), C.c_void_p(X.data_ptr()), m, len(kp),
+                            kp.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
+                            _stream_ptr(stream)))
+    return out
+
+
+def rsgdf_last_stats() -> dict:
+    s = Stats()
+    _check(load().rsgdf_last_stats(C.byref(s)))
+    return s.asdict()
+
+
+def rsgdf_last_error() -> str:
+    return load().rsgdf_last_error().decode()
+
+
+def rsgdf_probe_fp64(stream=None) -> float:
+    v = C.c_double()
+    _check(load().rsgdf_probe_fp64(C.byref(v), _stream_ptr(stream)))
+    return float(v.value)

@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/rsgdf.h declares; argument errors come back as status codes before
+any device work (so they are checked without a GPU); the host-side omega /
+G-mesh rule agrees with its restatement in the tests."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2102_02989_gb300 import inputs
+from rules_ref import gmesh_for, omega_for
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rs():
+    from paper_2102_02989_gb300 import rsgdf
+    rsgdf.load()
+    return rsgdf
+
+
+def test_header_symbols_exported(rs):
+    hdr = open(os.path.join(ROOT, "include", "rsgdf.h")).read()
+    names = set(re.findall(r"^\s*(?:int|const char \*)\s*(rsgdf_\w+)\s*\(", hdr, re.M))
+    assert names, "no declarations found"
+    lib = rs.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names <= set(rs.EXPORTS)
+
+
+def test_params_rule_matches(rs):
+    for p in (inputs.config1(), inputs.config2(), inputs.config2((4, 4, 4))):
+        if p.omega:
+            w, gm = rs.rsgdf_params(p.a, p.kmesh, omega=p.omega, eps_lr=p.eps_lr)
+            assert gm == gmesh_for(p.a, p.omega, p.eps_lr, p.kmesh)
+        else:
+            w, gm = rs.rsgdf_params(p.a, p.kmesh, gmesh=p.gmesh, eps_lr=p.eps_lr)
+            assert abs(w - omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)) < 1e-14
+
+
+@pytest.mark.parametrize("bad", ["npair", "kidx", "shells", "eps", "gmesh_even", "lmax", "exp"])
+def test_argument_errors_without_device(rs, bad):
+    p = inputs.tiny()
+    kw = dict(omega=0.9, eps_screen=1e-10, eps_lr=1e-10)
+    kp, sh, ao = [(0, 0)], None, p.ao
+    if bad == "kidx":
+        kp = [(0, 3)]
+    if bad == "shells":
+        sh = (2, 2)
+    if bad == "eps":
+        kw["eps_screen"] = 0.0
+    if bad == "gmesh_even":
+        kw["gmesh"] = (6, 7, 7)
+    if bad == "lmax":
+        ao = inputs.make_basis([(4, (0, 0, 0), [1.0], [1.0])])
+    if bad == "exp":
+        ao = inputs.make_basis([(0, (0, 0, 0), [-1.0], [1.0])])
+    lib = rs.load()
+    import ctypes as C
+    ra, rx = rs._BasisRef(ao), rs._BasisRef(p.aux)
+    o = rs._Opts()
+    o.omega, o.eps_screen, o.eps_lr = kw["omega"], kw["eps_screen"], kw["eps_lr"]
+    for i in range(3):
+        o.gmesh[i] = kw.get("gmesh", (0, 0, 0))[i]
+    c = rs._cell(p.a, (1, 1, 1))
+    kpa = np.ascontiguousarray(np.asarray(kp, np.int32).reshape(-1, 2))
+    npair = 0 if bad == "npair" else len(kpa)
+    s0, s1 = sh if sh else (0, len(rx.l))
+    rc = lib.rsgdf_j3c(C.byref(c), ra.ref(), rx.ref(), C.byref(o), npair, kpa.ctypes.data_as(C.c_void_p), s0, s1,
+                       C.c_void_p(16))
+    assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+    assert rs.rsgdf_last_error() != ""
