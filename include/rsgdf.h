@@ -155,6 +155,12 @@ typedef struct {
     double omega;
     int gmesh[3];
     int n_launch;            /* kernels launched by the call */
+    /* device time (ms, CUDA events on the call's stream) per phase */
+    double sr_ms;            /* SR lattice-sum kernels */
+    double aft_ms;           /* pair and aux Fourier transforms */
+    double lr_gemm_ms;       /* LR contraction GEMMs */
+    double phase_ms;         /* Bloch-phase contractions and the G = 0 correction */
+    double other_ms;         /* Cholesky, overlaps, aux charges */
 } rsgdf_stats;
 
 int rsgdf_last_stats(rsgdf_stats *out);

@@ -22,6 +22,45 @@ static thread_local cudaStream_t t_stats_stream = nullptr;
 static thread_local unsigned long long *t_count_host = nullptr;   // pinned [LTOT_MAX+1]
 static thread_local bool t_count_valid = false;
 
+// Per-phase device timers: an event pair around each launch group, summed
+// when the statistics are read.
+enum { PH_SR = 0, PH_AFT, PH_GEMM, PH_PHASE, PH_OTHER, PH_N };
+struct PhaseTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    cudaStream_t st = nullptr;
+    void reset(cudaStream_t s)
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+        ev.clear();
+        kind.clear();
+        st = s;
+    }
+    cudaEvent_t mark()
+    {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        return e;
+    }
+    void begin(int k)
+    {
+        kind.push_back(k);
+        mark();
+    }
+    void end() { mark(); }
+    void totals(double *ms)
+    {
+        for (int i = 0; i < PH_N; i++) ms[i] = 0.0;
+        for (size_t i = 0; i + 1 < ev.size() && i / 2 < kind.size(); i += 2) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ms[kind[i / 2]] += t;
+        }
+    }
+};
+static thread_local PhaseTimer t_timer;
+
 static int fail(int code, const std::string &msg)
 {
     t_err = msg;
@@ -266,6 +305,7 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     RC(check_device());
     cudaStream_t st = (cudaStream_t)opts->stream;
     RC(ensure_boys(st));
+    t_timer.reset(st);
     Scratch S(st);
     const int nao = ao.nfunc;
     const int pfunc0 = ax.foff[s0];
@@ -305,8 +345,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     RC(S.upload(dplist, plist));
     RC(S.upload(dpk2, pk2));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, LTOT_MAX + 1));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 1), st));
+    RC(S.alloc(dcnt, LTOT_MAX + 2));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 2), st));
 
     // SR folded sums X[lt][dt][P][mu][nu]
     double *X = nullptr;
@@ -315,24 +355,59 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
         RC(S.alloc(X, (size_t)Nk * Nk * m));
         CU(cudaMemsetAsync(X, 0, sizeof(double) * Nk * Nk * m, st));
+        t_timer.begin(PH_SR);
         RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
                   dcnt, st, nlaunch));
+        t_timer.end();
     }
-    // AFT pair lists (also the overlaps of the G = 0 correction)
+    // AFT pair lists (also the overlaps of the G = 0 correction): entries
+    // (pair, d, primitive pair) grouped by (pair, BvK cell of d)
     std::vector<int> apoff, alist;
     plan_pairs(L, ao, opts->eps_lr, apoff, alist);
-    int *dapoff, *dalist;
-    RC(S.upload(dapoff, apoff));
+    std::vector<PairEntry> ent;
+    std::vector<int> seg((size_t)ao.nshell * ao.nshell * Nk + 1, 0);
+    long long tab_len = 0;
+    {
+        std::vector<std::vector<int>> bybin(Nk);
+        for (int pr = 0; pr < ao.nshell * ao.nshell; pr++) {
+            int mu = pr / ao.nshell, nu = pr % ao.nshell;
+            long long esz = 5 + 3LL * (ao.l[mu] + 1) * (ao.l[nu] + 1) * (ao.l[mu] + ao.l[nu] + 2) / 2;
+            for (auto &v : bybin) v.clear();
+            for (int di = apoff[pr]; di < apoff[pr + 1]; di++)
+                bybin[bvk_bin(alist[3 * di], alist[3 * di + 1], alist[3 * di + 2], L.nk)].push_back(di);
+            for (int dt = 0; dt < Nk; dt++) {
+                seg[(size_t)pr * Nk + dt] = (int)ent.size();
+                for (int i = 0; i < ao.nprim[mu]; i++)
+                    for (int j = 0; j < ao.nprim[nu]; j++)
+                        for (int di : bybin[dt]) {
+                            ent.push_back({tab_len, pr, di, i, j});
+                            tab_len += esz;
+                        }
+            }
+        }
+        seg[(size_t)ao.nshell * ao.nshell * Nk] = (int)ent.size();
+    }
+    PairEntry *dent;
+    int *dseg, *dalist;
+    double *ptab;
+    RC(S.upload(dent, ent));
+    RC(S.upload(dseg, seg));
     RC(S.upload(dalist, alist));
+    RC(S.alloc(ptab, (size_t)tab_len));
+    t_timer.begin(PH_AFT);
+    RC(launch_pair_prep(dao, ao.nshell, dent, (int)ent.size(), dalist, da9, ptab, st));
+    t_timer.end();
+    nlaunch++;
     double *SP = nullptr, *Sf = nullptr;
     const double g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
     if ((mode & MODE_SR) && groups.count(0)) {
         RC(S.alloc(SP, nP));
         RC(S.alloc(Sf, (size_t)Nk * nao * nao));
+        t_timer.begin(PH_OTHER);
         k_aux_charge<<<(s1 - s0 + 63) / 64, 64, 0, st>>>(dax, s0, s1, pfunc0, SP);
-        int nth = ao.nshell * ao.nshell * Nk;
-        k_ovlp_fold<<<(nth + 127) / 128, 128, 0, st>>>(dao, ao.nshell, nao, dapoff, dalist, da9, dnk, Nk, Sf);
         CU(cudaGetLastError());
+        RC(launch_ovlp_fold(dao, ao.nshell, nao, dent, dseg, ptab, Nk, Sf, st));
+        t_timer.end();
         nlaunch += 2;
     }
     // G-space data
@@ -353,6 +428,7 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         const int k12 = gkey[gi];
         bool have = false;
         if (mode & MODE_SR) {
+            t_timer.begin(PH_PHASE);
             RC(launch_phase1(X, m, Nk, Nk, k12, dph, T, 0, st));
             nlaunch++;
             have = true;
@@ -360,6 +436,7 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
                 RC(launch_g0_fold(T, m, Nk, nP, nao, SP, Sf, g0fac, st));
                 nlaunch++;
             }
+            t_timer.end();
         }
         if (mode & MODE_LR) {
             if (!have) CU(cudaMemsetAsync(T, 0, sizeof(double) * 2 * Nk * m, st));
@@ -372,27 +449,28 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
             k12_frac(L, k12, G.f12);
             G.vol = L.vol;
             G.omega = omega;
+            t_timer.begin(PH_AFT);
             RC(launch_aux_ft(G, dax, s0, s1, pfunc0, nP, W, nullptr, st));
-            RC(launch_aft(G, dao, ao.nshell, nao, dapoff, dalist, da9, dnk, Nk, Y, st));
+            RC(launch_aft(G, dao, ao.nshell, nao, dent, dseg, ptab, Nk, Y, st));
+            t_timer.end();
+            t_timer.begin(PH_GEMM);
             RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, T, 2 * m, st));
+            t_timer.end();
             nlaunch += 3;
         }
+        t_timer.begin(PH_PHASE);
         RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V,
                          (mode == MODE_LR) ? 1 : 0, st));
+        t_timer.end();
         nlaunch++;
     }
     if (mode & MODE_LR) {
-        for (int mu = 0; mu < ao.nshell; mu++)
-            for (int nu = 0; nu < ao.nshell; nu++) {
-                int pr = mu * ao.nshell + nu;
-                aft_units += (long long)(apoff[pr + 1] - apoff[pr]) * ao.nprim[mu] * ao.nprim[nu];
-            }
-        aft_units *= (long long)NG * (long long)gkey.size();
+        aft_units = (long long)ent.size() * NG * (long long)gkey.size();
     }
     CU(cudaGetLastError());
     // statistics
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 1)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 1), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 2)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 2), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -448,6 +526,7 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     RC(check_device());
     cudaStream_t st = (cudaStream_t)opts->stream;
     RC(ensure_boys(st));
+    t_timer.reset(st);
     Scratch S(st);
     unit_partner_basis(ax, axu);
     const int naux = ax.nfunc, Nk = L.Nk;
@@ -460,8 +539,8 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     double *dph;
     RC(S.upload(dph, ph));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, LTOT_MAX + 1));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 1), st));
+    RC(S.alloc(dcnt, LTOT_MAX + 2));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 2), st));
     // SR: X2[lt][P][Q] = sum_{l -> lt} (chi_P^l | erfc | chi_Q^0), the
     // three-center kernel with the unit function as the second pair member
     SRPlan plan;
@@ -470,7 +549,9 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     double *X2;
     RC(S.alloc(X2, (size_t)Nk * m));
     CU(cudaMemsetAsync(X2, 0, sizeof(double) * Nk * m, st));
+    t_timer.begin(PH_SR);
     RC(run_sr(S, L, plan, daxu, dax, axu, ax, omega, X2, m, 0, naux, 1, 0, 0, dcnt, st, nlaunch));
+    t_timer.end();
     double *SP;
     RC(S.alloc(SP, naux));
     k_aux_charge<<<(ax.nshell + 63) / 64, 64, 0, st>>>(dax, 0, ax.nshell, 0, SP);
@@ -489,12 +570,14 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     for (int i = 0; i < nk; i++) {
         const int k = kidx[i];
         double *Jk = J_out + (size_t)2 * i * m;
+        t_timer.begin(PH_PHASE);
         RC(launch_phase1(X2, m, Nk, 1, k, dph, Jk, 0, st));
         nlaunch++;
         if (k == 0) {
             RC(launch_g0_outer(Jk, naux, SP, g0fac, st));
             nlaunch++;
         }
+        t_timer.end();
         GArgs G;
         memset(&G, 0, sizeof(G));
         G.g = dg;
@@ -504,19 +587,25 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
         k12_frac(L, k, G.f12);
         G.vol = L.vol;
         G.omega = omega;
+        t_timer.begin(PH_AFT);
         RC(launch_aux_ft(G, dax, 0, ax.nshell, 0, naux, W, F, st));
+        t_timer.end();
+        t_timer.begin(PH_GEMM);
         RC(launch_zgemm_tn(naux, naux, NG, 1, W, F, 0, Jk, 0, st));
+        t_timer.end();
         nlaunch += 2;
     }
     if (L_out) {
+        t_timer.begin(PH_OTHER);
         RC(launch_cholesky(naux, nk, J_out, L_out, info_out, st));
+        t_timer.end();
         nlaunch++;
     } else if (info_out) {
         CU(cudaMemsetAsync(info_out, 0xff, sizeof(int) * nk, st));
     }
     CU(cudaGetLastError());
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 1)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 1), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 2)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 2), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -580,6 +669,14 @@ int rsgdf_last_stats(rsgdf_stats *out)
             t_stats.sr_terms += (long long)t_count_host[L];
             t_stats.sr_flops += (long long)t_count_host[L] * sr_term_flops(L);
         }
+        t_stats.sr_integrals = (long long)t_count_host[LTOT_MAX + 1];
+        double ms[PH_N];
+        t_timer.totals(ms);
+        t_stats.sr_ms = ms[PH_SR];
+        t_stats.aft_ms = ms[PH_AFT];
+        t_stats.lr_gemm_ms = ms[PH_GEMM];
+        t_stats.phase_ms = ms[PH_PHASE];
+        t_stats.other_ms = ms[PH_OTHER];
     }
     *out = t_stats;
     return RSGDF_OK;

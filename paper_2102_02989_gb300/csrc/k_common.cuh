@@ -73,8 +73,6 @@ __device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int 
 int upload_boys_table(const double *tab, cudaStream_t st);
 int launch_sr(int L, SRArgs args, int ncomp_max, cudaStream_t st);
 __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S);
-__global__ void k_ovlp_fold(DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist, const double *a9,
-                            const int *nk3, int Nk, double *Sf);
 __global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,
                              const double *Sf, const int *nk3, int Nk, double fac);
 
@@ -90,8 +88,16 @@ struct GArgs {
 
 int launch_aux_ft(const GArgs &G, DevShells ax, int s0, int s1, int pfunc0, int nP, double *W, double *F,
                   cudaStream_t st);
-int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist,
-               const double *a9, const int *nk3, int Nk, double *Y, cudaStream_t st);
+struct PairEntry {
+    long long off;   // offset of the entry in the table (doubles)
+    int pair, d, i, j;
+};
+int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist, const double *a9,
+                     double *tab, cudaStream_t st);
+int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
+               const double *tab, int Nk, double *Y, cudaStream_t st);
+int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,
+                     int Nk, double *Sf, cudaStream_t st);
 int launch_zgemm_tn(int M, int N, int K, int batch, const double *A, const double *B, long long strideB,
                     double *C, long long strideC, cudaStream_t st);
 int launch_phase1(const double *X, long long m, int Nk, int ndt, int k12, const double *ph, double *T, int accumulate,

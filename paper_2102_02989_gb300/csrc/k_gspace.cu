@@ -132,81 +132,137 @@ int launch_aux_ft(const GArgs &G, DevShells ax, int s0, int s1, int pfunc0, int 
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
-// Y[dt][G][mu][nu] = sum_{d -> dt} int phi_mu^0 phi_nu^d e^{-i q.r} dr (Eq.
-// AFT_pairden folded on the BvK cells of d).  Block = (G chunk, dt, shell
-// pair); the Hermite coefficients of each (d, primitive pair) are shared
-// through shared memory by the block's threads (one G each).
+// ---------------------------------------------------------------------------
+// Pair transforms (Eq. AFT_pairden) folded on the BvK cells of d.
+//
+// Entry = (AO shell pair, d, primitive pair): its Hermite coefficients, centre
+// and constants do not depend on G or k12 and are written once per call by
+// k_pair_prep.  Entry layout (doubles, compact per shell pair):
+//   [0..2] P (product centre), [3] 1/(4p), [4] c_i c_j (pi/p)^{3/2},
+//   then for x, y, z: E^{ab}_t for a <= lm, b <= ln, t <= a+b, packed by
+//   (a, b) with offset eoff(a, b) = sum of (a'+b'+1) over earlier (a', b').
+// Entries of one (pair, BvK cell) are contiguous and ordered by primitive pair.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int pair_e1(int lm, int ln) { return (lm + 1) * (ln + 1) * (lm + ln + 2) / 2; }
+
+__device__ __forceinline__ int eoff(int a, int b, int ln)
+{
+    // sum over (a', b') < (a, b) in row-major order of (a' + b' + 1)
+    int o = 0;
+    for (int x = 0; x < a; x++) o += (ln + 1) * (2 * x + ln + 2) / 2;
+    for (int y = 0; y < b; y++) o += a + y + 1;
+    return o;
+}
+
+__global__ void k_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist,
+                            const double *a9, double *tab)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const PairEntry en = ent[e];
+    const int mu = en.pair / nshell, nu = en.pair % nshell;
+    const int lm = ao.l[mu], ln = ao.l[nu];
+    const int oi = ao.poff[mu] + en.i, oj = ao.poff[nu] + en.j;
+    const double a = ao.exps[oi], b = ao.exps[oj], p = a + b;
+    const int d0 = dlist[3 * en.d], d1 = dlist[3 * en.d + 1], d2 = dlist[3 * en.d + 2];
+    double *out = tab + en.off;
+    double E[EAB_SZ];
+    const int n1 = pair_e1(lm, ln);
+    for (int x = 0; x < 3; x++) {
+        const double Ax = ao.cen[3 * mu + x];
+        const double Bx = ao.cen[3 * nu + x] + d0 * a9[x] + d1 * a9[3 + x] + d2 * a9[6 + x];
+        out[x] = (a * Ax + b * Bx) / p;
+        pair_E_g(lm, ln, a, b, Ax, Bx, E);
+        double *o = out + 5 + x * n1;
+        int k = 0;
+        for (int ia = 0; ia <= lm; ia++)
+            for (int ib = 0; ib <= ln; ib++)
+                for (int t = 0; t <= ia + ib; t++) o[k++] = E[(ia * (LMAX + 1) + ib) * EMT + t];
+    }
+    out[3] = 0.25 / p;
+    out[4] = ao.cn[oi] * ao.cn[oj] * KPI * sqrt(KPI) / (p * sqrt(p));
+}
+
+int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist, const double *a9,
+                     double *tab, cudaStream_t st)
+{
+    if (nent <= 0) return RSGDF_OK;
+    k_pair_prep<<<(nent + 127) / 128, 128, 0, st>>>(ao, nshell, ent, nent, dlist, a9, tab);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// Y[dt][G][mu][nu] = sum over the entries of (pair, dt) of
+//   c e^{-q^2/4p} e^{-i q.P} prod_x sum_t E^x_t (-i q_x)^t
 constexpr int AFT_THREADS = 128;
 
-__global__ void __launch_bounds__(AFT_THREADS) k_aft(GArgs G, DevShells ao, int nshell, int nao, const int *pair_doff,
-                                                     const int *dlist, const double *a9, const int *nk3, int Nk,
-                                                     double *Y)
+__global__ void __launch_bounds__(AFT_THREADS) k_aft(GArgs G, DevShells ao, int nshell, int nao, const PairEntry *ent,
+                                                     const int *seg, const double *tab, int Nk, double *Y)
 {
-    __shared__ double E[3][EAB_SZ];
     const int ig = blockIdx.x * AFT_THREADS + threadIdx.x;
     const int dt = blockIdx.y, pr = blockIdx.z;
+    if (ig >= G.NG) return;
     const int mu = pr / nshell, nu = pr % nshell;
     const int lm = ao.l[mu], ln = ao.l[nu];
     const int ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
-    int nk[3] = {nk3[0], nk3[1], nk3[2]};
-    double q[3] = {0, 0, 0}, q2 = 0.0;
-    const bool on = ig < G.NG;
-    if (on) {
-        qvec(G, ig, q);
-        q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    const int n1 = pair_e1(lm, ln);
+    double q[3];
+    qvec(G, ig, q);
+    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    // powers q_x^t, t <= 2 LMAX
+    double qp[3][EMT];
+    for (int x = 0; x < 3; x++) {
+        qp[x][0] = 1.0;
+        for (int t = 1; t <= lm + ln; t++) qp[x][t] = qp[x][t - 1] * q[x];
     }
     double accr[NC_MAX * NC_MAX], acci[NC_MAX * NC_MAX];
     for (int z = 0; z < ncm * ncn; z++) { accr[z] = 0.0; acci[z] = 0.0; }
-    const double *Av = ao.cen + 3 * mu;
-    for (int di = pair_doff[pr]; di < pair_doff[pr + 1]; di++) {
-        const int d0 = dlist[3 * di], d1 = dlist[3 * di + 1], d2 = dlist[3 * di + 2];
-        if (bvk_bin(d0, d1, d2, nk) != dt) continue;
-        double Bv[3];
-        for (int x = 0; x < 3; x++) Bv[x] = ao.cen[3 * nu + x] + d0 * a9[x] + d1 * a9[3 + x] + d2 * a9[6 + x];
-        for (int i = 0; i < ao.nprim[mu]; i++)
-            for (int j = 0; j < ao.nprim[nu]; j++) {
-                const int oi = ao.poff[mu] + i, oj = ao.poff[nu] + j;
-                const double ea = ao.exps[oi], eb = ao.exps[oj], p = ea + eb;
-                __syncthreads();
-                if (threadIdx.x < 3) pair_E_g(lm, ln, ea, eb, Av[threadIdx.x], Bv[threadIdx.x], E[threadIdx.x]);
-                __syncthreads();
-                if (!on) continue;
-                double Pc[3];
-                for (int x = 0; x < 3; x++) Pc[x] = (ea * Av[x] + eb * Bv[x]) / p;
-                const double base = ao.cn[oi] * ao.cn[oj] * pow(KPI / p, 1.5) * exp(-q2 / (4.0 * p));
-                double sp, cp;
-                sincos(q[0] * Pc[0] + q[1] * Pc[1] + q[2] * Pc[2], &sp, &cp);
-                const double br = base * cp, bi = -base * sp;   // base e^{-i q.P}
-                double fr[3][(LMAX + 1) * (LMAX + 1)], fi[3][(LMAX + 1) * (LMAX + 1)];
-                for (int x = 0; x < 3; x++)
-                    for (int a = 0; a <= lm; a++)
-                        for (int b = 0; b <= ln; b++) {
-                            double ar = 0.0, ai = 0.0, wr = 1.0, wi = 0.0;
-                            for (int t = 0; t <= a + b; t++) {
-                                double e = E[x][(a * (LMAX + 1) + b) * EMT + t];
-                                ar += e * wr;
-                                ai += e * wi;
-                                double nr = wi * q[x], ni = -wr * q[x];
-                                wr = nr;
-                                wi = ni;
-                            }
-                            fr[x][a * (LMAX + 1) + b] = ar;
-                            fi[x][a * (LMAX + 1) + b] = ai;
+    double last_inv4p = -1.0, gauss = 0.0;
+    const int e0 = seg[pr * Nk + dt], e1 = seg[pr * Nk + dt + 1];
+    for (int e = e0; e < e1; e++) {
+        const double *en = tab + ent[e].off;
+        const double inv4p = en[3];
+        if (inv4p != last_inv4p) {
+            gauss = exp(-q2 * inv4p);
+            last_inv4p = inv4p;
+        }
+        double sp, cp;
+        sincos(q[0] * en[0] + q[1] * en[1] + q[2] * en[2], &sp, &cp);
+        const double base = en[4] * gauss;
+        const double br = base * cp, bi = -base * sp;   // base e^{-i q.P}
+        // f_x(a, b) = sum_t E_t (-i q_x)^t: even t real, odd t imaginary
+        double fr[3][(LMAX + 1) * (LMAX + 1)], fi[3][(LMAX + 1) * (LMAX + 1)];
+        for (int x = 0; x < 3; x++) {
+            const double *Ex = en + 5 + x * n1;
+            int k = 0;
+            for (int a = 0; a <= lm; a++)
+                for (int b = 0; b <= ln; b++) {
+                    double re = 0.0, im = 0.0;
+                    for (int t = 0; t <= a + b; t++, k++) {
+                        // (-i)^t = 1, -i, -1, i
+                        const double v = Ex[k] * qp[x][t];
+                        switch (t & 3) {
+                        case 0: re += v; break;
+                        case 1: im -= v; break;
+                        case 2: re -= v; break;
+                        default: im += v; break;
                         }
-                for (int ia = 0; ia < ncm; ia++)
-                    for (int ib = 0; ib < ncn; ib++) {
-                        const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
-                        int i0 = ca[0] * (LMAX + 1) + cb[0], i1 = ca[1] * (LMAX + 1) + cb[1], i2 = ca[2] * (LMAX + 1) + cb[2];
-                        double xr = fr[0][i0] * fr[1][i1] - fi[0][i0] * fi[1][i1];
-                        double xi = fr[0][i0] * fi[1][i1] + fi[0][i0] * fr[1][i1];
-                        double yr = xr * fr[2][i2] - xi * fi[2][i2];
-                        double yi = xr * fi[2][i2] + xi * fr[2][i2];
-                        accr[ia * ncn + ib] += yr * br - yi * bi;
-                        acci[ia * ncn + ib] += yr * bi + yi * br;
                     }
+                    fr[x][a * (LMAX + 1) + b] = re;
+                    fi[x][a * (LMAX + 1) + b] = im;
+                }
+        }
+        for (int ia = 0; ia < ncm; ia++)
+            for (int ib = 0; ib < ncn; ib++) {
+                const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
+                const int i0 = ca[0] * (LMAX + 1) + cb[0], i1 = ca[1] * (LMAX + 1) + cb[1], i2 = ca[2] * (LMAX + 1) + cb[2];
+                const double xr = fr[0][i0] * fr[1][i1] - fi[0][i0] * fi[1][i1];
+                const double xi = fr[0][i0] * fi[1][i1] + fi[0][i0] * fr[1][i1];
+                const double yr = xr * fr[2][i2] - xi * fi[2][i2];
+                const double yi = xr * fi[2][i2] + xi * fr[2][i2];
+                accr[ia * ncn + ib] += yr * br - yi * bi;
+                acci[ia * ncn + ib] += yr * bi + yi * br;
             }
     }
-    if (!on) return;
     const int mf = ao.foff[mu], nf = ao.foff[nu];
     for (int ia = 0; ia < ncm; ia++)
         for (int ib = 0; ib < ncn; ib++) {
@@ -216,11 +272,47 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft(GArgs G, DevShells ao, int 
         }
 }
 
-int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist,
-               const double *a9, const int *nk3, int Nk, double *Y, cudaStream_t st)
+int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
+               const double *tab, int Nk, double *Y, cudaStream_t st)
 {
     dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
-    k_aft<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, pair_doff, dlist, a9, nk3, Nk, Y);
+    k_aft<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab, Nk, Y);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// Folded overlaps Sf[dt][mu][nu] = sum over the entries of (pair, dt) of
+// c prod_x E^x_0 (the transform at q = 0); one thread per (pair, dt).
+__global__ void k_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
+                            const double *tab, int Nk, double *Sf)
+{
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nshell * nshell * Nk) return;
+    const int pr = id / Nk, dt = id % Nk;
+    const int mu = pr / nshell, nu = pr % nshell;
+    const int lm = ao.l[mu], ln = ao.l[nu], ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
+    const int n1 = pair_e1(lm, ln);
+    double acc[NC_MAX * NC_MAX];
+    for (int z = 0; z < ncm * ncn; z++) acc[z] = 0.0;
+    for (int e = seg[pr * Nk + dt]; e < seg[pr * Nk + dt + 1]; e++) {
+        const double *en = tab + ent[e].off;
+        for (int ia = 0; ia < ncm; ia++)
+            for (int ib = 0; ib < ncn; ib++) {
+                const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
+                double v = en[4];
+                for (int x = 0; x < 3; x++) v *= en[5 + x * n1 + eoff(ca[x], cb[x], ln)];
+                acc[ia * ncn + ib] += v;
+            }
+    }
+    const int mf = ao.foff[mu], nf = ao.foff[nu];
+    for (int ia = 0; ia < ncm; ia++)
+        for (int ib = 0; ib < ncn; ib++) Sf[((long long)dt * nao + mf + ia) * nao + nf + ib] = acc[ia * ncn + ib];
+}
+
+int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,
+                     int Nk, double *Sf, cudaStream_t st)
+{
+    int n = nshell * nshell * Nk;
+    k_ovlp_fold<<<(n + 127) / 128, 128, 0, st>>>(ao, nshell, nao, ent, seg, tab, Nk, Sf);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

@@ -382,7 +382,10 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
             nT = 0;
         }
     }
-    if (lane == 0 && A.term_count) atomicAdd(A.term_count + L, kept);
+    if (lane == 0 && A.term_count) {
+        atomicAdd(A.term_count + L, kept);
+        atomicAdd(A.term_count + LTOT_MAX + 1, kept * (unsigned long long)ncomp);
+    }
 }
 
 typedef void (*SRKern)(SRArgs);
@@ -434,48 +437,6 @@ __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S
             S[ax.foff[P] - pfunc0 + ic] += base * E[c[0] * (LMAX + 1)] * E[c[1] * (LMAX + 1)] * E[c[2] * (LMAX + 1)];
         }
     }
-}
-
-// Folded overlaps Sf[dt][mu][nu] = sum_{d -> dt} (phi_mu^0 | phi_nu^d); one
-// thread per BvK cell and shell pair (deterministic order over its d's).
-__global__ void k_ovlp_fold(DevShells ao, int nshell, int nao, const int *pair_doff, const int *dlist, const double *a9,
-                            const int *nk3, int Nk, double *Sf)
-{
-    int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= nshell * nshell * Nk) return;
-    int pr = id / Nk, bin = id % Nk;
-    int mu = pr / nshell, nu = pr % nshell;
-    int lm = ao.l[mu], ln = ao.l[nu], ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
-    double acc[NC_MAX * NC_MAX];
-    for (int q = 0; q < ncm * ncn; q++) acc[q] = 0.0;
-    double E[3][EAB_SZ];
-    int nk[3] = {nk3[0], nk3[1], nk3[2]};
-    for (int di = pair_doff[pr]; di < pair_doff[pr + 1]; di++) {
-        int d0 = dlist[3 * di], d1 = dlist[3 * di + 1], d2 = dlist[3 * di + 2];
-        if (bvk_bin(d0, d1, d2, nk) != bin) continue;
-        double Av[3], Bv[3];
-        for (int x = 0; x < 3; x++) {
-            Av[x] = ao.cen[3 * mu + x];
-            Bv[x] = ao.cen[3 * nu + x] + d0 * a9[x] + d1 * a9[3 + x] + d2 * a9[6 + x];
-        }
-        for (int i = 0; i < ao.nprim[mu]; i++)
-            for (int j = 0; j < ao.nprim[nu]; j++) {
-                int oi = ao.poff[mu] + i, oj = ao.poff[nu] + j;
-                double ea = ao.exps[oi], eb = ao.exps[oj];
-                for (int x = 0; x < 3; x++) pair_E(lm, ln, ea, eb, Av[x], Bv[x], E[x]);
-                double base = ao.cn[oi] * ao.cn[oj] * pow(KPI / (ea + eb), 1.5);
-                for (int ia = 0; ia < ncm; ia++)
-                    for (int ib = 0; ib < ncn; ib++) {
-                        const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
-                        acc[ia * ncn + ib] += base * E[0][(ca[0] * (LMAX + 1) + cb[0]) * EMT] *
-                                              E[1][(ca[1] * (LMAX + 1) + cb[1]) * EMT] *
-                                              E[2][(ca[2] * (LMAX + 1) + cb[2]) * EMT];
-                    }
-            }
-    }
-    int mf = ao.foff[mu], nf = ao.foff[nu];
-    for (int ia = 0; ia < ncm; ia++)
-        for (int ib = 0; ib < ncn; ib++) Sf[((long long)bin * nao + mf + ia) * nao + nf + ib] = acc[ia * ncn + ib];
 }
 
 // V[pair][P][mu][nu] -= pi/(Omega omega^2) S_P sum_dt e^{i k.dt} Sf[dt][mu][nu]

@@ -2,7 +2,9 @@
 // the Supplementary Material's screening of the SR double lattice sum, work
 // lists for the kernels, the Boys-function table and the omega / G-box rule.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <cstring>
 #include <numeric>
 
@@ -189,6 +191,29 @@ int derive_params(const Lattice &L, const rsgdf_opts *o, double &omega, int gmes
 
 namespace {
 
+// static partition of [0, n) over the hardware threads
+template <class F>
+void parallel_for(int n, F f)
+{
+    int nt = (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 32));
+    if (n < 64 || nt == 1) {
+        for (int i = 0; i < n; i++) f(i);
+        return;
+    }
+    std::atomic<int> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; t++)
+        th.emplace_back([&]() {
+            for (;;) {
+                int i = next.fetch_add(1);
+                if (i >= n) break;
+                f(i);
+            }
+        });
+    for (auto &x : th) x.join();
+}
+
 struct Vec3 { double x, y, z; };
 inline Vec3 lat(const Lattice &L, int i, int j, int k)
 {
@@ -226,15 +251,21 @@ double w1s(const HBasis &b, int s, int idx)
 
 // Growth of a Cartesian pair of degrees (lm, ln) with separation R, and of the
 // erfc tail seen by degrees lP and lpair at distance R, relative to s functions.
+inline double ipow(double x, int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; i++) r *= x;
+    return r;
+}
 inline double grow_r12(int lm, int ln, double am, double an, double R)
 {
     double p = am + an;
-    return std::pow(1.0 + std::sqrt(4.0 * am) * an / p * R, lm) * std::pow(1.0 + std::sqrt(4.0 * an) * am / p * R, ln);
+    return ipow(1.0 + std::sqrt(4.0 * am) * an / p * R, lm) * ipow(1.0 + std::sqrt(4.0 * an) * am / p * R, ln);
 }
 inline double grow_rc(int lP, int lpair, double aP, double p, double eta2, double R)
 {
     double x = 2.0 * eta2 * eta2 * R;
-    return std::pow(1.0 + x / std::sqrt(aP), lP) * std::pow(1.0 + x / std::sqrt(p), lpair);
+    return ipow(1.0 + x / std::sqrt(aP), lP) * ipow(1.0 + x / std::sqrt(p), lpair);
 }
 
 // Eq. Ncell with dR = 1 Bohr
@@ -267,7 +298,7 @@ void pair_images(const Lattice &L, Vec3 d0, double rmax, PairImages &out)
 template <class F>
 double outer_root(F f, double lo, double hi, double eps)
 {
-    for (int it = 0; it < 200; it++) {
+    for (int it = 0; it < 64; it++) {
         double mid = 0.5 * (lo + hi);
         if (f(mid) >= eps) lo = mid; else hi = mid;
     }
@@ -281,42 +312,42 @@ struct Bounds {
     double amu, anu;
 };
 
-// The bounds for one (aux shell P, AO shell mu, AO shell nu).
-void triple_bounds(const Lattice &L, double omega, double eps, const HBasis &aux, int P, const HBasis &ao,
-                   int mu, int nu, Bounds &B)
+// Everything of the bounds that depends only on the AO shell pair.
+struct PairPart {
+    double am, an, p, beta;
+    int lm, ln;
+    double qp;        // sum over primitive pairs of the 1s weights / p^{3/2}
+    double Sh;        // Eq. S_h (with the growth factor), never below the largest term
+    double r12min;    // Eq. R12cutmin
+    double xm;        // argmax of x e^{-beta x^2} grow(x), the left bracket of Eq. bound_R12_FF
+};
+
+void pair_part(const Lattice &L, const HBasis &ao, int mu, int nu, PairPart &Q)
 {
-    int iP = diffuse_index(aux, P), im = diffuse_index(ao, mu), in = diffuse_index(ao, nu);
-    double aP = aux.exps[iP], am = ao.exps[im], an = ao.exps[in];
-    int lP = aux.l[P], lm = ao.l[mu], ln = ao.l[nu];
+    int im = diffuse_index(ao, mu), in = diffuse_index(ao, nu);
+    double am = ao.exps[im], an = ao.exps[in];
+    int lm = ao.l[mu], ln = ao.l[nu];
     double p = am + an, beta = am * an / p;
-    double eta1 = 1.0 / std::sqrt(1.0 / aP + 1.0 / p);
-    double eta2 = 1.0 / std::sqrt(1.0 / (eta1 * eta1) + 1.0 / (omega * omega));
-    // s-type prefactor pi^3 C_P C_mu C_nu / (a_P p)^{3/2}, summed over the
-    // primitive combinations of the contractions (decay rates stay those of
-    // the most diffuse primitives)
-    double qa = 0.0, qp = 0.0;
-    for (int k = 0; k < aux.nprim[P]; k++) {
-        int o = aux.poff[P] + k;
-        qa += w1s(aux, P, o) / std::pow(aux.exps[o], 1.5);
-    }
+    Q.am = am; Q.an = an; Q.p = p; Q.beta = beta; Q.lm = lm; Q.ln = ln;
+    Q.qp = 0.0;
     for (int i = 0; i < ao.nprim[mu]; i++)
         for (int j = 0; j < ao.nprim[nu]; j++) {
             int oi = ao.poff[mu] + i, oj = ao.poff[nu] + j;
-            qp += w1s(ao, mu, oi) * w1s(ao, nu, oj) / std::pow(ao.exps[oi] + ao.exps[oj], 1.5);
+            Q.qp += w1s(ao, mu, oi) * w1s(ao, nu, oj) / std::pow(ao.exps[oi] + ao.exps[oj], 1.5);
         }
-    double A = PI * PI * PI * qa * qp;
     Vec3 d0 = {ao.center[3 * nu] - ao.center[3 * mu], ao.center[3 * nu + 1] - ao.center[3 * mu + 1],
                ao.center[3 * nu + 2] - ao.center[3 * mu + 2]};
     double rprime = std::sqrt(-std::log(SCREEN_EPS_PRIME) / beta);   // h(R) = eps' radius
     PairImages img;
     pair_images(L, d0, rprime + 1e-9, img);
     auto hfun = [&](double R) { return std::exp(-beta * R * R) * grow_r12(lm, ln, am, an, R); };
-    // S_h (Eq. S_h): sum of h over images with e^{-beta R^2} >= eps', at least the largest term
     double Sh = 0.0, hbig = 0.0;
-    for (double r : img.r) {
-        double h = hfun(r);
-        if (std::exp(-beta * r * r) >= SCREEN_EPS_PRIME) Sh += h;
-        hbig = std::max(hbig, h);
+    std::vector<double> hv(img.r.size());
+    for (size_t i = 0; i < img.r.size(); i++) {
+        double r = img.r[i];
+        hv[i] = hfun(r);
+        if (std::exp(-beta * r * r) >= SCREEN_EPS_PRIME) Sh += hv[i];
+        hbig = std::max(hbig, hv[i]);
     }
     if (img.r.empty()) {   // no image within the eps' radius: take the nearest one
         PairImages near;
@@ -324,54 +355,80 @@ void triple_bounds(const Lattice &L, double omega, double eps, const HBasis &aux
         do { rr *= 2; pair_images(L, d0, rr, near); } while (near.r.empty());
         hbig = hfun(near.r[0]);
     }
-    Sh = std::max(Sh, hbig);
+    Q.Sh = std::max(Sh, hbig);
+    // Eq. R12cutmin: first x on a 0.01 Bohr grid where the continuum estimate
+    // is no smaller than the eps'-truncated image sum beyond x (suffix sums of
+    // the sorted images)
+    std::vector<double> suffix(img.r.size() + 1, 0.0);
+    for (size_t i = img.r.size(); i-- > 0;)
+        suffix[i] = suffix[i + 1] + ((std::exp(-beta * img.r[i] * img.r[i]) >= SCREEN_EPS_PRIME) ? hv[i] : 0.0);
+    double xmax = rprime + SCREEN_DR;
+    Q.r12min = xmax;
+    size_t pos = 0;
+    for (int ix = 0;; ix++) {
+        double x = 0.01 * ix;
+        if (x > xmax) break;
+        while (pos < img.r.size() && img.r[pos] <= x) pos++;
+        double est = 4.0 * PI / L.vol * x / (2.0 * beta) * std::exp(-beta * x * x) * grow_r12(lm, ln, am, an, x);
+        if (est >= suffix[pos]) { Q.r12min = x; break; }
+    }
+    double x0 = 1.0 / std::sqrt(2.0 * beta);
+    auto shape = [&](double x) { return x * std::exp(-beta * x * x) * grow_r12(lm, ln, am, an, x); };
+    Q.xm = x0;
+    double vm = shape(x0);
+    double step = 0.05 / std::sqrt(beta), top = x0 + 10.0 / std::sqrt(beta);
+    for (int it = 0;; it++) {
+        double t = it * step;
+        if (!(t < top)) break;
+        double v = shape(t);
+        if (v > vm) { vm = v; Q.xm = t; }
+    }
+}
+
+// The bounds for one (aux shell P, AO shell pair) from the pair part.
+void triple_bounds(const Lattice &L, double omega, double eps, const HBasis &aux, int P, const PairPart &Q,
+                   Bounds &B)
+{
+    int iP = diffuse_index(aux, P);
+    double aP = aux.exps[iP];
+    int lP = aux.l[P], lm = Q.lm, ln = Q.ln;
+    double p = Q.p, beta = Q.beta, am = Q.am, an = Q.an;
+    double eta1 = 1.0 / std::sqrt(1.0 / aP + 1.0 / p);
+    double eta2 = 1.0 / std::sqrt(1.0 / (eta1 * eta1) + 1.0 / (omega * omega));
+    // s-type prefactor pi^3 C_P C_mu C_nu / (a_P p)^{3/2}, summed over the
+    // primitive combinations of the contractions (decay rates stay those of
+    // the most diffuse primitives)
+    double qa = 0.0;
+    for (int k = 0; k < aux.nprim[P]; k++) {
+        int o = aux.poff[P] + k;
+        qa += w1s(aux, P, o) / std::pow(aux.exps[o], 1.5);
+    }
+    double A = PI * PI * PI * qa * Q.qp;
     B.amu = am;
     B.anu = an;
     // Eq. bound_Rc
-    double c0 = A * Sh * 4.0 * PI / L.vol / std::sqrt(PI) / (2.0 * eta2 * eta2 * eta2);
+    double c0 = A * Q.Sh * 4.0 * PI / L.vol / std::sqrt(PI) / (2.0 * eta2 * eta2 * eta2);
     auto grc = [&](double R) { return c0 / R * std::exp(-eta2 * eta2 * R * R) * grow_rc(lP, lm + ln, aP, p, eta2, R); };
     double hi = 1e-6;
     while (grc(hi) >= eps && hi < 1e4) hi *= 2;
     B.Rc_cut = (hi > 1e-6) ? outer_root(grc, 1e-6, hi, eps) : hi;
-    // Eq. R12cutmin: first x on a 0.01 Bohr grid where the continuum estimate
-    // is no smaller than the eps'-truncated image sum beyond x
-    double xmax = rprime + SCREEN_DR;
-    double r12min = xmax;
-    for (int ix = 0;; ix++) {
-        double x = 0.01 * ix;
-        if (x > xmax) break;
-        double est = 4.0 * PI / L.vol * x / (2.0 * beta) * std::exp(-beta * x * x) * grow_r12(lm, ln, am, an, x);
-        double tail = 0.0;
-        for (double r : img.r)
-            if (r > x && std::exp(-beta * r * r) >= SCREEN_EPS_PRIME) tail += hfun(r);
-        if (est >= tail) { r12min = x; break; }
-    }
     // Eq. bound_R12_FF per window, then Eq. bound_R12
     int nw = (int)std::floor(B.Rc_cut / SCREEN_DR) + 1;
     nw = std::min(nw, 512);
     B.r12.assign(nw, 0.0);
     B.r12_max = 0.0;
-    double x0 = 1.0 / std::sqrt(2.0 * beta);
     for (int w = 0; w < nw; w++) {
         double R = w * SCREEN_DR;
         double fR = (R < 1e-8) ? 2.0 * (eta1 - eta2) / std::sqrt(PI) : (std::erf(eta1 * R) - std::erf(eta2 * R)) / R;
         double c1 = A * cells_in_shell(L, R) * fR * grow_rc(lP, lm + ln, aP, p, eta2, R) * 4.0 * PI / L.vol / (2.0 * beta);
         auto g = [&](double x) { return c1 * x * std::exp(-beta * x * x) * grow_r12(lm, ln, am, an, x); };
-        double xm = x0, vm = g(x0);
-        double step = 0.05 / std::sqrt(beta), top = x0 + 10.0 / std::sqrt(beta);
-        for (int it = 0;; it++) {
-            double t = it * step;
-            if (!(t < top)) break;
-            double v = g(t);
-            if (v > vm) { vm = v; xm = t; }
-        }
         double x = 0.0;
-        if (vm >= eps) {
-            double b = xm + 1e-3;
+        if (g(Q.xm) >= eps) {
+            double b = Q.xm + 1e-3;
             while (g(b) >= eps && b < 1e4) b *= 2;
-            x = outer_root(g, xm, b, eps);
+            x = outer_root(g, Q.xm, b, eps);
         }
-        B.r12[w] = std::max(x, r12min);
+        B.r12[w] = std::max(x, Q.r12min);
         B.r12_max = std::max(B.r12_max, B.r12[w]);
     }
 }
@@ -457,15 +514,17 @@ void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, in
 {
     plan = SRPlan();
     int ns = ao.nshell;
+    std::vector<PairPart> pp((size_t)ns * ns);
     std::vector<Bounds> bnd((size_t)(s1 - s0) * ns * ns);
     std::vector<double> pair_rmax((size_t)ns * ns, 0.0);
+    parallel_for(ns * ns, [&](int pr) { pair_part(L, ao, pr / ns, pr % ns, pp[pr]); });
+    parallel_for((s1 - s0) * ns * ns, [&](int id) {
+        int P = s0 + id / (ns * ns), pr = id % (ns * ns);
+        triple_bounds(L, omega, eps, aux, P, pp[pr], bnd[id]);
+    });
     for (int P = s0; P < s1; P++)
-        for (int mu = 0; mu < ns; mu++)
-            for (int nu = 0; nu < ns; nu++) {
-                Bounds &B = bnd[((size_t)(P - s0) * ns + mu) * ns + nu];
-                triple_bounds(L, omega, eps, aux, P, ao, mu, nu, B);
-                pair_rmax[mu * ns + nu] = std::max(pair_rmax[mu * ns + nu], B.r12_max);
-            }
+        for (int pr = 0; pr < ns * ns; pr++)
+            pair_rmax[pr] = std::max(pair_rmax[pr], bnd[(size_t)(P - s0) * ns * ns + pr].r12_max);
     // per AO shell pair: d vectors with R12 <= max over P, sorted by R12
     plan.pair_doff.assign(ns * ns + 1, 0);
     std::vector<std::vector<double>> pair_r12(ns * ns);

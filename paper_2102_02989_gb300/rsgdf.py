@@ -53,12 +53,15 @@ class Stats(C.Structure):
     _fields_ = [("sr_terms", C.c_longlong), ("sr_integrals", C.c_longlong),
                 ("sr_flops", C.c_longlong), ("aft_units", C.c_longlong),
                 ("lr_flops", C.c_longlong), ("omega", C.c_double), ("gmesh", C.c_int * 3),
-                ("n_launch", C.c_int)]
+                ("n_launch", C.c_int), ("sr_ms", C.c_double), ("aft_ms", C.c_double),
+                ("lr_gemm_ms", C.c_double), ("phase_ms", C.c_double), ("other_ms", C.c_double)]
 
     def asdict(self):
         return {"sr_terms": self.sr_terms, "sr_integrals": self.sr_integrals,
                 "sr_flops": self.sr_flops, "aft_units": self.aft_units, "lr_flops": self.lr_flops,
-                "omega": self.omega, "gmesh": tuple(self.gmesh), "n_launch": self.n_launch}
+                "omega": self.omega, "gmesh": tuple(self.gmesh), "n_launch": self.n_launch,
+                "sr_ms": self.sr_ms, "aft_ms": self.aft_ms, "lr_gemm_ms": self.lr_gemm_ms,
+                "phase_ms": self.phase_ms, "other_ms": self.other_ms}
 
 
 def library_path() -> str:
