@@ -269,6 +269,8 @@ def main():
         "phases_ms_per_step": {k: v["ms"] for k, v in ph.items()},
         "phases_tflops": {k: v["tflops"] for k, v in ph.items()},
         "sr_terms_per_step": int(terms / args.steps), "sr_integrals_per_step": int(stats[0][1]["sr_integrals"]),
+        "sr_primitive_terms_per_step": int(sum(s3["sr_prim_terms"] + s2["sr_prim_terms"] for s2, s3 in stats) / args.steps),
+        "j3c_sr_by_L": {"terms": stats[-1][1]["sr_terms_by_L"], "ms": [round(x, 3) for x in stats[-1][1]["sr_ms_by_L"]]},
         "j3c_build_ms": statistics.median([s3["sr_ms"] + s3["aft_ms"] + s3["lr_gemm_ms"] + s3["phase_ms"] +
                                            s3["other_ms"] for _, s3 in stats]),
     }

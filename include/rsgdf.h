@@ -161,6 +161,9 @@ typedef struct {
     double lr_gemm_ms;       /* LR contraction GEMMs */
     double phase_ms;         /* Bloch-phase contractions and the G = 0 correction */
     double other_ms;         /* Cholesky, overlaps, aux charges */
+    long long sr_terms_by_L[10];   /* SR terms per total angular momentum L = lP + lmu + lnu */
+    long long sr_prim_terms;       /* SR terms times their primitive combinations */
+    double sr_ms_by_L[10];         /* device time of the SR kernel of each L class */
 } rsgdf_stats;
 
 int rsgdf_last_stats(rsgdf_stats *out);

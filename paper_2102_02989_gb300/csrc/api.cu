@@ -27,13 +27,14 @@ static thread_local bool t_count_valid = false;
 enum { PH_SR = 0, PH_AFT, PH_GEMM, PH_PHASE, PH_OTHER, PH_N };
 struct PhaseTimer {
     std::vector<cudaEvent_t> ev;
-    std::vector<int> kind;
+    std::vector<int> kind, cls;
     cudaStream_t st = nullptr;
     void reset(cudaStream_t s)
     {
         for (auto e : ev) cudaEventDestroy(e);
         ev.clear();
         kind.clear();
+        cls.clear();
         st = s;
     }
     cudaEvent_t mark()
@@ -44,18 +45,23 @@ struct PhaseTimer {
         ev.push_back(e);
         return e;
     }
-    void begin(int k)
+    void begin(int k, int c = -1)
     {
         kind.push_back(k);
+        cls.push_back(c);
         mark();
     }
     void end() { mark(); }
-    void totals(double *ms)
+    void totals(double *ms, double *cls_ms)
     {
         for (int i = 0; i < PH_N; i++) ms[i] = 0.0;
+        for (int i = 0; i <= LTOT_MAX; i++) cls_ms[i] = 0.0;
         for (size_t i = 0; i + 1 < ev.size() && i / 2 < kind.size(); i += 2) {
             float t = 0.0f;
-            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ms[kind[i / 2]] += t;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
+                ms[kind[i / 2]] += t;
+                if (cls[i / 2] >= 0) cls_ms[cls[i / 2]] += t;
+            }
         }
     }
 };
@@ -233,6 +239,9 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
                   cudaStream_t st, int &nlaunch)
 {
     if (plan.tri.empty()) return RSGDF_OK;
+    for (const SRTriple &t : plan.tri)
+        if (hax.nprim[t.P] * hao.nprim[t.mu] * hao.nprim[t.nu] > 64)
+            return fail(RSGDF_ENOTIMPL, "more than 64 primitive combinations in one shell triple");
     std::vector<SRTripleDev> td(plan.tri.size());
     for (size_t i = 0; i < plan.tri.size(); i++) {
         const SRTriple &t = plan.tri[i];
@@ -246,6 +255,48 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     RC(S.upload(dpoff, plan.pair_doff));
     RC(S.upload(dl, plan.dlist));
     RC(S.upload(dsph, plan.sph));
+    // Hermite tables of every (pair, d, primitive pair) of the SR d lists,
+    // shared by all aux shells (entries of one d contiguous, ij order)
+    const int npairs = hao.nshell * hao.nshell;
+    std::vector<long long> sr_doff(plan.pair_doff[npairs] + 1, 0);
+    std::vector<PairEntry> ent;
+    long long off = 0;
+    for (int pr = 0; pr < npairs; pr++) {
+        const int mu = pr / hao.nshell, nu = pr % hao.nshell;
+        const long long esz = ENT_HDR + 3LL * (hao.l[mu] + 1) * (hao.l[nu] + 1) * (hao.l[mu] + hao.l[nu] + 2) / 2;
+        for (int gd = plan.pair_doff[pr]; gd < plan.pair_doff[pr + 1]; gd++) {
+            sr_doff[gd] = off;
+            for (int i = 0; i < hao.nprim[mu]; i++)
+                for (int j = 0; j < hao.nprim[nu]; j++) {
+                    ent.push_back({off, pr, gd, i, j});
+                    off += esz;
+                }
+        }
+    }
+    PairEntry *dent;
+    long long *dsrdoff;
+    double *ptab;
+    RC(S.upload(dent, ent));
+    RC(S.upload(dsrdoff, sr_doff));
+    RC(S.alloc(ptab, (size_t)std::max(off, 1LL)));
+    double a9h[9], bq_unused[9];
+    int nk_unused[3];
+    fill_lattice(L, a9h, bq_unused, nk_unused);
+    double *da9;
+    RC(S.upload(da9, std::vector<double>(a9h, a9h + 9)));
+    t_timer.begin(PH_SR);
+    RC(launch_pair_prep(ao, hao.nshell, dent, (int)ent.size(), dl, da9, ptab, st));
+    t_timer.end();
+    nlaunch++;
+    // single-centre Hermite coefficients of every aux primitive
+    std::vector<double> ec((size_t)hax.exps.size() * (LMAX + 1) * (LMAX + 1), 0.0);
+    for (int sh = 0; sh < hax.nshell; sh++)
+        for (int k = 0; k < hax.nprim[sh]; k++) {
+            const int o = hax.poff[sh] + k;
+            single_E_host(hax.l[sh], hax.exps[o], &ec[(size_t)o * (LMAX + 1) * (LMAX + 1)]);
+        }
+    double *dec;
+    RC(S.upload(dec, ec));
     SRArgs A;
     memset(&A, 0, sizeof(A));
     A.ao = ao;
@@ -262,19 +313,40 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     A.s_lt = s_lt; A.s_dt = s_dt; A.s_P = s_P; A.s_mu = s_mu; A.s_nu = s_nu;
     A.pfunc0 = pfunc0;
     A.term_count = counts;
+    for (int x = 0; x < 9; x++) A.af[x] = (float)A.a[x];
+    A.ec_tab = dec;
+    A.ptab = ptab;
+    A.sr_doff = dsrdoff;
     for (int c = 0; c <= LTOT_MAX; c++) {
         int b = plan.class_tri_begin[c], e = plan.class_tri_begin[c + 1];
         if (b >= e) continue;
-        int ncmax = 0;
+        int ncmax = 0, wmax = 0, lmax_list = 0;
         for (int i = b; i < e; i++) {
             const SRTriple &t = plan.tri[i];
-            ncmax = std::max(ncmax, ncart(hax.l[t.P]) * ncart(hao.l[t.mu]) * ncart(hao.l[t.nu]));
+            const int lP = hax.l[t.P], lm = hao.l[t.mu], ln = hao.l[t.nu];
+            ncmax = std::max(ncmax, ncart(lP) * ncart(lm) * ncart(ln));
+            if (lP > 0) wmax = std::max(wmax, ncart(lP) * ntuv(lm + ln));
+            // coefficient-list length: sum over (a, b) of (ax+bx+1)(ay+by+1)(az+bz+1)
+            int tot = 0;
+            for (int ia = 0; ia < ncart(lm); ia++)
+                for (int ib = 0; ib < ncart(ln); ib++) {
+                    int ax[3], bx[3], n = 0;
+                    for (int x = lm; x >= 0; x--)
+                        for (int y = lm - x; y >= 0; y--) { if (n++ == ia) { ax[0] = x; ax[1] = y; ax[2] = lm - x - y; } }
+                    n = 0;
+                    for (int x = ln; x >= 0; x--)
+                        for (int y = ln - x; y >= 0; y--) { if (n++ == ib) { bx[0] = x; bx[1] = y; bx[2] = ln - x - y; } }
+                    tot += (ax[0] + bx[0] + 1) * (ax[1] + bx[1] + 1) * (ax[2] + bx[2] + 1);
+                }
+            lmax_list = std::max(lmax_list, tot);
         }
         A.tri_begin = b;
         A.tri_end = e;
         A.item_begin = plan.tri[b].item_off;
         A.item_end = (e < (int)plan.tri.size()) ? plan.tri[e].item_off : plan.n_items;
-        RC(launch_sr(c, A, ncmax, st));
+        t_timer.begin(PH_SR, c);
+        RC(launch_sr(c, A, ncmax, wmax, lmax_list, st));
+        t_timer.end();
         nlaunch++;
     }
     return RSGDF_OK;
@@ -345,8 +417,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     RC(S.upload(dplist, plist));
     RC(S.upload(dpk2, pk2));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, LTOT_MAX + 2));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 2), st));
+    RC(S.alloc(dcnt, 2 * LTOT_MAX + 4));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), st));
 
     // SR folded sums X[lt][dt][P][mu][nu]
     double *X = nullptr;
@@ -355,10 +427,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
         RC(S.alloc(X, (size_t)Nk * Nk * m));
         CU(cudaMemsetAsync(X, 0, sizeof(double) * Nk * Nk * m, st));
-        t_timer.begin(PH_SR);
         RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
                   dcnt, st, nlaunch));
-        t_timer.end();
     }
     // AFT pair lists (also the overlaps of the G = 0 correction): entries
     // (pair, d, primitive pair) grouped by (pair, BvK cell of d)
@@ -371,7 +441,7 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         std::vector<std::vector<int>> bybin(Nk);
         for (int pr = 0; pr < ao.nshell * ao.nshell; pr++) {
             int mu = pr / ao.nshell, nu = pr % ao.nshell;
-            long long esz = 5 + 3LL * (ao.l[mu] + 1) * (ao.l[nu] + 1) * (ao.l[mu] + ao.l[nu] + 2) / 2;
+            long long esz = ENT_HDR + 3LL * (ao.l[mu] + 1) * (ao.l[nu] + 1) * (ao.l[mu] + ao.l[nu] + 2) / 2;
             for (auto &v : bybin) v.clear();
             for (int di = apoff[pr]; di < apoff[pr + 1]; di++)
                 bybin[bvk_bin(alist[3 * di], alist[3 * di + 1], alist[3 * di + 2], L.nk)].push_back(di);
@@ -469,8 +539,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     }
     CU(cudaGetLastError());
     // statistics
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 2)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 2), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 4)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -539,8 +609,8 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     double *dph;
     RC(S.upload(dph, ph));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, LTOT_MAX + 2));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (LTOT_MAX + 2), st));
+    RC(S.alloc(dcnt, 2 * LTOT_MAX + 4));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), st));
     // SR: X2[lt][P][Q] = sum_{l -> lt} (chi_P^l | erfc | chi_Q^0), the
     // three-center kernel with the unit function as the second pair member
     SRPlan plan;
@@ -549,9 +619,7 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     double *X2;
     RC(S.alloc(X2, (size_t)Nk * m));
     CU(cudaMemsetAsync(X2, 0, sizeof(double) * Nk * m, st));
-    t_timer.begin(PH_SR);
     RC(run_sr(S, L, plan, daxu, dax, axu, ax, omega, X2, m, 0, naux, 1, 0, 0, dcnt, st, nlaunch));
-    t_timer.end();
     double *SP;
     RC(S.alloc(SP, naux));
     k_aux_charge<<<(ax.nshell + 63) / 64, 64, 0, st>>>(dax, 0, ax.nshell, 0, SP);
@@ -604,8 +672,8 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
         CU(cudaMemsetAsync(info_out, 0xff, sizeof(int) * nk, st));
     }
     CU(cudaGetLastError());
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (LTOT_MAX + 2)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (LTOT_MAX + 2), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 4)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -667,11 +735,14 @@ int rsgdf_last_stats(rsgdf_stats *out)
         t_stats.sr_flops = 0;
         for (int L = 0; L <= LTOT_MAX; L++) {
             t_stats.sr_terms += (long long)t_count_host[L];
-            t_stats.sr_flops += (long long)t_count_host[L] * sr_term_flops(L);
+            // the Hermite work is done per primitive combination of a term
+            t_stats.sr_flops += (long long)t_count_host[LTOT_MAX + 2 + L] * sr_term_flops(L);
+            t_stats.sr_prim_terms += (long long)t_count_host[LTOT_MAX + 2 + L];
         }
         t_stats.sr_integrals = (long long)t_count_host[LTOT_MAX + 1];
         double ms[PH_N];
-        t_timer.totals(ms);
+        t_timer.totals(ms, t_stats.sr_ms_by_L);
+        for (int L = 0; L <= LTOT_MAX; L++) t_stats.sr_terms_by_L[L] = (long long)t_count_host[L];
         t_stats.sr_ms = ms[PH_SR];
         t_stats.aft_ms = ms[PH_AFT];
         t_stats.lr_gemm_ms = ms[PH_GEMM];

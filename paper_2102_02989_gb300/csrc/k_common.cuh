@@ -37,6 +37,7 @@ struct SRArgs {
     const double *win;
     const int *pair_doff, *dlist, *sph;
     double a[9];    // lattice vectors (rows)
+    float af[9];    // the same in FP32 (pre-filter of the translations)
     double bq[9];   // b_i / 2 pi: fractional coordinates
     int nk[3];
     int Nk;
@@ -46,7 +47,11 @@ struct SRArgs {
     int pfunc0;
     int bc;
     int warp_bytes;
-    unsigned long long *term_count;   // [LTOT_MAX+1] or NULL
+    int ncomp_max, w_max, list_max;
+    unsigned long long *term_count;   // [LTOT_MAX+2] or NULL
+    const double *ec_tab;             // [aux primitive][(LMAX+1)^2] single-centre Hermite coefficients
+    const double *ptab;               // pair entries of the SR d list
+    const long long *sr_doff;         // [global d index] offset of its first entry
 };
 
 // BvK cell (mesh order, last index fastest) of an integer lattice vector
@@ -71,8 +76,9 @@ __device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int 
 }
 
 int upload_boys_table(const double *tab, cudaStream_t st);
-int launch_sr(int L, SRArgs args, int ncomp_max, cudaStream_t st);
+int launch_sr(int L, SRArgs args, int ncomp_max, int w_max, int list_max, cudaStream_t st);
 __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S);
+__host__ __device__ void single_E(int lc, double g, double *E);
 __global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,
                              const double *Sf, const int *nk3, int Nk, double fac);
 

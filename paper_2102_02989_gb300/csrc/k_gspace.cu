@@ -138,8 +138,8 @@ int launch_aux_ft(const GArgs &G, DevShells ax, int s0, int s1, int pfunc0, int 
 // Entry = (AO shell pair, d, primitive pair): its Hermite coefficients, centre
 // and constants do not depend on G or k12 and are written once per call by
 // k_pair_prep.  Entry layout (doubles, compact per shell pair):
-//   [0..2] P (product centre), [3] 1/(4p), [4] c_i c_j (pi/p)^{3/2},
-//   then for x, y, z: E^{ab}_t for a <= lm, b <= ln, t <= a+b, packed by
+//   [0..2] P (product centre), [3] 1/(4p), [4] c_i c_j (pi/p)^{3/2}, [5] p,
+//   [6] c_i c_j, [7] unused, then for x, y, z: E^{ab}_t for a <= lm, b <= ln, t <= a+b, packed by
 //   (a, b) with offset eoff(a, b) = sum of (a'+b'+1) over earlier (a', b').
 // Entries of one (pair, BvK cell) are contiguous and ordered by primitive pair.
 // ---------------------------------------------------------------------------
@@ -173,7 +173,7 @@ __global__ void k_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int 
         const double Bx = ao.cen[3 * nu + x] + d0 * a9[x] + d1 * a9[3 + x] + d2 * a9[6 + x];
         out[x] = (a * Ax + b * Bx) / p;
         pair_E_g(lm, ln, a, b, Ax, Bx, E);
-        double *o = out + 5 + x * n1;
+        double *o = out + ENT_HDR + x * n1;
         int k = 0;
         for (int ia = 0; ia <= lm; ia++)
             for (int ib = 0; ib <= ln; ib++)
@@ -181,6 +181,9 @@ __global__ void k_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int 
     }
     out[3] = 0.25 / p;
     out[4] = ao.cn[oi] * ao.cn[oj] * KPI * sqrt(KPI) / (p * sqrt(p));
+    out[5] = p;
+    out[6] = ao.cn[oi] * ao.cn[oj];
+    out[7] = 0.0;
 }
 
 int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist, const double *a9,
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft(GArgs G, DevShells ao, int 
         // f_x(a, b) = sum_t E_t (-i q_x)^t: even t real, odd t imaginary
         double fr[3][(LMAX + 1) * (LMAX + 1)], fi[3][(LMAX + 1) * (LMAX + 1)];
         for (int x = 0; x < 3; x++) {
-            const double *Ex = en + 5 + x * n1;
+            const double *Ex = en + ENT_HDR + x * n1;
             int k = 0;
             for (int a = 0; a <= lm; a++)
                 for (int b = 0; b <= ln; b++) {
@@ -299,7 +302,7 @@ __global__ void k_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *
             for (int ib = 0; ib < ncn; ib++) {
                 const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
                 double v = en[4];
-                for (int x = 0; x < 3; x++) v *= en[5 + x * n1 + eoff(ca[x], cb[x], ln)];
+                for (int x = 0; x < 3; x++) v *= en[ENT_HDR + x * n1 + eoff(ca[x], cb[x], ln)];
                 acc[ia * ncn + ib] += v;
             }
     }

@@ -18,13 +18,14 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdint>
 
 #include "k_common.cuh"
 #include "rsgdf_internal.h"
 
 namespace rsgdf {
 
-__device__ double g_boys_table[BOYS_NT * BOYS_NM];
+__device__ double g_boys_table[BOYS_NT * BOYS_ROW];
 static bool g_boys_ready[64] = {false};
 
 int upload_boys_table(const double *tab, cudaStream_t st)
@@ -32,7 +33,7 @@ int upload_boys_table(const double *tab, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RSGDF_EDEVICE;
     if (dev < 64 && g_boys_ready[dev]) return RSGDF_OK;
-    if (cudaMemcpyToSymbolAsync(g_boys_table, tab, sizeof(double) * BOYS_NT * BOYS_NM, 0,
+    if (cudaMemcpyToSymbolAsync(g_boys_table, tab, sizeof(double) * BOYS_NT * BOYS_ROW, 0,
                                 cudaMemcpyHostToDevice, st) != cudaSuccess)
         return RSGDF_EDEVICE;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSGDF_EDEVICE;
@@ -41,26 +42,46 @@ int upload_boys_table(const double *tab, cudaStream_t st)
 }
 
 // F_m(T), m = 0..L: Taylor series of F_L about the nearest tabulated point,
-// then downward recursion F_m = (2T F_{m+1} + e^{-T})/(2m+1); for T beyond the
-// table F_0 = sqrt(pi/T)/2 and the upward recursion.
+// then downward recursion F_m = (2T F_{m+1} + e^{-T})/(2m+1) with e^{-T} =
+// e^{-T_i} e^{T_i - T} (tabulated value times a short Taylor series); for T
+// beyond the table F_0 = sqrt(pi/T)/2 and the upward recursion.
 template <int L>
 __device__ __forceinline__ void boys_f64(double T, double *F)
 {
     if (T < BOYS_TMAX) {
-        int i = __double2int_rn(T * (1.0 / BOYS_H));
-        double D = i * BOYS_H - T;
-        const double *row = g_boys_table + i * BOYS_NM + L;
-        double f = row[BOYS_TAYLOR - 1];
+        const int i = __double2int_rn(T * (1.0 / BOYS_H));
+        const double D = i * BOYS_H - T;
+        // row[m*BOYS_TAYLOR + k] = F_{m+k}(T_i)/k!, row[BOYS_NM*BOYS_TAYLOR + k] = e^{-T_i}/k!
+        const double *row = g_boys_table + i * BOYS_ROW;
+        if (L <= 2) {
 #pragma unroll
-        for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D * (1.0 / (k + 1)), row[k]);
-        F[L] = f;
-        double e = exp(-T);
+            for (int m = 0; m <= L; m++) {
+                const double *c = row + m * BOYS_TAYLOR;
+                double f = c[BOYS_TAYLOR - 1];
 #pragma unroll
-        for (int m = L - 1; m >= 0; m--) F[m] = fma(2.0 * T, F[m + 1], e) * (1.0 / (2 * m + 1));
+                for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
+                F[m] = f;
+            }
+        } else {
+            const double *c = row + L * BOYS_TAYLOR;
+            double f = c[BOYS_TAYLOR - 1];
+#pragma unroll
+            for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
+            F[L] = f;
+            const double *ce = row + BOYS_NM * BOYS_TAYLOR;
+            double e = ce[BOYS_TAYLOR - 1];
+#pragma unroll
+            for (int k = BOYS_TAYLOR - 2; k >= 0; k--) e = fma(e, D, ce[k]);
+            const double T2 = 2.0 * T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; m--) F[m] = fma(T2, F[m + 1], e) * (1.0 / (2 * m + 1));
+        }
     } else {
-        double e = exp(-T);
-        double it = 1.0 / T;
-        F[0] = 0.5 * sqrt(KPI * it);
+        // e^{-T} is below 1e-43 of F_m for T >= 100 and m <= 9
+        const double e = (T < 100.0) ? exp(-T) : 0.0;
+        const double rs = rsqrt(T);
+        const double it = rs * rs;
+        F[0] = 0.5 * sqrt(KPI) * rs;
 #pragma unroll
         for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * it);
     }
@@ -72,26 +93,18 @@ __host__ __device__ constexpr int ridx(int t, int u, int v)
     return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
 }
 
-// Hermite integrals R_tuv, t+u+v <= L, of the erfc kernel, in place:
-// level n from L down to 0, totals from high to low so that every read still
-// sees level n+1.
+// Hermite integrals R_tuv, t+u+v <= L, of the erfc kernel, in place: level n
+// from L down to 0, totals from high to low so that every read still sees
+// level n+1.  sw[n] = s^{n+1/2}, fw[n] = (-2 alpha)^n (per primitive
+// combination), s = omega^2/(omega^2 + alpha).
 template <int L>
-__device__ __forceinline__ void hermite_R(double alpha, double omega2, double T, double X, double Y, double Z,
-                                          double *r)
+__device__ __forceinline__ void hermite_R(double T, double s, const double *sw, const double *fw, double X, double Y,
+                                          double Z, double *r)
 {
     double F[L + 1], Fs[L + 1];
-    double s = omega2 / (omega2 + alpha);
     boys_f64<L>(T, F);
     boys_f64<L>(s * T, Fs);
-    double g[L + 1];
-    double sp = sqrt(s), m2a = -2.0 * alpha, fac = 1.0;
-#pragma unroll
-    for (int n = 0; n <= L; n++) {
-        g[n] = fac * (F[n] - sp * Fs[n]);
-        sp *= s;
-        fac *= m2a;
-    }
-    r[0] = g[L];
+    r[0] = fw[L] * fma(-sw[L], Fs[L], F[L]);
 #pragma unroll
     for (int n = L - 1; n >= 0; n--) {
 #pragma unroll
@@ -116,69 +129,54 @@ __device__ __forceinline__ void hermite_R(double alpha, double omega2, double T,
                 }
             }
         }
-        r[0] = g[n];
+        r[0] = fw[n] * fma(-sw[n], Fs[n], F[n]);
     }
 }
 
-// Hermite expansion coefficients of the 1D product x_A^i x_B^j e^{-a xA^2 - b xB^2}:
-// E[(i*(lb+1)+j)*EMT + t], EMT = 2*LMAX+1.
-constexpr int EMT = 2 * LMAX + 1;
-constexpr int EAB_SZ = (LMAX + 1) * (LMAX + 1) * EMT;
-
-__device__ void pair_E(int la, int lb, double a, double b, double Ax, double Bx, double *E)
+// compact Hermite-coefficient layout of a pair entry: E^{ab}_t at eoff(a,b) + t
+__device__ __forceinline__ int eoff_sr(int a, int b, int ln)
 {
-    double p = a + b;
-    double Px = (a * Ax + b * Bx) / p;
-    double XPA = Px - Ax, XPB = Px - Bx, XAB = Ax - Bx;
-    double h = 0.5 / p;
-    for (int k = 0; k < EAB_SZ; k++) E[k] = 0.0;
-#define EE(i, j, t) E[((i) * (LMAX + 1) + (j)) * EMT + (t)]
-    EE(0, 0, 0) = exp(-(a * b / p) * XAB * XAB);
-    for (int i = 0; i <= la; i++)
-        for (int j = 0; j <= lb; j++) {
-            if (i == 0 && j == 0) continue;
-            for (int t = 0; t <= i + j; t++) {
-                double v;
-                if (i > 0) {
-                    v = XPA * EE(i - 1, j, t);
-                    if (t > 0) v += h * EE(i - 1, j, t - 1);
-                    if (t + 1 <= i - 1 + j) v += (t + 1) * EE(i - 1, j, t + 1);
-                } else {
-                    v = XPB * EE(i, j - 1, t);
-                    if (t > 0) v += h * EE(i, j - 1, t - 1);
-                    if (t + 1 <= i + j - 1) v += (t + 1) * EE(i, j - 1, t + 1);
-                }
-                EE(i, j, t) = v;
-            }
-        }
-#undef EE
+    int o = 0;
+    for (int x = 0; x < a; x++) o += (ln + 1) * (2 * x + ln + 2) / 2;
+    for (int y = 0; y < b; y++) o += a + y + 1;
+    return o;
 }
 
-// single-centre Gaussian x^c e^{-g x^2}: E[c*(LMAX+1) + tau]
-__device__ void single_E(int lc, double g, double *E)
-{
-    double h = 0.5 / g;
-    for (int k = 0; k < (LMAX + 1) * (LMAX + 1); k++) E[k] = 0.0;
-    E[0] = 1.0;
-    for (int c = 1; c <= lc; c++)
-        for (int t = 0; t <= c; t++) {
-            double v = 0.0;
-            if (t > 0) v += h * E[(c - 1) * (LMAX + 1) + t - 1];
-            if (t + 1 <= c - 1) v += (t + 1) * E[(c - 1) * (LMAX + 1) + t + 1];
-            E[c * (LMAX + 1) + t] = v;
-        }
-}
-
+constexpr int EAB_SZ = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 2) / 2 * 1;   // >= pair_e1(LMAX, LMAX) = 64
+constexpr int EC_SZ = (LMAX + 1) * (LMAX + 1);
 constexpr int SR_WARPS = 2;
 constexpr int SR_NT = 256;   // translations buffered per segment
+constexpr int SR_MAXCOMBO = 64;
+constexpr double SR_SKIP_ST = 70.0;   // erfc terms with s T beyond this vanish   // primitive combinations per triple (aux x AO x AO)
 
-size_t sr_warp_bytes(int L, int bc, int ncomp_max)
+// per-warp shared memory: term positions (3 doubles) and BvK cells, twice
+// (collected and sorted), bin counters, Hermite coefficients of the current
+// primitive combination, Hermite sums per cell and contracted blocks.
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max)
 {
-    size_t b = 2 * SR_NT * sizeof(int4) + 2 * (NBIN_MAX + 4) * sizeof(int);
+    size_t b = 2 * SR_NT * (3 * sizeof(double) + sizeof(int)) + 2 * (NBIN_MAX + 4) * sizeof(int);
+    b += (NC_MAX * NC_MAX + 4) * sizeof(int);                      // list offsets per (a, b)
+    b += 64 * sizeof(int);                                        // FP32 survivor queue
     b = (b + 15) & ~(size_t)15;
-    b += (3 * EAB_SZ + 3 * (LMAX + 1) * (LMAX + 1)) * sizeof(double);
-    b += (size_t)bc * (ntuv(L) + ncomp_max) * sizeof(double);
+    b += (3 * EAB_SZ + EC_SZ) * sizeof(double);
+    b += (size_t)bc * (ntuv(L) + ncomp_max + w_max) * sizeof(double);
+    b += (size_t)list_max * (sizeof(double) + sizeof(short));
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)SR_MAXCOMBO * 8 * sizeof(double);                    // per-combination constants
     return (b + 15) & ~(size_t)15;
+}
+
+// (t, u, v) of a packed index p = ridx(t, u, v)
+__device__ __forceinline__ void tuv_of(int p, int &t, int &u, int &v)
+{
+    int S = 0;
+    while ((S + 1) * (S + 2) * (S + 3) / 6 <= p) S++;
+    int q = p - S * (S + 1) * (S + 2) / 6;
+    int w = 0;
+    while ((w + 1) * (w + 2) / 2 <= q) w++;
+    v = q - w * (w + 1) / 2;
+    u = w - v;
+    t = S - w;
 }
 
 template <int L>
@@ -188,186 +186,306 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = A.item_begin + (long long)blockIdx.x * SR_WARPS + warp;
     if (item >= A.item_end) return;  // warp-uniform
-    unsigned char *base = smem_raw + (size_t)warp * A.warp_bytes;
-    int4 *Tl = (int4 *)base;
-    int4 *Ts = Tl + SR_NT;
-    int *cnt = (int *)(Ts + SR_NT);
-    int *fill = cnt + NBIN_MAX + 4;
-    double *Eab = (double *)(base + (((2 * SR_NT * sizeof(int4) + 2 * (NBIN_MAX + 4) * sizeof(int)) + 15) & ~(size_t)15));
-    double *Ec = Eab + 3 * EAB_SZ;
-    double *Rb = Ec + 3 * (LMAX + 1) * (LMAX + 1);
-    double *O = Rb + A.bc * ntuv(L);
     constexpr int NR = ntuv(L);
+    unsigned char *base = smem_raw + (size_t)warp * A.warp_bytes;
+    double *Tx = (double *)base;            // collected translations (Cartesian)
+    double *Ty = Tx + SR_NT, *Tz = Ty + SR_NT;
+    double *Sx = Tz + SR_NT, *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
+    int *Tb = (int *)(Sz + SR_NT);
+    int *Sb = Tb + SR_NT;
+    int *cnt = Sb + SR_NT;
+    int *fill = cnt + NBIN_MAX + 4;
+    int *loff = fill + NBIN_MAX + 4;
+    int *Qd = loff + NC_MAX * NC_MAX + 4;
+    double *Eab = (double *)(base + ((2 * SR_NT * (3 * sizeof(double) + sizeof(int)) + 2 * (NBIN_MAX + 4) * sizeof(int) +
+                                      (NC_MAX * NC_MAX + 4) * sizeof(int) + 64 * sizeof(int) + 15) &
+                                     ~(size_t)15));
+    double *Ec = Eab + 3 * EAB_SZ;
+    double *Rb = Ec + EC_SZ;
+    double *O = Rb + A.bc * NR;
+    double *Wb = O + A.bc * A.ncomp_max;
+    double *Lc = Wb + A.bc * A.w_max;
+    short *Li = (short *)(Lc + A.list_max);
+    double *Kc = (double *)(((uintptr_t)(Li + A.list_max) + 15) & ~(uintptr_t)15);   // [combo][8]
 
     // the triple of this item: last triple with item_off <= item
     int lo = A.tri_begin, hi = A.tri_end - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (A.tri[mid].item_off <= item) lo = mid; else hi = mid - 1;
     }
     const SRTripleDev tr = A.tri[lo];
-    const int di = (int)(item - tr.item_off);
+    const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);   // global d index
     const int P = tr.P, mu = tr.mu, nu = tr.nu;
     const int lP = A.ax.l[P], lm = A.ao.l[mu], ln = A.ao.l[nu];
     const int ncP = (lP + 1) * (lP + 2) / 2, ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
     const int ncomp = ncP * ncm * ncn;
-    const int *dv = A.dlist + 3 * (A.pair_doff[tr.pair] + di);
-    const int d0 = dv[0], d1 = dv[1], d2 = dv[2];
-    double Av[3], Bv[3], Cv[3], xr[3];
-#pragma unroll
-    for (int x = 0; x < 3; x++) {
-        Av[x] = A.ao.cen[3 * mu + x];
-        Bv[x] = A.ao.cen[3 * nu + x] + d0 * A.a[x] + d1 * A.a[3 + x] + d2 * A.a[6 + x];
-        Cv[x] = A.ax.cen[3 * P + x];
+    const int n1 = (lm + 1) * (ln + 1) * (lm + ln + 2) / 2;
+    const int Lp = lm + ln, npt = (Lp + 1) * (Lp + 2) * (Lp + 3) / 6;
+    if (lane == 0) {
+        // offsets of the pair-side coefficient lists, one list per (a, b)
+        int o = 0;
+        for (int ab = 0; ab < ncm * ncn; ab++) {
+            const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
+            loff[ab] = o;
+            o += (ca[0] + cb[0] + 1) * (ca[1] + cb[1] + 1) * (ca[2] + cb[2] + 1);
+        }
+        loff[ncm * ncn] = o;
     }
-    double R12 = sqrt((Bv[0] - Av[0]) * (Bv[0] - Av[0]) + (Bv[1] - Av[1]) * (Bv[1] - Av[1]) +
-                      (Bv[2] - Av[2]) * (Bv[2] - Av[2]));
-    const double wsum = tr.amu + tr.anu;
-#pragma unroll
-    for (int x = 0; x < 3; x++) xr[x] = (tr.amu * Av[x] + tr.anu * Bv[x]) / wsum - Cv[x];
-    int l0[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-        l0[i] = __double2int_rn(xr[0] * A.bq[3 * i] + xr[1] * A.bq[3 * i + 1] + xr[2] * A.bq[3 * i + 2]);
+    __syncwarp();
+    const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
+    const double Ax = A.ao.cen[3 * mu], Ay = A.ao.cen[3 * mu + 1], Az = A.ao.cen[3 * mu + 2];
+    const double Bx = A.ao.cen[3 * nu] + d0 * A.a[0] + d1 * A.a[3] + d2 * A.a[6];
+    const double By = A.ao.cen[3 * nu + 1] + d0 * A.a[1] + d1 * A.a[4] + d2 * A.a[7];
+    const double Bz = A.ao.cen[3 * nu + 2] + d0 * A.a[2] + d1 * A.a[5] + d2 * A.a[8];
+    const double Cx = A.ax.cen[3 * P], Cy = A.ax.cen[3 * P + 1], Cz = A.ax.cen[3 * P + 2];
+    const double R12 = sqrt((Bx - Ax) * (Bx - Ax) + (By - Ay) * (By - Ay) + (Bz - Az) * (Bz - Az));
+    const double iw = 1.0 / (tr.amu + tr.anu);
+    const double xr0 = (tr.amu * Ax + tr.anu * Bx) * iw - Cx;
+    const double xr1 = (tr.amu * Ay + tr.anu * By) * iw - Cy;
+    const double xr2 = (tr.amu * Az + tr.anu * Bz) * iw - Cz;
+    const int l00 = __double2int_rn(xr0 * A.bq[0] + xr1 * A.bq[1] + xr2 * A.bq[2]);
+    const int l01 = __double2int_rn(xr0 * A.bq[3] + xr1 * A.bq[4] + xr2 * A.bq[5]);
+    const int l02 = __double2int_rn(xr0 * A.bq[6] + xr1 * A.bq[7] + xr2 * A.bq[8]);
+    const float fx = (float)xr0, fy = (float)xr1, fz = (float)xr2;
+    const float fcut = (float)tr.Rc_cut + 1e-3f;
     const int dt = bvk_bin(d0, d1, d2, A.nk);
     const double *win = A.win + tr.win_off;
+    const double Rc2 = tr.Rc_cut * tr.Rc_cut;
     const double omega2 = A.omega * A.omega;
+
+    // constants of every primitive combination (k; i, j), one lane each:
+    // alpha, s = w^2/(w^2+alpha), sqrt(s), prefactor, product centre - C
+    const int npp = A.ao.nprim[mu] * A.ao.nprim[nu];
+    const int ncombo = A.ax.nprim[P] * npp;
+    for (int cb = lane; cb < ncombo; cb += 32) {
+        const int k = cb / npp, ij = cb - k * npp;
+        const int ok = A.ax.poff[P] + k;
+        const double g = A.ax.exps[ok];
+        const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
+        const double p = en[5];
+        const double ipg = 1.0 / (p + g);
+        const double alpha = p * g * ipg;
+        const double s = omega2 / (omega2 + alpha);
+        double *kc = Kc + 8 * cb;
+        kc[0] = alpha;
+        kc[1] = s;
+        kc[2] = sqrt(s);
+        kc[3] = 2.0 * KPI2_5 / (p * g) * sqrt(ipg) * A.ax.cn[ok] * en[6] * ((lP & 1) ? -1.0 : 1.0);
+        kc[4] = en[0] - Cx;
+        kc[5] = en[1] - Cy;
+        kc[6] = en[2] - Cz;
+        kc[7] = 0.0;
+    }
+    __syncwarp();
 
     int nT = 0;
     unsigned long long kept = 0;
+    int nq = 0;   // FP32 survivors waiting for the exact FP64 test (smem queue Qd)
     for (int b0 = 0; b0 < tr.nsph; b0 += 32) {
         const int idx = b0 + lane;
+        bool pass = false;
+        if (idx < tr.nsph) {
+            const int li0 = l00 + A.sph[3 * idx], li1 = l01 + A.sph[3 * idx + 1], li2 = l02 + A.sph[3 * idx + 2];
+            // FP32 pre-filter with a margin far above its rounding error
+            const float ex = fx - (li0 * A.af[0] + li1 * A.af[3] + li2 * A.af[6]);
+            const float ey = fy - (li0 * A.af[1] + li1 * A.af[4] + li2 * A.af[7]);
+            const float ez = fz - (li0 * A.af[2] + li1 * A.af[5] + li2 * A.af[8]);
+            pass = (ex * ex + ey * ey + ez * ez <= fcut * fcut);
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, pass);
+        if (pass) Qd[nq + __popc(pm & ((1u << lane) - 1u))] = idx;
+        nq += __popc(pm);
+        __syncwarp();
+        const bool lastround = (b0 + 32 >= tr.nsph);
+        if (nq < 32 && !lastround) continue;
+        // exact FP64 test of up to 64 queued candidates, 32 at a time
+        for (int q0 = 0; q0 < nq; q0 += 32) {
+        const int qi = q0 + lane;
         bool acc = false;
         int li0 = 0, li1 = 0, li2 = 0;
-        if (idx < tr.nsph) {
-            li0 = l0[0] + A.sph[3 * idx];
-            li1 = l0[1] + A.sph[3 * idx + 1];
-            li2 = l0[2] + A.sph[3 * idx + 2];
-            double r0 = xr[0] - (li0 * A.a[0] + li1 * A.a[3] + li2 * A.a[6]);
-            double r1 = xr[1] - (li0 * A.a[1] + li1 * A.a[4] + li2 * A.a[7]);
-            double r2 = xr[2] - (li0 * A.a[2] + li1 * A.a[5] + li2 * A.a[8]);
-            double rc = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-            if (rc <= tr.Rc_cut) {
-                int w = (int)floor(rc * (1.0 / SCREEN_DR));
-                if (w >= tr.nwin) w = tr.nwin - 1;
-                acc = (R12 <= win[w]);
+        double lx = 0.0, ly = 0.0, lz = 0.0;
+        if (qi < nq) {
+            const int ci = Qd[qi];
+            li0 = l00 + A.sph[3 * ci];
+            li1 = l01 + A.sph[3 * ci + 1];
+            li2 = l02 + A.sph[3 * ci + 2];
+            {
+                lx = li0 * A.a[0] + li1 * A.a[3] + li2 * A.a[6];
+                ly = li0 * A.a[1] + li1 * A.a[4] + li2 * A.a[7];
+                lz = li0 * A.a[2] + li1 * A.a[5] + li2 * A.a[8];
+                const double r0 = xr0 - lx, r1 = xr1 - ly, r2 = xr2 - lz;
+                const double rc = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+                if (rc <= tr.Rc_cut) {
+                    int w = (int)floor(rc * (1.0 / SCREEN_DR));
+                    if (w >= tr.nwin) w = tr.nwin - 1;
+                    acc = (R12 <= win[w]);
+                }
             }
         }
+        (void)Rc2;
         const unsigned m = __ballot_sync(0xffffffffu, acc);
         if (acc) {
-            int pos = nT + __popc(m & ((1u << lane) - 1u));
-            Tl[pos] = make_int4(li0, li1, li2, bvk_bin(li0, li1, li2, A.nk));
+            const int pos = nT + __popc(m & ((1u << lane) - 1u));
+            Tx[pos] = lx;
+            Ty[pos] = ly;
+            Tz[pos] = lz;
+            Tb[pos] = bvk_bin(li0, li1, li2, A.nk);
         }
         nT += __popc(m);
-        const bool last = (b0 + 32 >= tr.nsph);
-        if (nT > SR_NT - 32 || (last && nT > 0)) {
+        }
+        nq = 0;
+        __syncwarp();
+        const bool last = lastround;
+        if (nT > SR_NT - 64 || (last && nT > 0)) {
             __syncwarp();
             kept += nT;
             // ---- stable counting sort by BvK cell of l
             for (int b = lane; b < A.Nk + 1; b += 32) { cnt[b] = 0; fill[b] = 0; }
             __syncwarp();
-            for (int t = lane; t < nT; t += 32) atomicAdd(&cnt[Tl[t].w + 1], 1);
+            for (int t = lane; t < nT; t += 32) atomicAdd(&cnt[Tb[t] + 1], 1);
             __syncwarp();
             if (lane == 0)
                 for (int b = 1; b <= A.Nk; b++) cnt[b] += cnt[b - 1];   // cnt[b] = start of bin b
             __syncwarp();
             for (int t0 = 0; t0 < nT; t0 += 32) {
                 const int t = t0 + lane;
-                const int bin = (t < nT) ? Tl[t].w : -1 - lane;
+                const int bin = (t < nT) ? Tb[t] : -1 - lane;
                 const unsigned act = __ballot_sync(0xffffffffu, t < nT);
                 const unsigned peers = __match_any_sync(0xffffffffu, bin);
                 if (t < nT) {
-                    int rank = __popc(peers & act & ((1u << lane) - 1u));
-                    Ts[cnt[bin] + fill[bin] + rank] = Tl[t];
+                    const int rank = __popc(peers & act & ((1u << lane) - 1u));
+                    const int dst = cnt[bin] + fill[bin] + rank;
+                    Sx[dst] = Tx[t];
+                    Sy[dst] = Ty[t];
+                    Sz[dst] = Tz[t];
+                    Sb[dst] = bin;
                 }
                 __syncwarp();
                 if (t < nT && (peers & act & ((1u << lane) - 1u)) == 0) fill[bin] += __popc(peers & act);
                 __syncwarp();
             }
-            // ---- bins in chunks of bc
+            // ---- BvK cells of l in chunks of bc
             for (int c0 = 0; c0 < A.Nk; c0 += A.bc) {
                 const int nb = min(A.bc, A.Nk - c0);
                 const int r0 = cnt[c0], r1 = cnt[c0 + nb];
                 if (r0 == r1) continue;
                 for (int o = lane; o < nb * ncomp; o += 32) O[o] = 0.0;
-                for (int k = 0; k < A.ax.nprim[P]; k++)
-                    for (int i = 0; i < A.ao.nprim[mu]; i++)
-                        for (int j = 0; j < A.ao.nprim[nu]; j++) {
-                            const int ok = A.ax.poff[P] + k, oi = A.ao.poff[mu] + i, oj = A.ao.poff[nu] + j;
-                            const double g = A.ax.exps[ok], ea = A.ao.exps[oi], eb = A.ao.exps[oj];
-                            if (lane < 3) pair_E(lm, ln, ea, eb, Av[lane], Bv[lane], Eab + lane * EAB_SZ);
-                            else if (lane < 6) single_E(lP, g, Ec + (lane - 3) * (LMAX + 1) * (LMAX + 1));
-                            for (int o = lane; o < nb * NR; o += 32) Rb[o] = 0.0;
-                            const double p = ea + eb;
-                            const double alpha = p * g / (p + g);
-                            double Pc[3];
+                for (int k = 0; k < A.ax.nprim[P]; k++) {
+                    const int ok = A.ax.poff[P] + k;
+                    for (int e = lane; e < EC_SZ; e += 32) Ec[e] = A.ec_tab[ok * EC_SZ + e];
+                    for (int ij = 0; ij < A.ao.nprim[mu] * A.ao.nprim[nu]; ij++) {
+                        // Hermite coefficients and constants of (d, primitive pair)
+                        const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
+                        for (int e = lane; e < 3 * n1; e += 32) Eab[e] = en[ENT_HDR + e];
+                        for (int o = lane; o < nb * NR; o += 32) Rb[o] = 0.0;
+                        const double *kc = Kc + 8 * (k * npp + ij);
+                        const double alpha = kc[0], s = kc[1];
+                        double sw[L + 1], fw[L + 1];
+                        sw[0] = kc[2];
+                        fw[0] = 1.0;
 #pragma unroll
-                            for (int x = 0; x < 3; x++) Pc[x] = (ea * Av[x] + eb * Bv[x]) / p - Cv[x];
-                            __syncwarp();
-                            // contiguous slice of the sorted translations per lane
-                            const int per = (r1 - r0 + 31) >> 5;
-                            const int ta = r0 + lane * per, tb = min(ta + per, r1);
-                            double accR[NR];
+                        for (int n = 1; n <= L; n++) {
+                            sw[n] = sw[n - 1] * s;
+                            fw[n] = fw[n - 1] * (-2.0 * alpha);
+                        }
+                        const double Px = kc[4], Py = kc[5], Pz = kc[6];
+                        __syncwarp();
+                        // contiguous slice of the sorted translations per lane
+                        const int per = (r1 - r0 + 31) >> 5;
+                        const int ta = r0 + lane * per, tb = min(ta + per, r1);
+                        double accR[NR];
 #pragma unroll
-                            for (int q = 0; q < NR; q++) accR[q] = 0.0;
-                            int cur = -1;
-                            for (int tt = ta; tt < tb; tt++) {
-                                const int4 e = Ts[tt];
-                                if (e.w != cur) {
-                                    if (cur >= 0) {
+                        for (int q = 0; q < NR; q++) accR[q] = 0.0;
+                        int cur = -1;
+                        for (int tt = ta; tt < tb; tt++) {
+                            const int bn = Sb[tt];
+                            if (bn != cur) {
+                                if (cur >= 0) {
 #pragma unroll
-                                        for (int q = 0; q < NR; q++) {
-                                            atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
-                                            accR[q] = 0.0;
-                                        }
+                                    for (int q = 0; q < NR; q++) {
+                                        atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
+                                        accR[q] = 0.0;
                                     }
-                                    cur = e.w;
                                 }
-                                const double X = Pc[0] - (e.x * A.a[0] + e.y * A.a[3] + e.z * A.a[6]);
-                                const double Y = Pc[1] - (e.x * A.a[1] + e.y * A.a[4] + e.z * A.a[7]);
-                                const double Z = Pc[2] - (e.x * A.a[2] + e.y * A.a[5] + e.z * A.a[8]);
-                                const double T = alpha * (X * X + Y * Y + Z * Z);
-                                double r[NR];
-                                hermite_R<L>(alpha, omega2, T, X, Y, Z, r);
-#pragma unroll
-                                for (int q = 0; q < NR; q++) accR[q] += r[q];
+                                cur = bn;
                             }
-                            if (cur >= 0) {
+                            const double X = Px - Sx[tt], Y = Py - Sy[tt], Z = Pz - Sz[tt];
+                            const double T = alpha * (X * X + Y * Y + Z * Z);
+                            // F_n(T) and s^{n+1/2} F_n(sT) share their power-law part; for sT >= 70
+                            // they differ by O(e^{-sT}) < 1e-30: the erfc term vanishes
+                            if (s * T >= SR_SKIP_ST) continue;
+                            double r[NR];
+                            hermite_R<L>(T, s, sw, fw, X, Y, Z, r);
 #pragma unroll
-                                for (int q = 0; q < NR; q++) atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
-                            }
-                            __syncwarp();
-                            const double pref = 2.0 * KPI2_5 / (p * g * sqrt(p + g)) * A.ax.cn[ok] * A.ao.cn[oi] *
-                                                A.ao.cn[oj] * ((lP & 1) ? -1.0 : 1.0);
-                            for (int o = lane; o < nb * ncomp; o += 32) {
-                                const int bb = o / ncomp, comp = o - bb * ncomp;
-                                const int ic = comp / (ncm * ncn), ia = (comp / ncn) % ncm, ib = comp % ncn;
-                                const signed char *cc = c_cart[lP][ic], *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
+                            for (int q = 0; q < NR; q++) accR[q] += r[q];
+                        }
+                        if (cur >= 0) {
+#pragma unroll
+                            for (int q = 0; q < NR; q++) atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
+                        }
+                        __syncwarp();
+                        const double pref = kc[3];
+                        // (A) aux side: W[bb][c][tuv] = sum E^c_tau E^c_upsilon E^c_phi R[t+tau, u+upsilon, v+phi]
+                        const double *Wsrc = Rb;
+                        int wstride = NR, cstride = 0;
+                        if (lP > 0) {
+                            for (int w = lane; w < nb * ncP * npt; w += 32) {
+                                const int bb = w / (ncP * npt), rem = w - bb * (ncP * npt);
+                                const int ic = rem / npt, pq = rem - ic * npt;
+                                int t, u, v;
+                                tuv_of(pq, t, u, v);
+                                const signed char *cc = c_cart[lP][ic];
                                 const double *rb = Rb + bb * NR;
                                 double sum = 0.0;
-                                for (int t = 0; t <= ca[0] + cb[0]; t++) {
-                                    const double ex = Eab[(ca[0] * (LMAX + 1) + cb[0]) * EMT + t];
-                                    for (int u = 0; u <= ca[1] + cb[1]; u++) {
-                                        const double exy = ex * Eab[EAB_SZ + (ca[1] * (LMAX + 1) + cb[1]) * EMT + u];
-                                        for (int v = 0; v <= ca[2] + cb[2]; v++) {
-                                            const double e = exy * Eab[2 * EAB_SZ + (ca[2] * (LMAX + 1) + cb[2]) * EMT + v];
-                                            for (int ta2 = cc[0] & 1; ta2 <= cc[0]; ta2 += 2) {
-                                                const double e1 = e * Ec[cc[0] * (LMAX + 1) + ta2];
-                                                for (int ua = cc[1] & 1; ua <= cc[1]; ua += 2) {
-                                                    const double e2 = e1 * Ec[(LMAX + 1) * (LMAX + 1) + cc[1] * (LMAX + 1) + ua];
-                                                    for (int va = cc[2] & 1; va <= cc[2]; va += 2) {
-                                                        const double e3 = e2 * Ec[2 * (LMAX + 1) * (LMAX + 1) + cc[2] * (LMAX + 1) + va];
-                                                        sum = fma(e3, rb[ridx(t + ta2, u + ua, v + va)], sum);
-                                                    }
-                                                }
-                                            }
-                                        }
+                                for (int ta2 = cc[0] & 1; ta2 <= cc[0]; ta2 += 2)
+                                    for (int ua = cc[1] & 1; ua <= cc[1]; ua += 2) {
+                                        const double e2 = Ec[cc[0] * (LMAX + 1) + ta2] * Ec[cc[1] * (LMAX + 1) + ua];
+                                        for (int va = cc[2] & 1; va <= cc[2]; va += 2)
+                                            sum = fma(e2 * Ec[cc[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
+                                    }
+                                Wb[w] = sum;
+                            }
+                            Wsrc = Wb;
+                            wstride = ncP * npt;
+                            cstride = npt;
+                        }
+                        // (B) pair side: one coefficient list E^x_t E^y_u E^z_v per (a, b)
+                        for (int ab = lane; ab < ncm * ncn; ab += 32) {
+                            const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
+                            const double *ex0 = Eab + eoff_sr(ca[0], cb[0], ln);
+                            const double *ey0 = Eab + n1 + eoff_sr(ca[1], cb[1], ln);
+                            const double *ez0 = Eab + 2 * n1 + eoff_sr(ca[2], cb[2], ln);
+                            int k = loff[ab];
+                            for (int t = 0; t <= ca[0] + cb[0]; t++)
+                                for (int u = 0; u <= ca[1] + cb[1]; u++) {
+                                    const double exy = ex0[t] * ey0[u];
+                                    for (int v = 0; v <= ca[2] + cb[2]; v++, k++) {
+                                        Lc[k] = exy * ez0[v];
+                                        Li[k] = (short)ridx(t, u, v);
                                     }
                                 }
-                                O[o] = fma(pref, sum, O[o]);
-                            }
-                            __syncwarp();
                         }
+                        __syncwarp();
+                        // outputs ordered with (a, b) slowest so that neighbouring lanes share list lengths
+                        for (int o = lane; o < nb * ncomp; o += 32) {
+                            const int ab = o / (nb * ncP), rem = o - ab * (nb * ncP);
+                            const int bb = rem / ncP, ic = rem - bb * ncP;
+                            const double *w = Wsrc + bb * wstride + ic * cstride;
+                            double s0 = 0.0, s1 = 0.0;
+                            int k = loff[ab];
+                            const int ke = loff[ab + 1];
+                            for (; k + 1 < ke; k += 2) {
+                                s0 = fma(Lc[k], w[Li[k]], s0);
+                                s1 = fma(Lc[k + 1], w[Li[k + 1]], s1);
+                            }
+                            if (k < ke) s0 = fma(Lc[k], w[Li[k]], s0);
+                            const int oo = bb * ncomp + ic * ncm * ncn + ab;
+                            O[oo] = fma(pref, s0 + s1, O[oo]);
+                        }
+                        __syncwarp();
+                    }
+                }
                 // ---- add the blocks of this chunk to X
                 const long long pf = A.ax.foff[P] - A.pfunc0, mf = A.ao.foff[mu], nf = A.ao.foff[nu];
                 for (int o = lane; o < nb * ncomp; o += 32) {
@@ -385,6 +503,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
     if (lane == 0 && A.term_count) {
         atomicAdd(A.term_count + L, kept);
         atomicAdd(A.term_count + LTOT_MAX + 1, kept * (unsigned long long)ncomp);
+        atomicAdd(A.term_count + LTOT_MAX + 2 + L, kept * (unsigned long long)ncombo);
     }
 }
 
@@ -392,14 +511,17 @@ typedef void (*SRKern)(SRArgs);
 static SRKern sr_kernels[LTOT_MAX + 1] = {k_sr3c<0>, k_sr3c<1>, k_sr3c<2>, k_sr3c<3>, k_sr3c<4>,
                                           k_sr3c<5>, k_sr3c<6>, k_sr3c<7>, k_sr3c<8>, k_sr3c<9>};
 
-int launch_sr(int L, SRArgs args, int ncomp_max, cudaStream_t st)
+int launch_sr(int L, SRArgs args, int ncomp_max, int w_max, int list_max, cudaStream_t st)
 {
     long long n = args.item_end - args.item_begin;
     if (n <= 0) return RSGDF_OK;
-    int bc = 3072 / (ntuv(L) + ncomp_max);
+    int bc = 4096 / (ntuv(L) + ncomp_max + w_max);
     bc = bc < 1 ? 1 : (bc > 16 ? 16 : bc);
     args.bc = bc;
-    size_t wb = sr_warp_bytes(L, bc, ncomp_max);
+    args.ncomp_max = ncomp_max;
+    args.w_max = w_max;
+    args.list_max = list_max;
+    size_t wb = sr_warp_bytes(L, bc, ncomp_max, w_max, list_max);
     args.warp_bytes = (int)wb;
     size_t smem = wb * SR_WARPS;
     if (cudaFuncSetAttribute(sr_kernels[L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -413,6 +535,21 @@ int launch_sr(int L, SRArgs args, int ncomp_max, cudaStream_t st)
         grid -= g;
     }
     return RSGDF_OK;
+}
+
+// single-centre Gaussian x^c e^{-g x^2}: E[c*(LMAX+1) + tau]
+__host__ __device__ void single_E(int lc, double g, double *E)
+{
+    double h = 0.5 / g;
+    for (int k = 0; k < (LMAX + 1) * (LMAX + 1); k++) E[k] = 0.0;
+    E[0] = 1.0;
+    for (int c = 1; c <= lc; c++)
+        for (int t = 0; t <= c; t++) {
+            double v = 0.0;
+            if (t > 0) v += h * E[(c - 1) * (LMAX + 1) + t - 1];
+            if (t + 1 <= c - 1) v += (t + 1) * E[(c - 1) * (LMAX + 1) + t + 1];
+            E[c * (LMAX + 1) + t] = v;
+        }
 }
 
 // ---------------------------------------------------------------------------

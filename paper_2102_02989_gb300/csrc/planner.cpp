@@ -655,35 +655,62 @@ void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int>
     pair_doff[ns * ns] = (int)(dlist.size() / 3);
 }
 
-// F_m(T) = e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) in long double
+// F_m(T) = e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) in long double,
+// stored as Taylor blocks: row i holds F_{m+k}(T_i)/k! for m < BOYS_NM and
+// k < BOYS_TAYLOR (d^k F_m/dT^k = (-1)^k F_{m+k}), then e^{-T_i}/k!.
 void boys_table(std::vector<double> &tab)
 {
-    tab.assign((size_t)BOYS_NT * BOYS_NM, 0.0);
+    tab.assign((size_t)BOYS_NT * BOYS_ROW, 0.0);
+    std::vector<long double> F(BOYS_NF);
     for (int i = 0; i < BOYS_NT; i++) {
         long double T = (long double)i * BOYS_H;
         long double eT = expl(-T);
-        for (int m = 0; m < BOYS_NM; m++) {
+        for (int m = 0; m < BOYS_NF; m++) {
             long double term = 1.0L / (2 * m + 1), sum = term;
             for (int k = 1; k < 4000; k++) {
                 term *= 2.0L * T / (2 * m + 2 * k + 1);
                 sum += term;
                 if (term < 1e-22L * sum) break;
             }
-            tab[(size_t)i * BOYS_NM + m] = (double)(eT * sum);
+            F[m] = eT * sum;
+        }
+        double *row = &tab[(size_t)i * BOYS_ROW];
+        long double fact = 1.0L;
+        for (int k = 0; k < BOYS_TAYLOR; k++) {
+            if (k > 0) fact *= k;
+            for (int m = 0; m < BOYS_NM; m++) row[m * BOYS_TAYLOR + k] = (double)(F[m + k] / fact);
+            row[BOYS_NM * BOYS_TAYLOR + k] = (double)(eT / fact);
         }
     }
 }
 
-// Algorithmic FP64 flops of one SR term with total angular momentum L, as the
-// kernel evaluates it: pair-centre distance (8), two Boys evaluations (each a
-// 8-term Taylor series at one order, the exponential counted as 20, and the
-// downward recursion at 4 per order), the erfc combination (3 per order), the
-// seeds (-2 alpha)^n G_n (2 per order), the Hermite recursion (2 flops per
-// first-index step, 2 more when the (t-1) term is present) and the
-// accumulation (1 per Hermite integral).
+// Hermite coefficients of the single-centre Gaussian x^c e^{-g x^2}:
+// E^{c+1}_t = E^c_{t-1}/(2g) + (t+1) E^c_{t+1}
+void single_E_host(int lc, double g, double *E)
+{
+    double h = 0.5 / g;
+    for (int k = 0; k < (LMAX + 1) * (LMAX + 1); k++) E[k] = 0.0;
+    E[0] = 1.0;
+    for (int c = 1; c <= lc; c++)
+        for (int t = 0; t <= c; t++) {
+            double v = 0.0;
+            if (t > 0) v += h * E[(c - 1) * (LMAX + 1) + t - 1];
+            if (t + 1 <= c - 1) v += (t + 1) * E[(c - 1) * (LMAX + 1) + t + 1];
+            E[c * (LMAX + 1) + t] = v;
+        }
+}
+
+// Algorithmic FP64 flops of one SR term (one primitive combination) with
+// total angular momentum L, as the kernel evaluates it: pair-centre distance
+// and T (8); two Boys evaluations, each either a 7-step Taylor series per
+// order (L <= 2) or one for F_L and one for e^{-T} plus a 2-flop downward step
+// per order, counting an FMA as 2; the erfc combination and its seed scaling
+// (3 per order); the Hermite recursion (2 flops per first-index step, 2 more
+// when the (t-1) term is present); the accumulation (1 per Hermite integral).
 long long sr_term_flops(int L)
 {
-    long long f = 8 + 2 * (2 * BOYS_TAYLOR + 20 + 4 * L) + 3 * (L + 1) + 2 * (L + 1);
+    long long boys = (L <= 2) ? 14LL * (L + 1) : 28LL + 4LL * L;
+    long long f = 8 + 2 * boys + 3 * (L + 1);
     for (int n = 0; n < L; n++)
         for (int s = 1; s <= L - n; s++)
             for (int t = 0; t <= s; t++)

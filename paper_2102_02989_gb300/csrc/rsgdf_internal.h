@@ -25,7 +25,10 @@ constexpr double BOYS_H = 0.1;
 constexpr int BOYS_NT = 401;
 constexpr double BOYS_TMAX = 40.0;
 constexpr int BOYS_TAYLOR = 8;
-constexpr int BOYS_NM = LTOT_MAX + BOYS_TAYLOR + 2;
+constexpr int BOYS_NM = LTOT_MAX + 1;           // orders with a Taylor block
+constexpr int BOYS_NF = LTOT_MAX + BOYS_TAYLOR + 1;   // orders tabulated
+constexpr int BOYS_ROW = (BOYS_NM + 1) * BOYS_TAYLOR;   // F_{m+k}(T_i)/k! for m < NM, then e^{-T_i}/k!
+constexpr int ENT_HDR = 8;                      // header doubles of a pair entry
 
 __host__ __device__ constexpr inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 __host__ __device__ constexpr inline int ntuv(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -81,7 +84,8 @@ void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, in
 // j2c SR plan: "AO" basis = aux + unit partner, pairs (Q, unit)
 void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double omega, double eps,
                SRPlan &plan);
-void boys_table(std::vector<double> &tab);  // [BOYS_NT][BOYS_NM]
+void boys_table(std::vector<double> &tab);  // [BOYS_NT][BOYS_ROW]
+void single_E_host(int lc, double g, double *E);   // [(LMAX+1)^2]
 // AFT pair screening: list of d per AO shell pair with some primitive pair above eps
 void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int> &pair_doff,
                 std::vector<int> &dlist);

@@ -54,14 +54,18 @@ class Stats(C.Structure):
                 ("sr_flops", C.c_longlong), ("aft_units", C.c_longlong),
                 ("lr_flops", C.c_longlong), ("omega", C.c_double), ("gmesh", C.c_int * 3),
                 ("n_launch", C.c_int), ("sr_ms", C.c_double), ("aft_ms", C.c_double),
-                ("lr_gemm_ms", C.c_double), ("phase_ms", C.c_double), ("other_ms", C.c_double)]
+                ("lr_gemm_ms", C.c_double), ("phase_ms", C.c_double), ("other_ms", C.c_double),
+                ("sr_terms_by_L", C.c_longlong * 10), ("sr_prim_terms", C.c_longlong),
+                ("sr_ms_by_L", C.c_double * 10)]
 
     def asdict(self):
         return {"sr_terms": self.sr_terms, "sr_integrals": self.sr_integrals,
                 "sr_flops": self.sr_flops, "aft_units": self.aft_units, "lr_flops": self.lr_flops,
                 "omega": self.omega, "gmesh": tuple(self.gmesh), "n_launch": self.n_launch,
                 "sr_ms": self.sr_ms, "aft_ms": self.aft_ms, "lr_gemm_ms": self.lr_gemm_ms,
-                "phase_ms": self.phase_ms, "other_ms": self.other_ms}
+                "phase_ms": self.phase_ms, "other_ms": self.other_ms,
+                "sr_terms_by_L": list(self.sr_terms_by_L), "sr_prim_terms": self.sr_prim_terms,
+                "sr_ms_by_L": list(self.sr_ms_by_L)}
 
 
 def library_path() -> str:
