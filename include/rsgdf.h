@@ -142,6 +142,32 @@ int rsgdf_j3c(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *
 int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair,
                  const int *kpairs, double *V_out, void *stream);
 
+/*
+ * rsgdf_kphase without any device allocation (no counterpart in the paper;
+ * same arguments, result and ordering as rsgdf_kphase).
+ *
+ * For callers that must not allocate device memory while they run: code that
+ * records the call into a CUDA graph, where allocation calls are not allowed
+ * during capture; applications that own all device memory through their own
+ * pool and forbid libraries from calling cudaMalloc; steady-state loops that
+ * must not risk an allocation failure half way through a step.
+ *
+ * Scratch (the phase table, the k-pair lists and the intermediate T, about
+ * 16 Nk m bytes) lives in one static device array of RSGDF_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library keeps until the process exits.  Calls
+ * whose scratch would not fit return RSGDF_EINVAL before doing anything: split
+ * m (columns of X) or the k-pair list.  Nothing in the scratch needs to start
+ * at zero (every byte used is written first).  All calls share the array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race; serialise them on one stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ */
+#define RSGDF_NOALLOC_SCRATCH_BYTES (64LL << 20)
+int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, int npair,
+                         const int *kpairs, double *V_out, void *stream);
+
 /* Statistics of the last j3c/j2c call on this thread (host values, valid
  * after the call returns): SR lattice terms (aux shell, AO shell pair, l, d)
  * kept by the screening, the Cartesian integrals they carry, and the omega

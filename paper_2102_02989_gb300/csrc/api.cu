@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -551,6 +552,86 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     return RSGDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free k-phase contraction.  Its scratch is one file-scope device
+// array; the host-side name of that array is only a stand-in, so the device
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t NOALLOC_BYTES = (size_t)64 << 20;   // RSGDF_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+static void *g_noalloc_addr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(void *&base)
+{
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(RSGDF_EDEVICE, "device index beyond 63");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+    return RSGDF_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int kphase_noalloc_impl(const rsgdf_cell *cell, const double *X, long long m, int npair, const int *kpairs,
+                               double *V_out, void *stream)
+{
+    t_err.clear();
+    Lattice L;
+    RC(make_lattice(cell, L, t_err));
+    if (!X || !V_out || m < 1) return fail(RSGDF_EINVAL, "X, V_out and m >= 1 are required");
+    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
+    for (int i = 0; i < 2 * npair; i++)
+        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    const int Nk = L.Nk;
+    const size_t b_ph = align256(sizeof(double) * 2 * (size_t)Nk * Nk);
+    const size_t b_pl = align256(sizeof(int) * (size_t)npair);
+    const size_t b_T = sizeof(double) * 2 * (size_t)Nk * (size_t)m;
+    const size_t need = b_ph + 2 * b_pl + b_T;
+    if (need > NOALLOC_BYTES)
+        return fail(RSGDF_EINVAL, "kphase_noalloc needs " + std::to_string(need) + " bytes of scratch, more than the " +
+                                      std::to_string(NOALLOC_BYTES) + "-byte static array: split m or the k pairs");
+    RC(check_device());
+    void *base = nullptr;
+    RC(noalloc_scratch(base));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *b = (unsigned char *)base;
+    double *dph = (double *)b;
+    int *dplist = (int *)(b + b_ph);
+    int *dpk2 = (int *)(b + b_ph + b_pl);
+    double *T = (double *)(b + b_ph + 2 * b_pl);
+    std::vector<double> ph;
+    phase_table(L, ph);
+    std::map<int, std::vector<int>> groups;
+    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
+    std::vector<int> plist, pk2, goff, gkey;
+    for (auto &kv : groups) {
+        goff.push_back((int)plist.size());
+        gkey.push_back(kv.first);
+        for (int p : kv.second) {
+            plist.push_back(p);
+            pk2.push_back(kpairs[2 * p + 1]);
+        }
+    }
+    goff.push_back((int)plist.size());
+    // pageable sources: each copy has consumed its host buffer when it returns
+    CU(cudaMemcpyAsync(dph, ph.data(), sizeof(double) * ph.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dplist, plist.data(), sizeof(int) * plist.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dpk2, pk2.data(), sizeof(int) * pk2.size(), cudaMemcpyHostToDevice, st));
+    for (size_t gi = 0; gi < gkey.size(); gi++) {
+        RC(launch_phase1(X, m, Nk, Nk, gkey[gi], dph, T, 0, st));
+        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V_out, 0, st));
+    }
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
 }  // namespace rsgdf
 
 using namespace rsgdf;
@@ -724,6 +805,12 @@ int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair
     }
     CU(cudaGetLastError());
     return RSGDF_OK;
+}
+
+int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, int npair, const int *kpairs,
+                         double *V_out, void *stream)
+{
+    return kphase_noalloc_impl(cell, X, m, npair, kpairs, V_out, stream);
 }
 
 int rsgdf_last_stats(rsgdf_stats *out)

@@ -23,7 +23,7 @@ RSGDF_FP64, RSGDF_MIXED = 0, 1
 RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
 
 # names exported by the library (every declaration of include/rsgdf.h)
-EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase",
+EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase", "rsgdf_kphase_noalloc",
            "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64")
 
 
@@ -89,6 +89,7 @@ def load():
         for n in ("rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c"):
             getattr(lib, n).argtypes = [vp, vp, vp, vp, i, vp, i, i, vp]
         lib.rsgdf_kphase.argtypes = [vp, vp, C.c_longlong, i, vp, vp, vp]
+        lib.rsgdf_kphase_noalloc.argtypes = [vp, vp, C.c_longlong, i, vp, vp, vp]
         lib.rsgdf_last_stats.argtypes = [vp]
         lib.rsgdf_params.argtypes = [vp, vp, vp, vp]
         lib.rsgdf_last_error.restype = C.c_char_p
@@ -233,6 +234,25 @@ def rsgdf_kphase(a, kmesh, X, kpairs, out=None, stream=None):
     _check(lib.rsgdf_kphase(C.byref(c), C.c_void_p(X.data_ptr()), m, len(kp),
                             kp.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
                             _stream_ptr(stream)))
+    return out
+
+
+def rsgdf_kphase_noalloc(a, kmesh, X, kpairs, out, stream=None):
+    """rsgdf_kphase without device allocation: ``out`` (complex128 cuda
+    [npair][m]) must be given; the library's scratch is a static device array
+    of RSGDF_NOALLOC_SCRATCH_BYTES shared by all calls."""
+    import torch
+    lib = load()
+    assert X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()
+    assert out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()
+    nk = int(np.prod(kmesh))
+    m = X.numel() // (nk * nk)
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    assert tuple(out.shape) == (len(kp), m)
+    c = _cell(a, kmesh)
+    _check(lib.rsgdf_kphase_noalloc(C.byref(c), C.c_void_p(X.data_ptr()), m, len(kp),
+                                    kp.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream)))
     return out
 
 
