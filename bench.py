@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kmesh", default="2,2,2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     return ap.parse_args()
 
 
@@ -178,7 +179,8 @@ def main():
     omega, gmesh = rsgdf.rsgdf_params(p.a, p.kmesh, gmesh=p.gmesh, eps_lr=p.eps_lr)
     kp = np.array([(i, j) for i in range(p.nk) for j in range(p.nk)], dtype=np.int32)
     kl = list(range(p.nk))
-    opt = dict(omega=omega, gmesh=gmesh, eps_screen=p.eps_sr, eps_lr=p.eps_lr)
+    opt = dict(omega=omega, gmesh=gmesh, eps_screen=p.eps_sr, eps_lr=p.eps_lr,
+               precision=rsgdf.RSGDF_MIXED if args.precision == "mixed" else rsgdf.RSGDF_FP64)
     V = torch.zeros((len(kp), p.aux.nfunc, p.ao.nfunc, p.ao.nfunc), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -261,7 +263,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(p, omega, gmesh),
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+tf32x3/f32",
+        "data": "synthetic", "config": dict(describe(p, omega, gmesh), precision=args.precision),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_max / args.steps},
         "gpu_launches": int(sum(s2["n_launch"] + s3["n_launch"] for s2, s3 in stats)),

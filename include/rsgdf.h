@@ -194,6 +194,12 @@ typedef struct {
 
 int rsgdf_last_stats(rsgdf_stats *out);
 
+/* Synchronise a stream and report device-detected failures of the calls
+ * enqueued on it: RSGDF_ETIMEOUT when a bounded device wait (tensor-core
+ * completion barrier) gave up, in which case those results are invalid;
+ * RSGDF_OK otherwise.  Clears the flag. */
+int rsgdf_sync_status(void *stream);
+
 /* Range-separation parameter and G box implied by opts (host only). */
 int rsgdf_params(const rsgdf_cell *cell, const rsgdf_opts *opts, double *omega_out, int *gmesh_out);
 

@@ -226,7 +226,6 @@ static int check_opts(const rsgdf_opts *o)
     if (!o) return fail(RSGDF_EINVAL, "opts is NULL");
     if (!(o->eps_screen > 0.0 && o->eps_screen < 1.0)) return fail(RSGDF_EINVAL, "eps_screen must be in (0, 1)");
     if (o->precision != RSGDF_FP64 && o->precision != RSGDF_MIXED) return fail(RSGDF_EINVAL, "unknown precision mode");
-    if (o->precision == RSGDF_MIXED) return fail(RSGDF_ENOTIMPL, "mixed precision path not built in this library");
     if (o->screening != RSGDF_SCREEN_BOUND && o->screening != RSGDF_SCREEN_LEARNED)
         return fail(RSGDF_EINVAL, "unknown screening mode");
     if (o->screening == RSGDF_SCREEN_LEARNED) return fail(RSGDF_ENOTIMPL, "learned screening not built in this library");
@@ -286,7 +285,7 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     double *da9;
     RC(S.upload(da9, std::vector<double>(a9h, a9h + 9)));
     t_timer.begin(PH_SR);
-    RC(launch_pair_prep(ao, hao.nshell, dent, (int)ent.size(), dl, da9, ptab, st));
+    RC(launch_pair_prep(ao, hao.nshell, dent, (int)ent.size(), dl, da9, ptab, nullptr, nullptr, nullptr, st));
     t_timer.end();
     nlaunch++;
     // single-centre Hermite coefficients of every aux primitive
@@ -465,8 +464,21 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     RC(S.upload(dseg, seg));
     RC(S.upload(dalist, alist));
     RC(S.alloc(ptab, (size_t)tab_len));
+    float *ptab32 = nullptr;
+    float2 *uph = nullptr, *ph0 = nullptr;
+    double *db9 = nullptr;
+    const bool mixed_aft = (opts->precision == RSGDF_MIXED) && (mode & MODE_LR);
+    if (mixed_aft) {
+        std::vector<double> b9v(9);
+        for (int i = 0; i < 3; i++)
+            for (int x = 0; x < 3; x++) b9v[3 * i + x] = L.b[i][x];
+        RC(S.upload(db9, b9v));
+        RC(S.alloc(ptab32, (size_t)tab_len));
+        RC(S.alloc(uph, 3 * ent.size()));
+        RC(S.alloc(ph0, ent.size()));
+    }
     t_timer.begin(PH_AFT);
-    RC(launch_pair_prep(dao, ao.nshell, dent, (int)ent.size(), dalist, da9, ptab, st));
+    RC(launch_pair_prep(dao, ao.nshell, dent, (int)ent.size(), dalist, da9, ptab, ptab32, db9, uph, st));
     t_timer.end();
     nlaunch++;
     double *SP = nullptr, *Sf = nullptr;
@@ -492,46 +504,71 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         RC(S.alloc(W, (size_t)2 * NG * nP));
         RC(S.alloc(Y, (size_t)2 * Nk * NG * nao * nao));
     }
+    // k12 groups in batches whose T fits a fixed budget
+    const int G = (int)gkey.size();
+    const long long tbytes = (long long)Nk * m * 16;
+    int B = (int)std::max(1LL, std::min<long long>(G, (4LL << 30) / std::max(tbytes, 1LL)));
     double *T;
-    RC(S.alloc(T, (size_t)2 * Nk * m));
+    RC(S.alloc(T, (size_t)2 * B * Nk * m));
+    int *dk12, *dgoff;
+    RC(S.upload(dk12, gkey));
+    RC(S.upload(dgoff, goff));
+    const int fp32 = (opts->precision == RSGDF_MIXED) ? 1 : 0;
+    const void *phk = dph;
+    if (fp32) {
+        std::vector<float> ph32(ph.begin(), ph.end());
+        float *dph32;
+        RC(S.upload(dph32, ph32));
+        phk = dph32;
+    }
     long long aft_units = 0;
-    for (size_t gi = 0; gi < gkey.size(); gi++) {
-        const int k12 = gkey[gi];
-        bool have = false;
+    for (int gb0 = 0; gb0 < G; gb0 += B) {
+        const int nb = std::min(B, G - gb0);
         if (mode & MODE_SR) {
             t_timer.begin(PH_PHASE);
-            RC(launch_phase1(X, m, Nk, Nk, k12, dph, T, 0, st));
+            RC(launch_phase1_multi(X, m, Nk, dk12 + gb0, nb, phk, T, fp32, st));
             nlaunch++;
-            have = true;
-            if (k12 == 0) {
-                RC(launch_g0_fold(T, m, Nk, nP, nao, SP, Sf, g0fac, st));
-                nlaunch++;
-            }
+            for (int j = 0; j < nb; j++)
+                if (gkey[gb0 + j] == 0) {
+                    RC(launch_g0_fold(T + (size_t)2 * j * Nk * m, m, Nk, nP, nao, SP, Sf, g0fac, st));
+                    nlaunch++;
+                }
             t_timer.end();
+        } else {
+            CU(cudaMemsetAsync(T, 0, sizeof(double) * 2 * nb * Nk * m, st));
         }
         if (mode & MODE_LR) {
-            if (!have) CU(cudaMemsetAsync(T, 0, sizeof(double) * 2 * Nk * m, st));
-            GArgs G;
-            memset(&G, 0, sizeof(G));
-            G.g = dg;
-            G.NG = NG;
-            for (int i = 0; i < 3; i++)
-                for (int x = 0; x < 3; x++) G.b[3 * i + x] = L.b[i][x];
-            k12_frac(L, k12, G.f12);
-            G.vol = L.vol;
-            G.omega = omega;
-            t_timer.begin(PH_AFT);
-            RC(launch_aux_ft(G, dax, s0, s1, pfunc0, nP, W, nullptr, st));
-            RC(launch_aft(G, dao, ao.nshell, nao, dent, dseg, ptab, Nk, Y, st));
-            t_timer.end();
-            t_timer.begin(PH_GEMM);
-            RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, T, 2 * m, st));
-            t_timer.end();
-            nlaunch += 3;
+            for (int j = 0; j < nb; j++) {
+                const int k12 = gkey[gb0 + j];
+                double *Tj = T + (size_t)2 * j * Nk * m;
+                GArgs Ga;
+                memset(&Ga, 0, sizeof(Ga));
+                Ga.g = dg;
+                Ga.NG = NG;
+                for (int i = 0; i < 3; i++)
+                    for (int x = 0; x < 3; x++) Ga.b[3 * i + x] = L.b[i][x];
+                k12_frac(L, k12, Ga.f12);
+                Ga.vol = L.vol;
+                Ga.omega = omega;
+                t_timer.begin(PH_AFT);
+                RC(launch_aux_ft(Ga, dax, s0, s1, pfunc0, nP, W, nullptr, st));
+                if (mixed_aft)
+                    RC(launch_aft_f32(Ga, dao, ao.nshell, nao, dent, (int)ent.size(), dseg, ptab, ptab32, db9, uph, ph0,
+                                      Nk, Y, st));
+                else
+                    RC(launch_aft(Ga, dao, ao.nshell, nao, dent, dseg, ptab, Nk, Y, st));
+                t_timer.end();
+                t_timer.begin(PH_GEMM);
+                if (opts->precision == RSGDF_MIXED)
+                    RC(launch_zgemm_tn_tc(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
+                else
+                    RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
+                t_timer.end();
+                nlaunch += 3;
+            }
         }
         t_timer.begin(PH_PHASE);
-        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V,
-                         (mode == MODE_LR) ? 1 : 0, st));
+        RC(launch_phase2_multi(T, m, Nk, dgoff + gb0, nb, dplist, dpk2, phk, V, (mode == MODE_LR) ? 1 : 0, fp32, st));
         t_timer.end();
         nlaunch++;
     }
@@ -837,6 +874,16 @@ int rsgdf_last_stats(rsgdf_stats *out)
         t_stats.other_ms = ms[PH_OTHER];
     }
     *out = t_stats;
+    return RSGDF_OK;
+}
+
+int rsgdf_sync_status(void *stream)
+{
+    t_err.clear();
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return fail(RSGDF_EDEVICE, "stream sync failed");
+    int flag = 0;
+    RC(tc_status_take(&flag));
+    if (flag) return fail(RSGDF_ETIMEOUT, "a bounded device wait gave up; results of that call are invalid");
     return RSGDF_OK;
 }
 

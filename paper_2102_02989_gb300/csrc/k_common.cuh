@@ -99,7 +99,10 @@ struct PairEntry {
     int pair, d, i, j;
 };
 int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist, const double *a9,
-                     double *tab, cudaStream_t st);
+                     double *tab, float *tab32, const double *b9, float2 *uph, cudaStream_t st);
+int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
+                   const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
+                   double *Y, cudaStream_t st);
 int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
                const double *tab, int Nk, double *Y, cudaStream_t st);
 int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,
@@ -115,5 +118,13 @@ int launch_phase2(const double *T, long long m, int Nk, const int *pair_list, co
                   const double *ph, double *V, int accumulate, cudaStream_t st);
 int launch_cholesky(int n, int nk, const double *J, double *Lo, int *info, cudaStream_t st);
 int launch_probe_fp64(double *out, int iters, cudaStream_t st);
+int launch_zgemm_tn_tc(int M, int N, int K, int batch, const double *A, const double *B, long long strideB, double *C,
+                       long long strideC, cudaStream_t st);
+int tc_status_take(int *flag);
+// ph: double2 table for the FP64 path, float2 table when fp32 != 0
+int launch_phase1_multi(const double *X, long long m, int Nk, const int *k12list, int nk12, const void *ph,
+                        double *T, int fp32, cudaStream_t st);
+int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,
+                        const int *pk2, const void *ph, double *V, int accumulate, int fp32, cudaStream_t st);
 
 }  // namespace rsgdf

@@ -3,6 +3,8 @@
 // Cholesky factorisation of j2c, and the FP64 throughput probe.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "k_common.cuh"
 
 namespace rsgdf {
@@ -155,7 +157,7 @@ __device__ __forceinline__ int eoff(int a, int b, int ln)
 }
 
 __global__ void k_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist,
-                            const double *a9, double *tab)
+                            const double *a9, double *tab, float *tab32, const double *b9, float2 *uph)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nent) return;
@@ -184,13 +186,26 @@ __global__ void k_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int 
     out[5] = p;
     out[6] = ao.cn[oi] * ao.cn[oj];
     out[7] = 0.0;
+    if (tab32) {
+        // FP32 copy (same offsets) for the mixed-precision transforms
+        float *o32 = tab32 + en.off;
+        for (int k = 0; k < ENT_HDR + 3 * n1; k++) o32[k] = (float)out[k];
+        // unit phasors e^{-i b_j.P}, argument reduced in FP64
+        for (int j = 0; j < 3; j++) {
+            const double ph = b9[3 * j] * out[0] + b9[3 * j + 1] * out[1] + b9[3 * j + 2] * out[2];
+            const double r = ph - 2.0 * KPI * rint(ph * (0.5 / KPI));
+            double s, c;
+            sincos(r, &s, &c);
+            uph[3 * e + j] = make_float2((float)c, (float)-s);
+        }
+    }
 }
 
 int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, const int *dlist, const double *a9,
-                     double *tab, cudaStream_t st)
+                     double *tab, float *tab32, const double *b9, float2 *uph, cudaStream_t st)
 {
     if (nent <= 0) return RSGDF_OK;
-    k_pair_prep<<<(nent + 127) / 128, 128, 0, st>>>(ao, nshell, ent, nent, dlist, a9, tab);
+    k_pair_prep<<<(nent + 127) / 128, 128, 0, st>>>(ao, nshell, ent, nent, dlist, a9, tab, tab32, b9, uph);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
@@ -280,6 +295,125 @@ int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntr
 {
     dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
     k_aft<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab, Nk, Y);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// e^{-i f12.(b.P)} per entry for one k12 (argument in FP64, reduced)
+__global__ void k_aft_phase0(const PairEntry *ent, int nent, const double *tab, double f0, double f1, double f2,
+                             const double *b9, float2 *ph0)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const double *en = tab + ent[e].off;
+    double th = 0.0;
+    const double f[3] = {f0, f1, f2};
+    for (int j = 0; j < 3; j++) th += f[j] * (b9[3 * j] * en[0] + b9[3 * j + 1] * en[1] + b9[3 * j + 2] * en[2]);
+    const double r = th - 2.0 * KPI * rint(th * (0.5 / KPI));
+    double s, c;
+    sincos(r, &s, &c);
+    ph0[e] = make_float2((float)c, (float)-s);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+// integer power z^n of a unit phasor, |n| small (conjugate for n < 0)
+__device__ __forceinline__ float2 cpowf(float2 z, int n)
+{
+    float2 r = make_float2(1.0f, 0.0f);
+    const int a = n < 0 ? -n : n;
+    for (int k = 0; k < a; k++) r = cmulf(r, z);
+    if (n < 0) r.y = -r.y;
+    return r;
+}
+
+// Mixed-precision pair transforms: FP32 arithmetic; e^{-i q.P} =
+// e^{-i f.(b.P)} prod_j (e^{-i b_j.P})^{n_j} from FP64-accurate phasors.
+__global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, int nshell, int nao,
+                                                         const PairEntry *ent, const int *seg, const float *tab32,
+                                                         const float2 *uph, const float2 *ph0, int Nk, double *Y)
+{
+    const int ig = blockIdx.x * AFT_THREADS + threadIdx.x;
+    const int dt = blockIdx.y, pr = blockIdx.z;
+    if (ig >= G.NG) return;
+    const int mu = pr / nshell, nu = pr % nshell;
+    const int lm = ao.l[mu], ln = ao.l[nu];
+    const int ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
+    const int n1 = pair_e1(lm, ln);
+    const int gn[3] = {G.g[3 * ig], G.g[3 * ig + 1], G.g[3 * ig + 2]};
+    float q[3];
+    for (int x = 0; x < 3; x++)
+        q[x] = (float)((gn[0] + G.f12[0]) * G.b[x] + (gn[1] + G.f12[1]) * G.b[3 + x] + (gn[2] + G.f12[2]) * G.b[6 + x]);
+    const float q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    float qp[3][EMT];
+    for (int x = 0; x < 3; x++) {
+        qp[x][0] = 1.0f;
+        for (int t = 1; t <= lm + ln; t++) qp[x][t] = qp[x][t - 1] * q[x];
+    }
+    float accr[NC_MAX * NC_MAX], acci[NC_MAX * NC_MAX];
+    for (int z = 0; z < ncm * ncn; z++) { accr[z] = 0.0f; acci[z] = 0.0f; }
+    float last_inv4p = -1.0f, gauss = 0.0f;
+    const int e0 = seg[pr * Nk + dt], e1 = seg[pr * Nk + dt + 1];
+    for (int e = e0; e < e1; e++) {
+        const float *en = tab32 + ent[e].off;
+        const float inv4p = en[3];
+        if (inv4p != last_inv4p) {
+            gauss = expf(-q2 * inv4p);
+            last_inv4p = inv4p;
+        }
+        float2 ph = ph0[e];
+        ph = cmulf(ph, cpowf(uph[3 * e], gn[0]));
+        ph = cmulf(ph, cpowf(uph[3 * e + 1], gn[1]));
+        ph = cmulf(ph, cpowf(uph[3 * e + 2], gn[2]));
+        const float base = en[4] * gauss;
+        const float br = base * ph.x, bi = base * ph.y;
+        float fr[3][(LMAX + 1) * (LMAX + 1)], fi[3][(LMAX + 1) * (LMAX + 1)];
+        for (int x = 0; x < 3; x++) {
+            const float *Ex = en + ENT_HDR + x * n1;
+            int k = 0;
+            for (int a = 0; a <= lm; a++)
+                for (int b = 0; b <= ln; b++) {
+                    float re = 0.0f, im = 0.0f;
+                    for (int t = 0; t <= a + b; t++, k++) {
+                        const float v = Ex[k] * qp[x][t];
+                        switch (t & 3) {
+                        case 0: re += v; break;
+                        case 1: im -= v; break;
+                        case 2: re -= v; break;
+                        default: im += v; break;
+                        }
+                    }
+                    fr[x][a * (LMAX + 1) + b] = re;
+                    fi[x][a * (LMAX + 1) + b] = im;
+                }
+        }
+        for (int ia = 0; ia < ncm; ia++)
+            for (int ib = 0; ib < ncn; ib++) {
+                const signed char *ca = c_cart[lm][ia], *cb = c_cart[ln][ib];
+                const int i0 = ca[0] * (LMAX + 1) + cb[0], i1 = ca[1] * (LMAX + 1) + cb[1], i2 = ca[2] * (LMAX + 1) + cb[2];
+                const float xr = fr[0][i0] * fr[1][i1] - fi[0][i0] * fi[1][i1];
+                const float xi = fr[0][i0] * fi[1][i1] + fi[0][i0] * fr[1][i1];
+                const float yr = xr * fr[2][i2] - xi * fi[2][i2];
+                const float yi = xr * fi[2][i2] + xi * fr[2][i2];
+                accr[ia * ncn + ib] += yr * br - yi * bi;
+                acci[ia * ncn + ib] += yr * bi + yi * br;
+            }
+    }
+    const int mf = ao.foff[mu], nf = ao.foff[nu];
+    for (int ia = 0; ia < ncm; ia++)
+        for (int ib = 0; ib < ncn; ib++) {
+            long long o = (((long long)dt * G.NG + ig) * nao + mf + ia) * nao + nf + ib;
+            Y[2 * o] = (double)accr[ia * ncn + ib];
+            Y[2 * o + 1] = (double)acci[ia * ncn + ib];
+        }
+}
+
+int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
+                   const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
+                   double *Y, cudaStream_t st)
+{
+    k_aft_phase0<<<(nent + 127) / 128, 128, 0, st>>>(ent, nent, tab, G.f12[0], G.f12[1], G.f12[2], b9, ph0);
+    dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
+    k_aft_f32<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab32, uph, ph0, Nk, Y);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
@@ -578,6 +712,132 @@ int launch_probe_fp64(double *out, int iters, cudaStream_t st)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_probe_fp64<<<nsm * 8, 256, 0, st>>>(out, iters, 0.999999, 1e-7);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+}  // namespace rsgdf
+
+namespace rsgdf {
+
+// ---------------------------------------------------------------------------
+// Bloch-phase contractions for a batch of k12 values (Eq. BvK_latsum_LR):
+//   T[j][dt][i] = sum_lt e^{-i k12_j.lt} X[lt][dt][i]        (phase1)
+//   V[pair][i]  = sum_dt e^{+i k2.dt} T[j(pair)][dt][i]        (phase2)
+// Register-blocked over PH_KB k12 values (phase1) and PH_PB pairs (phase2) so
+// X and T are read a few times only.  R = double (FP64 path) or float
+// (mixed path: FP32 arithmetic, FP64 storage).
+// ---------------------------------------------------------------------------
+template <typename R> struct PhT;
+template <> struct PhT<double> { typedef double2 type; enum { KB = 8, PB = 8 }; };
+template <> struct PhT<float> { typedef float2 type; enum { KB = 16, PB = 16 }; };
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__ X, long long m, int Nk,
+                                                      const int *__restrict__ k12list, int nk12,
+                                                      const typename PhT<R>::type *__restrict__ ph,
+                                                      double2 *__restrict__ T)
+{
+    const long long n = (long long)Nk * m;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+        const int dt = (int)(id / m);
+        const long long i = id - (long long)dt * m;
+        constexpr int KB = PhT<R>::KB;
+        for (int j0 = 0; j0 < nk12; j0 += KB) {
+            R ar[KB], ai[KB];
+#pragma unroll
+            for (int j = 0; j < KB; j++) { ar[j] = 0; ai[j] = 0; }
+            for (int lt = 0; lt < Nk; lt++) {
+                const R x = (R)X[((long long)lt * Nk + dt) * m + i];
+#pragma unroll
+                for (int j = 0; j < KB; j++) {
+                    if (j0 + j < nk12) {
+                        const auto p = __ldg(&ph[(long long)k12list[j0 + j] * Nk + lt]);
+                        ar[j] += p.x * x;
+                        ai[j] -= p.y * x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KB; j++)
+                if (j0 + j < nk12) T[((long long)(j0 + j) * Nk + dt) * m + i] = make_double2((double)ar[j], (double)ai[j]);
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_phase2_multi(const double2 *__restrict__ T, long long m, int Nk,
+                                                      const int *__restrict__ goff, int ngroups,
+                                                      const int *__restrict__ plist, const int *__restrict__ pk2,
+                                                      const typename PhT<R>::type *__restrict__ ph,
+                                                      double2 *__restrict__ V, int accumulate)
+{
+    const int g = blockIdx.y;
+    const int p0 = goff[g], p1 = goff[g + 1];
+    const double2 *Tg = T + (long long)g * Nk * m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        constexpr int PB = PhT<R>::PB;
+        for (int q0 = p0; q0 < p1; q0 += PB) {
+            R ar[PB], ai[PB];
+#pragma unroll
+            for (int j = 0; j < PB; j++) { ar[j] = 0; ai[j] = 0; }
+            for (int dt = 0; dt < Nk; dt++) {
+                const double2 t = Tg[(long long)dt * m + i];
+                const R tr = (R)t.x, ti = (R)t.y;
+#pragma unroll
+                for (int j = 0; j < PB; j++) {
+                    if (q0 + j < p1) {
+                        const auto p = __ldg(&ph[(long long)pk2[q0 + j] * Nk + dt]);
+                        ar[j] += p.x * tr - p.y * ti;
+                        ai[j] += p.x * ti + p.y * tr;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PB; j++) {
+                if (q0 + j < p1) {
+                    const long long o = (long long)plist[q0 + j] * m + i;
+                    if (accumulate) {
+                        double2 v = V[o];
+                        v.x += (double)ar[j];
+                        v.y += (double)ai[j];
+                        V[o] = v;
+                    } else {
+                        V[o] = make_double2((double)ar[j], (double)ai[j]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+static int grid_for(long long n)
+{
+    long long g = (n + 255) / 256;
+    if (g > 152LL * 64) g = 152LL * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int launch_phase1_multi(const double *X, long long m, int Nk, const int *k12list, int nk12, const void *ph,
+                        double *T, int fp32, cudaStream_t st)
+{
+    const long long n = (long long)Nk * m;
+    if (fp32)
+        k_phase1_multi<float><<<grid_for(n), 256, 0, st>>>(X, m, Nk, k12list, nk12, (const float2 *)ph, (double2 *)T);
+    else
+        k_phase1_multi<double><<<grid_for(n), 256, 0, st>>>(X, m, Nk, k12list, nk12, (const double2 *)ph, (double2 *)T);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,
+                        const int *pk2, const void *ph, double *V, int accumulate, int fp32, cudaStream_t st)
+{
+    dim3 grid((unsigned)std::min<long long>((m + 255) / 256, 4096), ngroups);
+    if (fp32)
+        k_phase2_multi<float><<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, goff, ngroups, plist, pk2,
+                                                   (const float2 *)ph, (double2 *)V, accumulate);
+    else
+        k_phase2_multi<double><<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, goff, ngroups, plist, pk2,
+                                                    (const double2 *)ph, (double2 *)V, accumulate);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

@@ -1,0 +1,247 @@
+// Split-precision complex GEMM on the 5th-generation tensor cores (tcgen05,
+// kind::tf32, FP32 accumulators in tensor memory) for the mixed-precision LR
+// contraction (Eq. VPmunu_LR):
+//   C[b][m][n] += sum_k A[k][m] B[b][k][n]        (complex FP64 in and out)
+//
+// Complex arithmetic is embedded in one real GEMM: rows 0..63 of the 128-row
+// tile give Re C, rows 64..127 give Im C, and K is doubled by interleaving the
+// real and imaginary parts of every k:
+//   Re C = sum_k [ Re A, -Im A ] . [ Re B, Im B ],  Im C = sum_k [ Im A, Re A ] . [ Re B, Im B ].
+// Every operand value x (rounded to FP32) is split into TF32 parts hi + lo and
+// each K-step issues hi*hi + hi*lo + lo*hi into the same accumulator (the
+// "3xTF32" scheme: about 22 significant bits per product).  Each 16-complex-k
+// chunk is summed in tensor memory, read back with tcgen05.ld and added to a
+// compensated FP32 pair (TwoSum) per output, so the FP32 rounding of the long
+// K sum does not accumulate.  Operands are staged through registers (the FP64
+// to hi/lo conversion happens there) into shared memory in the canonical
+// no-swizzle K-major layout: core matrices of 8 rows x 16 bytes.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "k_common.cuh"
+
+namespace rsgdf {
+
+constexpr int TC_M = 64;         // complex rows of C per CTA (128 real rows)
+constexpr int TC_N = 64;         // columns of C per CTA
+constexpr int TC_KC = 16;        // complex k per chunk (32 real k = 4 MMAs of K = 8)
+constexpr int TC_KR = 2 * TC_KC;
+constexpr int TC_THREADS = 128;
+constexpr long long TC_SPIN = 1LL << 26;   // bounded mbarrier wait
+
+__device__ int g_tc_status;      // set to 1 when a bounded wait gives up
+
+__device__ __forceinline__ uint32_t core_off(int r, int k)
+{
+    // element (row r, k) of a K-major tile with TC_KR columns
+    return (uint32_t)(((r >> 3) * (TC_KR / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    const uint32_t lbo = 128;                  // next core matrix along K
+    const uint32_t sbo = (TC_KR / 4) * 128;    // next 8-row group
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                    // descriptor version of this architecture
+    return d;                                  // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ uint32_t instr_desc_tf32(int m, int n)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;                    // accumulator FP32
+    d |= 2u << 7;                    // A TF32
+    d |= 2u << 10;                   // B TF32
+    d |= (uint32_t)(n >> 3) << 17;   // both operands K-major
+    d |= (uint32_t)(m >> 4) << 24;
+    return d;
+}
+
+__device__ __forceinline__ void split_tf32(double v, float &hi, float &lo)
+{
+    const float f = (float)v;
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+    hi = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(f - hi));
+    lo = __uint_as_float(l);
+}
+
+__device__ __forceinline__ void two_sum(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_zgemm_tn_tc(int M, int N, int K, const double2 *A, const double2 *B,
+                                                             long long strideB, double2 *C, long long strideC)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sAh = smem;                                   // 128 x 32 fp32
+    unsigned char *sAl = sAh + 2 * TC_M * TC_KR * 4;
+    unsigned char *sBh = sAl + 2 * TC_M * TC_KR * 4;             // 64 x 32 fp32
+    unsigned char *sBl = sBh + TC_N * TC_KR * 4;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int b = blockIdx.z;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+    const double2 *Bb = B + b * strideB;
+    double2 *Cb = C + b * strideC;
+
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = instr_desc_tf32(2 * TC_M, TC_N);
+    const uint32_t aAh = (uint32_t)__cvta_generic_to_shared(sAh), aAl = (uint32_t)__cvta_generic_to_shared(sAl);
+    const uint32_t aBh = (uint32_t)__cvta_generic_to_shared(sBh), aBl = (uint32_t)__cvta_generic_to_shared(sBl);
+
+    float sh[TC_N], sc[TC_N];
+#pragma unroll
+    for (int j = 0; j < TC_N; j++) { sh[j] = 0.0f; sc[j] = 0.0f; }
+    bool ok = true;
+    int phase = 0;
+    for (int k0 = 0; k0 < K; k0 += TC_KC) {
+        // ---- stage A' (128 real rows) and B' (64 rows), hi and lo parts
+        for (int e = tid; e < 2 * TC_M * TC_KR; e += TC_THREADS) {
+            const int r = e / TC_KR, kr = e - r * TC_KR;
+            const int m = m0 + (r & (TC_M - 1)), k = k0 + (kr >> 1);
+            double v = 0.0;
+            if (m < M && k < K) {
+                const double2 a = A[(long long)k * M + m];
+                if (r < TC_M) v = (kr & 1) ? -a.y : a.x;   // Re row: [Re A, -Im A]
+                else v = (kr & 1) ? a.x : a.y;             // Im row: [Im A, Re A]
+            }
+            float hi, lo;
+            split_tf32(v, hi, lo);
+            *(float *)(sAh + core_off(r, kr)) = hi;
+            *(float *)(sAl + core_off(r, kr)) = lo;
+        }
+        for (int e = tid; e < TC_N * TC_KR; e += TC_THREADS) {
+            const int kr = e / TC_N, r = e - kr * TC_N;    // consecutive threads: consecutive n
+            const int n = n0 + r, k = k0 + (kr >> 1);
+            double v = 0.0;
+            if (n < N && k < K) {
+                const double2 x = Bb[(long long)k * N + n];
+                v = (kr & 1) ? x.y : x.x;
+            }
+            float hi, lo;
+            split_tf32(v, hi, lo);
+            *(float *)(sBh + core_off(r, kr)) = hi;
+            *(float *)(sBl + core_off(r, kr)) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < TC_KR / 8; ks++) {
+                const uint32_t off = ks * 256;   // two core matrices along K per MMA
+                const uint64_t dah = smem_desc(aAh + off), dal = smem_desc(aAl + off);
+                const uint64_t dbh = smem_desc(aBh + off), dbl = smem_desc(aBl + off);
+                const uint32_t acc0 = ks > 0 ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
+        }
+        // ---- wait for the chunk's MMAs (bounded)
+        {
+            uint32_t done = 0;
+            long long it = 0;
+            while (!done && it < TC_SPIN) {
+                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             "selp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(done)
+                             : "r"(mb), "r"(phase));
+                it++;
+            }
+            if (!done) ok = false;
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // ---- accumulator rows of this warp: TMEM lanes 32 warp .. 32 warp + 31
+#pragma unroll
+        for (int c0 = 0; c0 < TC_N; c0 += 8) {
+            uint32_t r[8];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 8; j++) two_sum(sh[c0 + j], sc[c0 + j], __uint_as_float(r[j]));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        // CTA-uniform decision: every thread leaves the loop together
+        const int all_ok = __syncthreads_and(ok ? 1 : 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!all_ok) {
+            ok = false;
+            break;
+        }
+    }
+    if (!ok && (tid & 31) == 0) atomicExch(&g_tc_status, 1);
+    // ---- epilogue: row r of the real tile is Re (r < 64) or Im (r >= 64) of complex row m0 + r % 64
+    const int r = warp * 32 + (tid & 31);
+    const int m = m0 + (r & (TC_M - 1));
+    if (ok && m < M) {
+        double *Cr = (double *)(Cb + (long long)m * N) + (r >= TC_M ? 1 : 0);
+#pragma unroll
+        for (int j = 0; j < TC_N; j++) {
+            const int n = n0 + j;
+            if (n < N) Cr[2LL * n] += (double)sh[j] + (double)sc[j];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+}
+
+size_t tc_smem_bytes() { return (size_t)(2 * 2 * TC_M + 2 * TC_N) * TC_KR * 4; }
+
+int launch_zgemm_tn_tc(int M, int N, int K, int batch, const double *A, const double *B, long long strideB, double *C,
+                       long long strideC, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return RSGDF_OK;
+    const size_t smem = tc_smem_bytes();
+    if (cudaFuncSetAttribute(k_zgemm_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RSGDF_EDEVICE;
+    dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, batch);
+    k_zgemm_tn_tc<<<grid, TC_THREADS, smem, st>>>(M, N, K, (const double2 *)A, (const double2 *)B, strideB / 2,
+                                                   (double2 *)C, strideC / 2);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int tc_status_take(int *flag)
+{
+    int z = 0;
+    if (cudaMemcpyFromSymbol(flag, g_tc_status, sizeof(int)) != cudaSuccess) return RSGDF_EDEVICE;
+    if (*flag && cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)) != cudaSuccess) return RSGDF_EDEVICE;
+    return RSGDF_OK;
+}
+
+}  // namespace rsgdf

@@ -24,7 +24,7 @@ RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
 
 # names exported by the library (every declaration of include/rsgdf.h)
 EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase", "rsgdf_kphase_noalloc",
-           "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64")
+           "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64", "rsgdf_sync_status")
 
 
 class RsgdfError(RuntimeError):
@@ -94,6 +94,7 @@ def load():
         lib.rsgdf_params.argtypes = [vp, vp, vp, vp]
         lib.rsgdf_last_error.restype = C.c_char_p
         lib.rsgdf_probe_fp64.argtypes = [vp, vp]
+        lib.rsgdf_sync_status.argtypes = [vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -260,6 +261,11 @@ def rsgdf_last_stats() -> dict:
     s = Stats()
     _check(load().rsgdf_last_stats(C.byref(s)))
     return s.asdict()
+
+
+def rsgdf_sync_status(stream=None) -> None:
+    """Synchronise the stream; raise RsgdfError(RSGDF_ETIMEOUT) if a bounded device wait gave up."""
+    _check(load().rsgdf_sync_status(_stream_ptr(stream)))
 
 
 def rsgdf_last_error() -> str:

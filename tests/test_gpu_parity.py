@@ -145,3 +145,63 @@ def test_invalid_arguments_rejected(rs):
     assert e.value.code == rs.RSGDF_EINVAL
     with pytest.raises(rs.RsgdfError):
         rs.rsgdf_j3c(p.a, (1, 1, 1), p.ao, p.aux, [(0, 0)], omega=0.9, gmesh=(4, 5, 5))
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision path (RSGDF_MIXED): split-TF32 tensor-core LR contraction.
+# Bound: the 3xTF32 products carry ~22 significant bits and each 16-k chunk is
+# summed in FP32 before a compensated FP32 accumulation; measured 3e-7 of
+# max|V_LR| on the tiny cell (the sum over G cancels); the test bound is
+# 1e-6 x max|V_LR| absolute.
+# ---------------------------------------------------------------------------
+MIXED_REL = 1e-6
+
+
+@pytest.mark.parametrize("km", [(1, 1, 1), (2, 2, 1)])
+def test_lr_mixed_tensor_core(rs, orc, km):
+    import torch
+    p = inputs.tiny(kmesh=km, lmax_ao=2, lmax_aux=3, natm=2, seed=5)
+    nk = int(np.prod(km))
+    kp = inputs.kpairs_all(nk)
+    w = 0.9
+    gm = gmesh_for(p.a, w, 1e-14, km)
+    ref = orc.j3c(p.a, km, p.ao, p.aux, w, kp, eps_lr=1e-14, gmesh=gm, sr=False, g0=False)
+    out = torch.zeros(ref.shape, dtype=torch.complex128, device="cuda")
+    got = _np(rs.rsgdf_j3c_lr(p.a, km, p.ao, p.aux, kp, out=out, omega=w, gmesh=gm, eps_screen=1e-12, eps_lr=1e-14,
+                              precision=rs.RSGDF_MIXED))
+    rs.rsgdf_sync_status()
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got - ref))
+    assert err < MIXED_REL * scale, (err, scale)
+    assert err > 0.0   # really a different arithmetic
+
+
+def test_config2_mixed_lr_error(rs, orc):
+    p = inputs.config2()
+    w = omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)
+    kp = [(0, 0), (1, 6), (3, 2), (7, 7), (5, 0)]
+    sh = (0, 32)
+    import torch
+    ref = orc.j3c(p.a, p.kmesh, p.ao, p.aux, w, kp, eps_lr=p.eps_lr, gmesh=p.gmesh, shells=sh, sr=False, g0=False)
+    out = torch.zeros(ref.shape, dtype=torch.complex128, device="cuda")
+    got = _np(rs.rsgdf_j3c_lr(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, out=out, gmesh=p.gmesh, eps_screen=1e-8,
+                              eps_lr=p.eps_lr, precision=rs.RSGDF_MIXED))
+    rs.rsgdf_sync_status()
+    assert np.max(np.abs(got - ref)) < MIXED_REL * np.max(np.abs(ref))
+
+
+def test_config2_mixed_full_all_pairs(rs, orc):
+    """Mixed path end to end (FP64 SR lattice sums, FP32 phase contractions,
+    split-TF32 tensor-core LR) on every k pair of the 2x2x2 mesh."""
+    p = inputs.config2()
+    w = omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)
+    kp = inputs.kpairs_all(p.nk)
+    sh = (14, 16)
+    eps = 1e-11
+    ref = orc.j3c(p.a, p.kmesh, p.ao, p.aux, w, kp, eps_sr=eps, eps_lr=p.eps_lr, gmesh=p.gmesh, shells=sh)
+    got = _np(rs.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, gmesh=p.gmesh, eps_screen=eps, eps_lr=p.eps_lr,
+                           precision=rs.RSGDF_MIXED))
+    rs.rsgdf_sync_status()
+    assert np.max(np.abs(got - ref)) < MIXED_REL * np.max(np.abs(ref))
+    fp = _np(rs.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, gmesh=p.gmesh, eps_screen=eps, eps_lr=p.eps_lr))
+    assert np.max(np.abs(fp - ref)) < TOL
