@@ -499,10 +499,19 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     const int NG = (int)(gl.size() / 3);
     int *dg = nullptr;
     double *W = nullptr, *Y = nullptr;
+    float *Apl = nullptr, *Bpl = nullptr;
     if (mode & MODE_LR) {
         RC(S.upload(dg, gl));
         RC(S.alloc(W, (size_t)2 * NG * nP));
-        RC(S.alloc(Y, (size_t)2 * Nk * NG * nao * nao));
+        if (opts->precision == RSGDF_MIXED) {
+            // split-TF32 operand tiles; the padding of B' stays zero for every k12
+            RC(S.alloc(Apl, (size_t)tc_a_floats(nP, NG)));
+            const long long nb = tc_b_floats(nao * nao, NG, Nk);
+            RC(S.alloc(Bpl, (size_t)nb));
+            CU(cudaMemsetAsync(Bpl, 0, sizeof(float) * nb, st));
+        } else {
+            RC(S.alloc(Y, (size_t)2 * Nk * NG * nao * nao));
+        }
     }
     // k12 groups in batches whose T fits a fixed budget
     const int G = (int)gkey.size();
@@ -552,15 +561,17 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
                 Ga.omega = omega;
                 t_timer.begin(PH_AFT);
                 RC(launch_aux_ft(Ga, dax, s0, s1, pfunc0, nP, W, nullptr, st));
-                if (mixed_aft)
+                if (mixed_aft) {
+                    RC(launch_split_a(nP, NG, W, Apl, st));
                     RC(launch_aft_f32(Ga, dao, ao.nshell, nao, dent, (int)ent.size(), dseg, ptab, ptab32, db9, uph, ph0,
-                                      Nk, Y, st));
-                else
+                                      Nk, Bpl, st));
+                } else {
                     RC(launch_aft(Ga, dao, ao.nshell, nao, dent, dseg, ptab, Nk, Y, st));
+                }
                 t_timer.end();
                 t_timer.begin(PH_GEMM);
-                if (opts->precision == RSGDF_MIXED)
-                    RC(launch_zgemm_tn_tc(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
+                if (mixed_aft)
+                    RC(launch_zgemm_tc2(nP, nao * nao, NG, Nk, Apl, Bpl, Tj, 2 * m, st));
                 else
                     RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
                 t_timer.end();

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "rsgdf_internal.h"
 
 namespace rsgdf {
@@ -102,7 +104,7 @@ int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, c
                      double *tab, float *tab32, const double *b9, float2 *uph, cudaStream_t st);
 int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
                    const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
-                   double *Y, cudaStream_t st);
+                   float *Bp, cudaStream_t st);
 int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
                const double *tab, int Nk, double *Y, cudaStream_t st);
 int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,
@@ -120,6 +122,52 @@ int launch_cholesky(int n, int nk, const double *J, double *Lo, int *info, cudaS
 int launch_probe_fp64(double *out, int iters, cudaStream_t st);
 int launch_zgemm_tn_tc(int M, int N, int K, int batch, const double *A, const double *B, long long strideB, double *C,
                        long long strideC, cudaStream_t st);
+
+// Tensor-core tiles of the mixed-precision LR contraction (k_tc.cu): 64
+// complex rows (128 real rows) x 64 columns per CTA, 16 complex k per chunk;
+// operands split into TF32 hi/lo parts in the no-swizzle K-major core-matrix
+// layout (8 rows x 16 bytes per core matrix).
+constexpr int TC_M = 64;
+constexpr int TC_N = 64;
+constexpr int TC_KC = 16;
+constexpr int TC_KR = 2 * TC_KC;
+constexpr int TC_ABLK = 2 * 2 * TC_M * TC_KR;   // floats per A' block (hi, lo)
+constexpr int TC_BBLK = 2 * TC_N * TC_KR;       // floats per B' block (hi, lo)
+
+__device__ __forceinline__ uint32_t core_off(int r, int k)
+{
+    return (uint32_t)(((r >> 3) * (TC_KR / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void split_tf32f(float f, float &hi, float &lo)
+{
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+    hi = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(f - hi));
+    lo = __uint_as_float(l);
+}
+
+// B' element (column n, complex k, real part 0 / imaginary part 1) of batch b
+__device__ __forceinline__ void tc_put_b(float *Bp, int nnt, int nkc, int b, int n, int k, int part, float x)
+{
+    const int nt = n / TC_N, r = n - nt * TC_N;
+    const int kr2 = 2 * k + part;
+    const int kc = kr2 / TC_KR, kr = kr2 - kc * TC_KR;
+    float *blkp = Bp + (((long long)b * nnt + nt) * nkc + kc) * TC_BBLK;
+    float hi, lo;
+    split_tf32f(x, hi, lo);
+    const uint32_t o = core_off(r, kr) >> 2;
+    blkp[o] = hi;
+    blkp[TC_N * TC_KR + o] = lo;
+}
+
+int launch_split_a(int M, int K, const double *A, float *Ap, cudaStream_t st);
+int launch_zgemm_tc2(int M, int N, int K, int batch, const float *Ap, const float *Bp, double *C, long long strideC,
+                     cudaStream_t st);
+long long tc_b_floats(int N, int K, int batch);
+long long tc_a_floats(int M, int K);
 int tc_status_take(int *flag);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
 int launch_phase1_multi(const double *X, long long m, int Nk, const int *k12list, int nk12, const void *ph,

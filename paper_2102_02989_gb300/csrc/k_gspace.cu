@@ -330,7 +330,8 @@ __device__ __forceinline__ float2 cpowf(float2 z, int n)
 // e^{-i f.(b.P)} prod_j (e^{-i b_j.P})^{n_j} from FP64-accurate phasors.
 __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, int nshell, int nao,
                                                          const PairEntry *ent, const int *seg, const float *tab32,
-                                                         const float2 *uph, const float2 *ph0, int Nk, double *Y)
+                                                         const float2 *uph, const float2 *ph0, int Nk, float *Bp,
+                                                         int nnt, int nkc)
 {
     const int ig = blockIdx.x * AFT_THREADS + threadIdx.x;
     const int dt = blockIdx.y, pr = blockIdx.z;
@@ -398,22 +399,24 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, 
                 acci[ia * ncn + ib] += yr * bi + yi * br;
             }
     }
+    // written straight into the split-TF32 operand tiles of the tensor-core contraction
     const int mf = ao.foff[mu], nf = ao.foff[nu];
     for (int ia = 0; ia < ncm; ia++)
         for (int ib = 0; ib < ncn; ib++) {
-            long long o = (((long long)dt * G.NG + ig) * nao + mf + ia) * nao + nf + ib;
-            Y[2 * o] = (double)accr[ia * ncn + ib];
-            Y[2 * o + 1] = (double)acci[ia * ncn + ib];
+            const int n = (mf + ia) * nao + nf + ib;
+            tc_put_b(Bp, nnt, nkc, dt, n, ig, 0, accr[ia * ncn + ib]);
+            tc_put_b(Bp, nnt, nkc, dt, n, ig, 1, acci[ia * ncn + ib]);
         }
 }
 
 int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
                    const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
-                   double *Y, cudaStream_t st)
+                   float *Bp, cudaStream_t st)
 {
+    const int nnt = (nao * nao + TC_N - 1) / TC_N, nkc = (G.NG + TC_KC - 1) / TC_KC;
     k_aft_phase0<<<(nent + 127) / 128, 128, 0, st>>>(ent, nent, tab, G.f12[0], G.f12[1], G.f12[2], b9, ph0);
     dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
-    k_aft_f32<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab32, uph, ph0, Nk, Y);
+    k_aft_f32<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab32, uph, ph0, Nk, Bp, nnt, nkc);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

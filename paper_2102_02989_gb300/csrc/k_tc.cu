@@ -23,20 +23,11 @@
 
 namespace rsgdf {
 
-constexpr int TC_M = 64;         // complex rows of C per CTA (128 real rows)
-constexpr int TC_N = 64;         // columns of C per CTA
-constexpr int TC_KC = 16;        // complex k per chunk (32 real k = 4 MMAs of K = 8)
-constexpr int TC_KR = 2 * TC_KC;
 constexpr int TC_THREADS = 128;
 constexpr long long TC_SPIN = 1LL << 26;   // bounded mbarrier wait
 
 __device__ int g_tc_status;      // set to 1 when a bounded wait gives up
 
-__device__ __forceinline__ uint32_t core_off(int r, int k)
-{
-    // element (row r, k) of a K-major tile with TC_KR columns
-    return (uint32_t)(((r >> 3) * (TC_KR / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
@@ -242,6 +233,244 @@ int tc_status_take(int *flag)
     if (cudaMemcpyFromSymbol(flag, g_tc_status, sizeof(int)) != cudaSuccess) return RSGDF_EDEVICE;
     if (*flag && cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)) != cudaSuccess) return RSGDF_EDEVICE;
     return RSGDF_OK;
+}
+
+}  // namespace rsgdf
+
+namespace rsgdf {
+
+// ---------------------------------------------------------------------------
+// Pre-split operand tiles and the pipelined GEMM.
+//
+// A' block (m tile, k chunk): hi then lo, each 128 real rows x 32 real k in
+// the core-matrix layout above (8192 floats per block).  B' block (batch,
+// n tile, k chunk): hi then lo, each 64 rows x 32 (4096 floats per block).
+// The blocks are contiguous, so each chunk arrives by two bulk copies
+// (cp.async.bulk, completion counted on an mbarrier).
+// ---------------------------------------------------------------------------
+
+// A'[mt][kc] from A[k][m] (complex FP64): Re rows [Re A, -Im A], Im rows [Im A, Re A]
+__global__ void k_split_a(int M, int K, const double2 *A, float *Ap, int nmt, int nkc)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)nmt * nkc * 2 * TC_M * TC_KR;
+    if (id >= tot) return;
+    const int per = 2 * TC_M * TC_KR;
+    const long long blk = id / per;
+    const int e = (int)(id - blk * per);
+    const int mt = (int)(blk / nkc), kc = (int)(blk - (long long)mt * nkc);
+    const int r = e / TC_KR, kr = e - r * TC_KR;
+    const int m = mt * TC_M + (r & (TC_M - 1)), k = kc * TC_KC + (kr >> 1);
+    float v = 0.0f;
+    if (m < M && k < K) {
+        const double2 a = A[(long long)k * M + m];
+        const double d = (r < TC_M) ? ((kr & 1) ? -a.y : a.x) : ((kr & 1) ? a.x : a.y);
+        v = (float)d;
+    }
+    float hi, lo;
+    split_tf32f(v, hi, lo);
+    float *blkp = Ap + blk * TC_ABLK;
+    const uint32_t o = core_off(r, kr) >> 2;
+    blkp[o] = hi;
+    blkp[2 * TC_M * TC_KR + o] = lo;
+}
+
+int launch_split_a(int M, int K, const double *A, float *Ap, cudaStream_t st)
+{
+    const int nmt = (M + TC_M - 1) / TC_M, nkc = (K + TC_KC - 1) / TC_KC;
+    const long long tot = (long long)nmt * nkc * 2 * TC_M * TC_KR;
+    k_split_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, K, (const double2 *)A, Ap, nmt, nkc);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, int parity)
+{
+    uint32_t done = 0;
+    long long it = 0;
+    while (!done && it < TC_SPIN) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(mb), "r"(parity));
+        it++;
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+
+__device__ __forceinline__ void issue_chunk_mma(uint32_t tmem_acc, uint32_t sa, uint32_t sb, uint32_t idesc)
+{
+    const uint32_t aAh = sa, aAl = sa + 2 * TC_M * TC_KR * 4;
+    const uint32_t aBh = sb, aBl = sb + TC_N * TC_KR * 4;
+#pragma unroll
+    for (int ks = 0; ks < TC_KR / 8; ks++) {
+        const uint32_t off = ks * 256;
+        const uint64_t dah = smem_desc(aAh + off), dal = smem_desc(aAl + off);
+        const uint64_t dbh = smem_desc(aBh + off), dbl = smem_desc(aBl + off);
+        const uint32_t acc0 = ks > 0 ? 1u : 0u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_acc),
+                     "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_acc),
+                     "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_acc),
+                     "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+    }
+}
+
+// C[b][m][n] += A^T B from pre-split tiles; 2-stage bulk-copy pipeline and two
+// tensor-memory accumulators (chunk c in accumulator c & 1).
+__global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc, const float *Ap, const float *Bp,
+                                                          int nnt, double2 *C, long long strideC)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long full[2], done[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
+    const int m0 = mt * TC_M, n0 = nt * TC_N;
+    const int SB = (TC_ABLK + TC_BBLK) * 4;   // bytes per stage
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(2 * TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&done[s])), "r"(1));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = instr_desc_tf32(2 * TC_M, TC_N);
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+    const float *Ablk = Ap + (long long)mt * nkc * TC_ABLK;
+    const float *Bblk = Bp + ((long long)b * nnt + nt) * nkc * TC_BBLK;
+    auto load_chunk = [&](int c) {
+        const int s = c & 1;
+        const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(SB));
+        bulk_g2s(s0 + s * SB, Ablk + (long long)c * TC_ABLK, TC_ABLK * 4, mb);
+        bulk_g2s(s0 + s * SB + TC_ABLK * 4, Bblk + (long long)c * TC_BBLK, TC_BBLK * 4, mb);
+    };
+    float sh[TC_N], sc[TC_N];
+#pragma unroll
+    for (int j = 0; j < TC_N; j++) { sh[j] = 0.0f; sc[j] = 0.0f; }
+    bool ok = true;
+    if (tid == 0) load_chunk(0);
+    for (int c = 0; c < nkc; c++) {
+        const int s = c & 1;
+        if (tid == 0) {
+            // operands of chunk c have landed
+            if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&full[s]), (c >> 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ok) issue_chunk_mma(tmem + s * TC_N, s0 + s * SB, s0 + s * SB + TC_ABLK * 4, idesc);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                (uint32_t)__cvta_generic_to_shared(&done[s])));
+            // the other stage is free once chunk c-1's MMAs completed
+            if (c + 1 < nkc) {
+                if (c >= 1 && !mbar_wait((uint32_t)__cvta_generic_to_shared(&done[s ^ 1]), ((c - 1) >> 1) & 1)) ok = false;
+                if (ok) load_chunk(c + 1);
+            }
+        }
+        // read out chunk c-1 while chunk c runs
+        if (c >= 1) {
+            const int sp = (c - 1) & 1;
+            if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&done[sp]), ((c - 1) >> 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int c0 = 0; c0 < TC_N; c0 += 8) {
+                uint32_t r[8];
+                const uint32_t ta = tmem + sp * TC_N + ((uint32_t)(warp * 32) << 16) + c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 8; j++) two_sum(sh[c0 + j], sc[c0 + j], __uint_as_float(r[j]));
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        const int all_ok = __syncthreads_and(ok ? 1 : 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!all_ok) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok && nkc >= 1) {
+        const int sp = (nkc - 1) & 1;
+        if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&done[sp]), ((nkc - 1) >> 1) & 1)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+            for (int c0 = 0; c0 < TC_N; c0 += 8) {
+                uint32_t r[8];
+                const uint32_t ta = tmem + sp * TC_N + ((uint32_t)(warp * 32) << 16) + c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 8; j++) two_sum(sh[c0 + j], sc[c0 + j], __uint_as_float(r[j]));
+            }
+        } else {
+            ok = false;
+        }
+    }
+    if (!ok && (tid & 31) == 0) atomicExch(&g_tc_status, 1);
+    const int r = warp * 32 + (tid & 31);
+    const int m = m0 + (r & (TC_M - 1));
+    if (ok && m < M) {
+        double *Cr = (double *)(C + b * strideC + (long long)m * N) + (r >= TC_M ? 1 : 0);
+#pragma unroll
+        for (int j = 0; j < TC_N; j++) {
+            const int n = n0 + j;
+            if (n < N) Cr[2LL * n] += (double)sh[j] + (double)sc[j];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N));
+}
+
+int launch_zgemm_tc2(int M, int N, int K, int batch, const float *Ap, const float *Bp, double *C, long long strideC,
+                     cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return RSGDF_OK;
+    const int nkc = (K + TC_KC - 1) / TC_KC, nnt = (N + TC_N - 1) / TC_N, nmt = (M + TC_M - 1) / TC_M;
+    const size_t smem = 2 * (size_t)(TC_ABLK + TC_BBLK) * 4;
+    if (cudaFuncSetAttribute(k_zgemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RSGDF_EDEVICE;
+    dim3 grid(nnt, nmt, batch);
+    k_zgemm_tc2<<<grid, TC_THREADS, smem, st>>>(M, N, nkc, Ap, Bp, nnt, (double2 *)C, strideC / 2);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+long long tc_b_floats(int N, int K, int batch)
+{
+    const long long nkc = (K + TC_KC - 1) / TC_KC, nnt = (N + TC_N - 1) / TC_N;
+    return (long long)batch * nnt * nkc * TC_BBLK;
+}
+
+long long tc_a_floats(int M, int K)
+{
+    const long long nkc = (K + TC_KC - 1) / TC_KC, nmt = (M + TC_M - 1) / TC_M;
+    return nmt * nkc * TC_ABLK;
 }
 
 }  // namespace rsgdf
