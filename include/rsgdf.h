@@ -168,6 +168,63 @@ int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair
 int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, int npair,
                          const int *kpairs, double *V_out, void *stream);
 
+/*
+ * Learned screening of SR work items (no counterpart in the paper, whose
+ * screening is the Supplementary Material's estimates alone).  A work item
+ * is one (aux shell, AO shell pair, lattice vector d) of the SR double
+ * lattice sum that the estimates keep.  A 3 x 64 tanh network predicts
+ * log10 of the largest contracted block the item adds; with
+ * opts.screening = RSGDF_SCREEN_LEARNED and opts.mlp set, rsgdf_j3c /
+ * rsgdf_j3c_sr skip items whose prediction (network output, plus the base
+ * feature when one is set) plus the model's margin is below
+ * log10(eps_screen) - 1.  The estimates remain the outer filter (the network
+ * can only remove items they keep).  Parameters live on the device: FP32
+ * master copy and Adam moments, FP16 working copy; activations FP16, dot
+ * products FP32.  Features per item (RSGDF_MLP_NFEAT): lP, lmu, lnu, ln of
+ * the three most diffuse exponents, R12, the distance of the pair centre to
+ * the nearest aux image, log10 of the s-type SR integral of that nearest
+ * term summed over the primitive combinations, ln Rc_cut.
+ */
+#define RSGDF_MLP_NFEAT 10
+typedef struct rsgdf_mlp rsgdf_mlp;
+
+/* params: host float[rsgdf_mlp_nparams(nfeat)] in the packing W1 [64 x F],
+ * b1, W2 [64 x 64], b2, W3 [64 x 64], b3, w4 [64], b4 [1]; mean, stdv: host
+ * float[nfeat] input normalisation.  The handle owns device memory on the
+ * current device until rsgdf_mlp_destroy. */
+int rsgdf_mlp_nparams(int nfeat);
+int rsgdf_mlp_create(int nfeat, const float *params, const float *mean, const float *stdv, rsgdf_mlp **out);
+int rsgdf_mlp_destroy(rsgdf_mlp *m);
+int rsgdf_mlp_get_params(const rsgdf_mlp *m, float *params_out /* host */);
+/* margin >= 0 (log10 units) added to the prediction before the cut */
+int rsgdf_mlp_set_margin(rsgdf_mlp *m, float margin);
+/* Screening prediction = network output + X[feature] clamped to [lo, hi]
+ * when feature >= 0 (residual model on a physical estimate), or the network
+ * output alone when feature = -1 (the default).  Used by j3c only;
+ * rsgdf_mlp_forward returns the bare network output.  EINVAL if lo > hi. */
+int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi);
+/* y[n] = network(X[n][nfeat]) (device pointers) */
+int rsgdf_mlp_forward(const rsgdf_mlp *m, const float *X, long long n, float *y, void *stream);
+/* Expectile loss over (X, t): L = (1/n) sum_s w_s (y_s - t_s)^2 with
+ * w = 2 tau where y < t and 2 (1 - tau) elsewhere (tau = 1/2: mean squared
+ * error; tau near 1 fits an upper envelope), and its gradient w.r.t. the
+ * packed parameters, both returned to host memory (grad may be NULL);
+ * EINVAL unless 0 < tau < 1; synchronises */
+int rsgdf_mlp_loss_grad(rsgdf_mlp *m, const float *X, const float *t, long long n, float tau, float *loss_out,
+                        float *grad_out, void *stream);
+/* Adam training of that loss on device data: epochs over shuffled
+ * mini-batches of size batch; loss_out (host) = mean loss of the last epoch;
+ * synchronises */
+int rsgdf_mlp_train(rsgdf_mlp *m, const float *X, const float *t, long long n, int epochs, int batch, float lr,
+                    float tau, unsigned seed, float *loss_out, void *stream);
+
+/* SR work items of a j3c problem (the planner's order): count, features
+ * (device float[n][RSGDF_MLP_NFEAT], may be NULL) and, when mag_out is not
+ * NULL, log10 of the largest block each item adds, measured by running the
+ * FP64 SR kernels ("magnitude mode"; -30 for items that add nothing). */
+int rsgdf_sr_items(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux, const rsgdf_opts *opts,
+                   int s0, int s1, long long *n_items, float *feat_out, float *mag_out);
+
 /* Statistics of the last j3c/j2c call on this thread (host values, valid
  * after the call returns): SR lattice terms (aux shell, AO shell pair, l, d)
  * kept by the screening, the Cartesian integrals they carry, and the omega
@@ -189,6 +246,8 @@ typedef struct {
     double other_ms;         /* Cholesky, overlaps, aux charges */
     long long sr_terms_by_L[10];   /* SR terms per total angular momentum L = lP + lmu + lnu */
     long long sr_prim_terms;       /* SR terms times their primitive combinations */
+    long long sr_items;            /* SR work items kept by the estimates */
+    long long sr_items_pruned;     /* of which skipped by the learned screen */
     double sr_ms_by_L[10];         /* device time of the SR kernel of each L class */
 } rsgdf_stats;
 

@@ -8,8 +8,10 @@ hidden layers of 64 tanh units,
     h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3),
     y  = w4 . h3 + b4,
 
-fitted to log10 of SR work-item magnitudes with the mean squared error
-L = (1/n) sum_s (y_s - t_s)^2.  Parameters are packed in one vector in the
+fitted to log10 of SR work-item magnitudes with the expectile loss
+L = (1/n) sum_s w_s (y_s - t_s)^2, w_s = 2 tau where y_s < t_s and 2 (1 - tau)
+elsewhere (asymmetric least squares, Newey & Powell 1987; tau = 1/2 is the
+mean squared error, tau near 1 fits an upper envelope of the targets).  Parameters are packed in one vector in the
 order W1 [64 x F] (row-major), b1 [64], W2 [64 x 64], b2, W3 [64 x 64], b3,
 w4 [64], b4 [1] -- the same packing the CUDA kernels use.  The backward pass
 is the chain rule written out; tests pin it against central differences.
@@ -45,16 +47,17 @@ def forward(theta, X):
     return y, (h1, h2, h3)
 
 
-def loss_and_grad(theta, X, t):
-    """MSE loss and its gradient with respect to the packed parameters."""
+def loss_and_grad(theta, X, t, tau=0.5):
+    """Expectile loss and its gradient with respect to the packed parameters."""
     X = np.asarray(X, np.float64)
     t = np.asarray(t, np.float64)
     n, F = X.shape
     W1, b1, W2, b2, W3, b3, w4, b4 = unpack(np.asarray(theta, np.float64), F)
     y, (h1, h2, h3) = forward(theta, X)
     r = y - t
-    L = float(np.mean(r * r))
-    dy = 2.0 * r / n                      # dL/dy
+    w = np.where(r < 0.0, 2.0 * tau, 2.0 * (1.0 - tau))
+    L = float(np.mean(w * r * r))
+    dy = 2.0 * w * r / n                  # dL/dy
     gw4 = h3.T @ dy
     gb4 = np.array([dy.sum()])
     d3 = np.outer(dy, w4) * (1.0 - h3 * h3)
@@ -68,6 +71,20 @@ def loss_and_grad(theta, X, t):
     gb1 = d1.sum(0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3, gw4, gb4])
     return L, g
+
+
+def expectile(t, tau):
+    """The tau-expectile of a sample: the e solving
+    tau sum_{t > e} (t - e) = (1 - tau) sum_{t < e} (e - t), by bisection."""
+    t = np.asarray(t, np.float64)
+    lo, hi = float(t.min()), float(t.max())
+    for _ in range(200):
+        e = 0.5 * (lo + hi)
+        if tau * np.sum(np.maximum(t - e, 0.0)) > (1.0 - tau) * np.sum(np.maximum(e - t, 0.0)):
+            lo = e
+        else:
+            hi = e
+    return 0.5 * (lo + hi)
 
 
 def init(F: int, seed: int = 0) -> np.ndarray:

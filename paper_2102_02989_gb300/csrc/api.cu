@@ -228,15 +228,36 @@ static int check_opts(const rsgdf_opts *o)
     if (o->precision != RSGDF_FP64 && o->precision != RSGDF_MIXED) return fail(RSGDF_EINVAL, "unknown precision mode");
     if (o->screening != RSGDF_SCREEN_BOUND && o->screening != RSGDF_SCREEN_LEARNED)
         return fail(RSGDF_EINVAL, "unknown screening mode");
-    if (o->screening == RSGDF_SCREEN_LEARNED) return fail(RSGDF_ENOTIMPL, "learned screening not built in this library");
     return RSGDF_OK;
 }
 
+}  // namespace rsgdf
+
+struct rsgdf_mlp {
+    int F, np, dev;
+    float *P, *G, *m, *v, *mean, *stdv;
+    __half *P16;
+    float margin;
+    int base;                  // feature added to the network output (-1: none)
+    float base_lo, base_hi;    // clamp of that feature
+    int step;
+};
+
+namespace rsgdf {
+
 // Launch the SR kernels of a plan into X.
+struct SRExtras {
+    const rsgdf_mlp *mlp = nullptr;   // learned screen
+    double log10_cut = 0.0;           // prune below this predicted log10 magnitude (after the margin)
+    float *feat_out = nullptr;        // features of every item (device [n][SR_NFEAT])
+    float *mag_out = nullptr;         // magnitude mode (device [n])
+    bool skip_sr = false;             // features only
+};
+
 static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShells &ao, const DevShells &ax,
                   const HBasis &hao, const HBasis &hax, double omega, double *X, long long s_lt, long long s_dt,
                   long long s_P, long long s_mu, long long s_nu, int pfunc0, unsigned long long *counts,
-                  cudaStream_t st, int &nlaunch)
+                  cudaStream_t st, int &nlaunch, const SRExtras &ex = SRExtras())
 {
     if (plan.tri.empty()) return RSGDF_OK;
     for (const SRTriple &t : plan.tri)
@@ -245,7 +266,8 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     std::vector<SRTripleDev> td(plan.tri.size());
     for (size_t i = 0; i < plan.tri.size(); i++) {
         const SRTriple &t = plan.tri[i];
-        td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, t.Rc_cut, t.amu, t.anu, t.item_off};
+        td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, t.Rc_cut, t.amu, t.anu, t.item_off,
+                 t.log10A, t.beta, t.eta1, t.eta2, t.aP};
     }
     SRTripleDev *dtri;
     double *dwin;
@@ -317,6 +339,33 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     A.ec_tab = dec;
     A.ptab = ptab;
     A.sr_doff = dsrdoff;
+    A.item_mag = ex.mag_out;
+    // learned screen: features -> prediction -> skip mask, all on the device
+    float *feat = ex.feat_out;
+    if ((ex.mlp || feat) && plan.n_items > 0) {
+        if (!feat) RC(S.alloc(feat, (size_t)plan.n_items * SR_NFEAT));
+        SRArgs F = A;
+        F.tri_begin = 0;
+        F.tri_end = (int)plan.tri.size();
+        F.item_begin = 0;
+        F.item_end = plan.n_items;
+        t_timer.begin(PH_OTHER);
+        RC(launch_sr_features(F, feat, st));
+        nlaunch++;
+        if (ex.mlp) {
+            float *pred;
+            unsigned char *skip;
+            RC(S.alloc(pred, (size_t)plan.n_items));
+            RC(S.alloc(skip, (size_t)plan.n_items));
+            RC(launch_mlp_forward(ex.mlp->F, ex.mlp->P16, ex.mlp->mean, ex.mlp->stdv, feat, plan.n_items, pred, st));
+            RC(launch_mlp_mask(plan.n_items, SR_NFEAT, feat, ex.mlp->base, ex.mlp->base_lo, ex.mlp->base_hi, pred, ex.mlp->margin,
+                               (float)ex.log10_cut, skip, counts ? counts + 2 * LTOT_MAX + 4 : nullptr, st));
+            nlaunch += 2;
+            A.item_skip = skip;
+        }
+        t_timer.end();
+    }
+    if (ex.skip_sr) return RSGDF_OK;
     for (int c = 0; c <= LTOT_MAX; c++) {
         int b = plan.class_tri_begin[c], e = plan.class_tri_begin[c + 1];
         if (b >= e) continue;
@@ -417,8 +466,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     RC(S.upload(dplist, plist));
     RC(S.upload(dpk2, pk2));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, 2 * LTOT_MAX + 4));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), st));
+    RC(S.alloc(dcnt, 2 * LTOT_MAX + 6));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
 
     // SR folded sums X[lt][dt][P][mu][nu]
     double *X = nullptr;
@@ -427,8 +476,16 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
         RC(S.alloc(X, (size_t)Nk * Nk * m));
         CU(cudaMemsetAsync(X, 0, sizeof(double) * Nk * Nk * m, st));
+        SRExtras ex;
+        if (opts->screening == RSGDF_SCREEN_LEARNED) {
+            if (!opts->mlp) return fail(RSGDF_EINVAL, "learned screening needs opts->mlp");
+            ex.mlp = (const rsgdf_mlp *)opts->mlp;
+            if (ex.mlp->F != SR_NFEAT) return fail(RSGDF_EINVAL, "network input width does not match the SR features");
+            ex.log10_cut = std::log10(opts->eps_screen) - 1.0;
+        }
         RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
-                  dcnt, st, nlaunch));
+                  dcnt, st, nlaunch, ex));
+        t_stats.sr_items = plan.n_items;
     }
     // AFT pair lists (also the overlaps of the G = 0 correction): entries
     // (pair, d, primitive pair) grouped by (pair, BvK cell of d)
@@ -588,8 +645,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     }
     CU(cudaGetLastError());
     // statistics
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 4)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 6)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -738,8 +795,8 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     double *dph;
     RC(S.upload(dph, ph));
     unsigned long long *dcnt;
-    RC(S.alloc(dcnt, 2 * LTOT_MAX + 4));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), st));
+    RC(S.alloc(dcnt, 2 * LTOT_MAX + 6));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
     // SR: X2[lt][P][Q] = sum_{l -> lt} (chi_P^l | erfc | chi_Q^0), the
     // three-center kernel with the unit function as the second pair member
     SRPlan plan;
@@ -801,8 +858,8 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
         CU(cudaMemsetAsync(info_out, 0xff, sizeof(int) * nk, st));
     }
     CU(cudaGetLastError());
-    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 4)));
-    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 4), cudaMemcpyDeviceToHost, st));
+    if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 6)));
+    CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
     t_stats.omega = omega;
@@ -861,6 +918,208 @@ int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, i
     return kphase_noalloc_impl(cell, X, m, npair, kpairs, V_out, stream);
 }
 
+
+int rsgdf_mlp_nparams(int nfeat) { return nfeat > 0 ? mlp_param_count(nfeat) : 0; }
+
+int rsgdf_mlp_create(int nfeat, const float *params, const float *mean, const float *stdv, rsgdf_mlp **out)
+{
+    t_err.clear();
+    if (!out || !params || !mean || !stdv) return fail(RSGDF_EINVAL, "NULL argument");
+    if (nfeat < 1 || nfeat > SR_NFEAT_MAX) return fail(RSGDF_EINVAL, "nfeat outside 1..16");
+    for (int f = 0; f < nfeat; f++)
+        if (!(stdv[f] > 0.0f)) return fail(RSGDF_EINVAL, "stdv must be positive");
+    RC(check_device());
+    rsgdf_mlp *m = new rsgdf_mlp();
+    m->F = nfeat;
+    m->np = mlp_param_count(nfeat);
+    m->margin = 0.0f;
+    m->base = -1;
+    m->base_lo = m->base_hi = 0.0f;
+    m->step = 0;
+    cudaGetDevice(&m->dev);
+    const size_t fb = sizeof(float) * m->np;
+    bool ok = cudaMalloc(&m->P, fb) == cudaSuccess && cudaMalloc(&m->G, fb) == cudaSuccess &&
+              cudaMalloc(&m->m, fb) == cudaSuccess && cudaMalloc(&m->v, fb) == cudaSuccess &&
+              cudaMalloc(&m->P16, sizeof(__half) * m->np) == cudaSuccess &&
+              cudaMalloc(&m->mean, sizeof(float) * nfeat) == cudaSuccess &&
+              cudaMalloc(&m->stdv, sizeof(float) * nfeat) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        rsgdf_mlp_destroy(m);
+        return fail(RSGDF_ENOMEM, "network allocation failed");
+    }
+    cudaMemcpy(m->P, params, fb, cudaMemcpyHostToDevice);
+    cudaMemset(m->G, 0, fb);
+    cudaMemset(m->m, 0, fb);
+    cudaMemset(m->v, 0, fb);
+    cudaMemcpy(m->mean, mean, sizeof(float) * nfeat, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->stdv, stdv, sizeof(float) * nfeat, cudaMemcpyHostToDevice);
+    if (launch_to_half(m->np, m->P, m->P16, 0) != RSGDF_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        rsgdf_mlp_destroy(m);
+        return fail(RSGDF_EDEVICE, "network upload failed");
+    }
+    *out = m;
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_destroy(rsgdf_mlp *m)
+{
+    if (!m) return RSGDF_OK;
+    cudaFree(m->P);
+    cudaFree(m->G);
+    cudaFree(m->m);
+    cudaFree(m->v);
+    cudaFree(m->P16);
+    cudaFree(m->mean);
+    cudaFree(m->stdv);
+    delete m;
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_get_params(const rsgdf_mlp *m, float *params_out)
+{
+    t_err.clear();
+    if (!m || !params_out) return fail(RSGDF_EINVAL, "NULL argument");
+    CU(cudaMemcpy(params_out, m->P, sizeof(float) * m->np, cudaMemcpyDeviceToHost));
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_set_margin(rsgdf_mlp *m, float margin)
+{
+    t_err.clear();
+    if (!m || !(margin >= 0.0f)) return fail(RSGDF_EINVAL, "margin must be >= 0");
+    m->margin = margin;
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi)
+{
+    t_err.clear();
+    if (!m || feature < -1 || feature >= m->F || !(lo <= hi)) return fail(RSGDF_EINVAL, "bad base feature or clamp");
+    m->base = feature;
+    m->base_lo = lo;
+    m->base_hi = hi;
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_forward(const rsgdf_mlp *m, const float *X, long long n, float *y, void *stream)
+{
+    t_err.clear();
+    if (!m || !X || !y || n < 0) return fail(RSGDF_EINVAL, "bad argument");
+    RC(launch_mlp_forward(m->F, m->P16, m->mean, m->stdv, X, n, y, (cudaStream_t)stream));
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_loss_grad(rsgdf_mlp *m, const float *X, const float *t, long long n, float tau, float *loss_out,
+                        float *grad_out, void *stream)
+{
+    t_err.clear();
+    if (!m || !X || !t || n < 1 || !loss_out || !(tau > 0.0f && tau < 1.0f)) return fail(RSGDF_EINVAL, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    float *dl;
+    RC(S.alloc(dl, 1));
+    CU(cudaMemsetAsync(dl, 0, sizeof(float), st));
+    CU(cudaMemsetAsync(m->G, 0, sizeof(float) * m->np, st));
+    RC(launch_mlp_fwd_bwd(m->F, m->P16, m->mean, m->stdv, X, t, nullptr, n, 1.0f / (float)n, tau, m->G, dl, st));
+    CU(cudaMemcpyAsync(loss_out, dl, sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (grad_out) CU(cudaMemcpyAsync(grad_out, m->G, sizeof(float) * m->np, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemsetAsync(m->G, 0, sizeof(float) * m->np, st));
+    CU(cudaStreamSynchronize(st));
+    return RSGDF_OK;
+}
+
+int rsgdf_mlp_train(rsgdf_mlp *m, const float *X, const float *t, long long n, int epochs, int batch, float lr,
+                    float tau, unsigned seed, float *loss_out, void *stream)
+{
+    t_err.clear();
+    if (!m || !X || !t || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f) || !(tau > 0.0f && tau < 1.0f))
+        return fail(RSGDF_EINVAL, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    int *didx;
+    float *dl;
+    RC(S.alloc(didx, (size_t)n));
+    RC(S.alloc(dl, 1));
+    std::vector<int> idx((size_t)n);
+    for (long long i = 0; i < n; i++) idx[i] = (int)i;
+    unsigned long long state = 0x9E3779B97F4A7C15ULL ^ seed;
+    auto rnd = [&]() {   // splitmix64
+        state += 0x9E3779B97F4A7C15ULL;
+        unsigned long long z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    };
+    float last = 0.0f;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (long long i = n - 1; i > 0; i--) std::swap(idx[i], idx[rnd() % (unsigned long long)(i + 1)]);
+        CU(cudaMemcpyAsync(didx, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(dl, 0, sizeof(float), st));
+        for (long long b0 = 0; b0 < n; b0 += batch) {
+            const long long nb = std::min<long long>(batch, n - b0);
+            RC(launch_mlp_fwd_bwd(m->F, m->P16, m->mean, m->stdv, X, t, didx + b0, nb, 1.0f / (float)nb, tau, m->G, dl,
+                                  st));
+            m->step++;
+            RC(launch_mlp_adam(m->np, m->P, m->P16, m->G, m->m, m->v, lr, m->step, st));
+        }
+        if (ep == epochs - 1) {
+            float h = 0.0f;
+            CU(cudaMemcpyAsync(&h, dl, sizeof(float), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            last = h / (float)((n + batch - 1) / batch);
+        }
+    }
+    if (loss_out) *loss_out = last;
+    return RSGDF_OK;
+}
+
+int rsgdf_sr_items(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in, const rsgdf_opts *opts,
+                   int s0, int s1, long long *n_items, float *feat_out, float *mag_out)
+{
+    t_err.clear();
+    RC(check_opts(opts));
+    if (!n_items) return fail(RSGDF_EINVAL, "n_items is NULL");
+    Lattice L;
+    HBasis ao, ax;
+    RC(make_lattice(cell, L, t_err));
+    RC(load_basis(ao_in, ao, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    if (s0 < 0 || s1 > ax.nshell || s0 >= s1) return fail(RSGDF_EINVAL, "aux shell range is empty or out of bounds");
+    double omega;
+    int gm[3];
+    RC(derive_params(L, opts, omega, gm, t_err));
+    SRPlan plan;
+    plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
+    *n_items = plan.n_items;
+    if (!feat_out && !mag_out) return RSGDF_OK;
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    RC(ensure_boys(st));
+    t_timer.reset(st);
+    Scratch S(st);
+    DevShells dao, dax;
+    RC(upload_shells(S, ao, dao));
+    RC(upload_shells(S, ax, dax));
+    const int nao = ao.nfunc, pfunc0 = ax.foff[s0];
+    const int nP = (s1 < ax.nshell ? ax.foff[s1] : ax.nfunc) - pfunc0;
+    const long long m = (long long)nP * nao * nao;
+    double *X = nullptr;
+    if (mag_out) {
+        RC(S.alloc(X, (size_t)L.Nk * L.Nk * m));
+        CU(cudaMemsetAsync(X, 0, sizeof(double) * L.Nk * L.Nk * m, st));
+    }
+    int nl = 0;
+    SRExtras ex;
+    ex.feat_out = feat_out;
+    ex.mag_out = mag_out;
+    ex.skip_sr = (mag_out == nullptr);
+    RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)L.Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
+              nullptr, st, nl, ex));
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
 int rsgdf_last_stats(rsgdf_stats *out)
 {
     if (!out) return fail(RSGDF_EINVAL, "out is NULL");
@@ -875,6 +1134,7 @@ int rsgdf_last_stats(rsgdf_stats *out)
             t_stats.sr_prim_terms += (long long)t_count_host[LTOT_MAX + 2 + L];
         }
         t_stats.sr_integrals = (long long)t_count_host[LTOT_MAX + 1];
+        t_stats.sr_items_pruned = (long long)t_count_host[2 * LTOT_MAX + 4];
         double ms[PH_N];
         t_timer.totals(ms, t_stats.sr_ms_by_L);
         for (int L = 0; L <= LTOT_MAX; L++) t_stats.sr_terms_by_L[L] = (long long)t_count_host[L];

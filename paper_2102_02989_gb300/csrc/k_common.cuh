@@ -1,5 +1,6 @@
 // Device-side declarations shared by the library's CUDA translation units.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,6 +30,7 @@ struct SRTripleDev {
     int nwin, win_off, nd, nsph;
     double Rc_cut, amu, anu;
     long long item_off;
+    double log10A, beta, eta1, eta2, aP;
 };
 
 struct SRArgs {
@@ -54,6 +56,8 @@ struct SRArgs {
     const double *ec_tab;             // [aux primitive][(LMAX+1)^2] single-centre Hermite coefficients
     const double *ptab;               // pair entries of the SR d list
     const long long *sr_doff;         // [global d index] offset of its first entry
+    float *item_mag;                  // [n_items] log10 of the item's largest block, or NULL
+    const unsigned char *item_skip;   // [n_items] 1: pruned by the learned screen, or NULL
 };
 
 // BvK cell (mesh order, last index fastest) of an integer lattice vector
@@ -83,6 +87,20 @@ __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S
 __host__ __device__ void single_E(int lc, double g, double *E);
 __global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,
                              const double *Sf, const int *nk3, int Nk, double fac);
+
+// Learned screening (k_mlp.cu)
+constexpr int SR_NFEAT = 10;        // features per SR work item
+constexpr int SR_NFEAT_MAX = 16;
+int launch_sr_features(const SRArgs &A, float *feat, cudaStream_t st);
+int launch_mlp_forward(int F, const __half *P16, const float *mean, const float *stdv, const float *X, long long n,
+                       float *y, cudaStream_t st);
+int launch_mlp_fwd_bwd(int F, const __half *P16, const float *mean, const float *stdv, const float *X, const float *t,
+                       const int *idx, long long n, float inv_ntot, float tau, float *G, float *loss, cudaStream_t st);
+int launch_mlp_adam(int np, float *P, __half *P16, float *G, float *m, float *v, float lr, int step, cudaStream_t st);
+int launch_to_half(int n, const float *a, __half *b, cudaStream_t st);
+int launch_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *pred,
+                    float margin, float log10_cut, unsigned char *skip, unsigned long long *count, cudaStream_t st);
+int mlp_param_count(int F);
 
 // G-space and phase kernels (k_gspace.cu)
 struct GArgs {

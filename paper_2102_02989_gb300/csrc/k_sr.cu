@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = A.item_begin + (long long)blockIdx.x * SR_WARPS + warp;
     if (item >= A.item_end) return;  // warp-uniform
+    if (A.item_skip && A.item_skip[item]) return;   // pruned by the learned screen (warp-uniform)
     constexpr int NR = ntuv(L);
     unsigned char *base = smem_raw + (size_t)warp * A.warp_bytes;
     double *Tx = (double *)base;            // collected translations (Cartesian)
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
 
     int nT = 0;
     unsigned long long kept = 0;
+    float magmax = 0.0f;   // largest |block| the item adds (magnitude mode)
     int nq = 0;   // FP32 survivors waiting for the exact FP64 test (smem queue Qd)
     for (int b0 = 0; b0 < tr.nsph; b0 += 32) {
         const int idx = b0 + lane;
@@ -494,11 +496,16 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
                     const long long dst = (long long)(c0 + bb) * A.s_lt + (long long)dt * A.s_dt + (pf + ic) * A.s_P +
                                           (mf + ia) * A.s_mu + (nf + ib) * A.s_nu;
                     if (O[o] != 0.0) atomicAdd(&A.X[dst], O[o]);
+                    magmax = fmaxf(magmax, (float)fabs(O[o]));
                 }
                 __syncwarp();
             }
             nT = 0;
         }
+    }
+    if (A.item_mag) {
+        for (int o = 16; o > 0; o >>= 1) magmax = fmaxf(magmax, __shfl_xor_sync(0xffffffffu, magmax, o));
+        if (lane == 0) A.item_mag[item] = magmax > 0.0f ? log10f(magmax) : -30.0f;
     }
     if (lane == 0 && A.term_count) {
         atomicAdd(A.term_count + L, kept);

@@ -310,6 +310,7 @@ struct Bounds {
     std::vector<double> r12;  // per window
     double r12_max;
     double amu, anu;
+    double log10A, beta, eta1, eta2, aP;
 };
 
 // Everything of the bounds that depends only on the AO shell pair.
@@ -406,6 +407,11 @@ void triple_bounds(const Lattice &L, double omega, double eps, const HBasis &aux
     double A = PI * PI * PI * qa * Q.qp;
     B.amu = am;
     B.anu = an;
+    B.log10A = std::log10(A);
+    B.beta = beta;
+    B.eta1 = eta1;
+    B.eta2 = eta2;
+    B.aP = aP;
     // Eq. bound_Rc
     double c0 = A * Q.Sh * 4.0 * PI / L.vol / std::sqrt(PI) / (2.0 * eta2 * eta2 * eta2);
     auto grc = [&](double R) { return c0 / R * std::exp(-eta2 * eta2 * R * R) * grow_rc(lP, lm + ln, aP, p, eta2, R); };
@@ -571,6 +577,11 @@ void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, in
                 t.anu = B.anu;
                 t.nsph = 0;
                 t.item_off = 0;
+                t.log10A = B.log10A;
+                t.beta = B.beta;
+                t.eta1 = B.eta1;
+                t.eta2 = B.eta2;
+                t.aP = B.aP;
                 if (t.nd > 0) plan.tri.push_back(t);
             }
     finish_plan(L, plan);
@@ -605,6 +616,10 @@ void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double o
             t.anu = 0.0;
             t.nsph = 0;
             t.item_off = 0;
+            t.log10A = 0.0;
+            t.beta = 0.0;
+            t.eta1 = t.eta2 = 1.0;
+            t.aP = aux.exps[diffuse_index(aux, P)];
             plan.tri.push_back(t);
         }
     finish_plan(L, plan);

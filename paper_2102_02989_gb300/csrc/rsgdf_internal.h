@@ -59,6 +59,7 @@ struct SRTriple {
     int nsph;         // leading entries of the sphere list with |l| <= Rc_cut + r_round
     double Rc_cut, amu, anu;
     long long item_off;
+    double log10A, beta, eta1, eta2, aP;   // the s-type estimate of the Supplementary Material
 };
 
 struct SRPlan {

@@ -24,7 +24,11 @@ RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
 
 # names exported by the library (every declaration of include/rsgdf.h)
 EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase", "rsgdf_kphase_noalloc",
-           "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64", "rsgdf_sync_status")
+           "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64", "rsgdf_sync_status",
+           "rsgdf_mlp_nparams", "rsgdf_mlp_create", "rsgdf_mlp_destroy", "rsgdf_mlp_get_params",
+           "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
+           "rsgdf_sr_items")
+RSGDF_MLP_NFEAT = 10
 
 
 class RsgdfError(RuntimeError):
@@ -56,6 +60,7 @@ class Stats(C.Structure):
                 ("n_launch", C.c_int), ("sr_ms", C.c_double), ("aft_ms", C.c_double),
                 ("lr_gemm_ms", C.c_double), ("phase_ms", C.c_double), ("other_ms", C.c_double),
                 ("sr_terms_by_L", C.c_longlong * 10), ("sr_prim_terms", C.c_longlong),
+                ("sr_items", C.c_longlong), ("sr_items_pruned", C.c_longlong),
                 ("sr_ms_by_L", C.c_double * 10)]
 
     def asdict(self):
@@ -65,6 +70,7 @@ class Stats(C.Structure):
                 "sr_ms": self.sr_ms, "aft_ms": self.aft_ms, "lr_gemm_ms": self.lr_gemm_ms,
                 "phase_ms": self.phase_ms, "other_ms": self.other_ms,
                 "sr_terms_by_L": list(self.sr_terms_by_L), "sr_prim_terms": self.sr_prim_terms,
+                "sr_items": self.sr_items, "sr_items_pruned": self.sr_items_pruned,
                 "sr_ms_by_L": list(self.sr_ms_by_L)}
 
 
@@ -95,6 +101,16 @@ def load():
         lib.rsgdf_last_error.restype = C.c_char_p
         lib.rsgdf_probe_fp64.argtypes = [vp, vp]
         lib.rsgdf_sync_status.argtypes = [vp]
+        lib.rsgdf_mlp_nparams.argtypes = [i]
+        lib.rsgdf_mlp_create.argtypes = [i, vp, vp, vp, vp]
+        lib.rsgdf_mlp_destroy.argtypes = [vp]
+        lib.rsgdf_mlp_get_params.argtypes = [vp, vp]
+        lib.rsgdf_mlp_set_margin.argtypes = [vp, C.c_float]
+        lib.rsgdf_mlp_set_base.argtypes = [vp, C.c_int, C.c_float, C.c_float]
+        lib.rsgdf_mlp_forward.argtypes = [vp, vp, C.c_longlong, vp, vp]
+        lib.rsgdf_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
+        lib.rsgdf_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, i, i, C.c_float, C.c_float, C.c_uint, vp, vp]
+        lib.rsgdf_sr_items.argtypes = [vp, vp, vp, vp, i, i, vp, vp, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -276,3 +292,88 @@ def rsgdf_probe_fp64(stream=None) -> float:
     v = C.c_double()
     _check(load().rsgdf_probe_fp64(C.byref(v), _stream_ptr(stream)))
     return float(v.value)
+
+
+class Mlp:
+    """Handle of the learned-screening network (parameters on the device)."""
+
+    def __init__(self, params, mean, std):
+        lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        mu = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(std, dtype=np.float32)
+        self.F = len(mu)
+        assert len(p) == lib.rsgdf_mlp_nparams(self.F)
+        h = C.c_void_p()
+        _check(lib.rsgdf_mlp_create(self.F, p.ctypes.data_as(C.c_void_p), mu.ctypes.data_as(C.c_void_p),
+                                    sd.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def nparams(F=RSGDF_MLP_NFEAT):
+        return int(load().rsgdf_mlp_nparams(F))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rsgdf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.zeros(self.nparams(self.F), dtype=np.float32)
+        _check(load().rsgdf_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_margin(self, margin):
+        _check(load().rsgdf_mlp_set_margin(self.h, float(margin)))
+
+    def set_base(self, feature, lo=-20.0, hi=20.0):
+        _check(load().rsgdf_mlp_set_base(self.h, int(feature), float(lo), float(hi)))
+
+    def forward(self, X, stream=None):
+        import torch
+        assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(load().rsgdf_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(y.data_ptr()),
+                                        _stream_ptr(stream)))
+        return y
+
+    def loss_grad(self, X, t, tau=0.5, stream=None):
+        loss = C.c_float()
+        g = np.zeros(self.nparams(self.F), dtype=np.float32)
+        _check(load().rsgdf_mlp_loss_grad(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(t.data_ptr()), X.shape[0],
+                                          float(tau), C.byref(loss), g.ctypes.data_as(C.c_void_p),
+                                          _stream_ptr(stream)))
+        return float(loss.value), g
+
+    def train(self, X, t, epochs=20, batch=1024, lr=1e-3, tau=0.5, seed=0, stream=None):
+        loss = C.c_float()
+        _check(load().rsgdf_mlp_train(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(t.data_ptr()), X.shape[0],
+                                      int(epochs), int(batch), float(lr), float(tau), int(seed), C.byref(loss),
+                                      _stream_ptr(stream)))
+        return float(loss.value)
+
+
+def rsgdf_sr_items(a, kmesh, ao, aux, shells=None, features=True, magnitudes=False, **opt):
+    """(n_items, features [n][10] float32 cuda or None, log10 magnitudes [n] or None)"""
+    import torch
+    lib = load()
+    ra, rx = _BasisRef(ao), _BasisRef(aux)
+    s0, s1 = shells if shells is not None else (0, len(rx.l))
+    c = _cell(a, kmesh)
+    o = _opts(**opt)
+    n = C.c_longlong()
+    _check(lib.rsgdf_sr_items(C.byref(c), ra.ref(), rx.ref(), C.byref(o), s0, s1, C.byref(n), None, None))
+    nn = int(n.value)
+    feat = torch.zeros((nn, RSGDF_MLP_NFEAT), dtype=torch.float32, device="cuda") if features else None
+    mag = torch.zeros(nn, dtype=torch.float32, device="cuda") if magnitudes else None
+    if nn and (features or magnitudes):
+        _check(lib.rsgdf_sr_items(C.byref(c), ra.ref(), rx.ref(), C.byref(o), s0, s1, C.byref(n),
+                                  C.c_void_p(feat.data_ptr()) if feat is not None else None,
+                                  C.c_void_p(mag.data_ptr()) if mag is not None else None))
+    return nn, feat, mag

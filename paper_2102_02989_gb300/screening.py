@@ -1,0 +1,83 @@
+"""Learned screening driver: training data from the FP64 SR kernels'
+magnitude mode, training with the library's kernels, margin calibration and
+use in j3c.  Host orchestration only; every numerical step runs in the CUDA
+library (features, magnitudes, forward, backward, Adam, masking).
+
+Model: the network learns the correction to the s-type estimate carried as
+feature ``BASE`` (log10 of the SR integral of the nearest term, exact for s
+shells).  Targets and that estimate are clamped to the decision window
+[k - 5, k + 1] around the keep level k = log10(eps) - ``drop``: outside it
+only the side of the cut matters.
+Item magnitudes are not a smooth function of the features (symmetric images
+cancel for odd angular momentum, to a depth set by rounding and truncation),
+so the network is fitted to an upper expectile (tau = 0.99) of the targets
+rather than their mean.  Screening prediction = clamp(est) + network(x).
+
+Policy: the library skips an item when its prediction plus the margin is
+below cut = log10(eps) - 1.  The margin is calibrated on held-out items that
+must be kept (magnitude >= eps 10^-drop; many skipped items can land in one
+output element, so the per-item budget sits well below eps): the largest
+shortfall cut - prediction among them plus ``safety`` decades (zero if
+negative), so no held-out item of that magnitude or more is skipped.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import rsgdf
+
+
+def items_dataset(problems, eps_screen=1e-8):
+    """Features and log10 magnitudes of every SR work item of the problems
+    (each a (cell a, kmesh, ao, aux, omega, gmesh, eps_lr) tuple)."""
+    import torch
+    Xs, ts = [], []
+    for (a, km, ao, aux, omega, gmesh, eps_lr) in problems:
+        n, feat, mag = rsgdf.rsgdf_sr_items(a, km, ao, aux, features=True, magnitudes=True, omega=omega, gmesh=gmesh,
+                                            eps_screen=eps_screen, eps_lr=eps_lr)
+        if n:
+            Xs.append(feat)
+            ts.append(mag)
+    torch.cuda.synchronize()
+    return torch.cat(Xs), torch.cat(ts)
+
+
+BASE = 8
+
+
+def train_screen(X, t, epochs=40, batch=2048, lr=2e-3, tau=0.99, seed=0, holdout=0.2, safety=0.5, eps_screen=1e-8,
+                 drop=2.0):
+    """Train the network on (X, t) and calibrate its margin on a held-out part."""
+    import torch
+    # data preparation and calibration statistics on host copies (torch only moves memory)
+    Xh = X.cpu().numpy()
+    traw = t.cpu().numpy()
+    le = float(np.log10(eps_screen))
+    k = le - drop
+    lo, hi = k - 5.0, k + 1.0
+    th = np.clip(traw, lo, hi).astype(np.float32)
+    base = np.clip(Xh[:, BASE], lo, hi).astype(np.float32)
+    n = Xh.shape[0]
+    perm = np.random.default_rng(seed).permutation(n)
+    nh = max(1, int(holdout * n))
+    hv, tr = perm[:nh], perm[nh:]
+    mean = Xh[tr].astype(np.float64).mean(0).astype(np.float32)
+    std = (Xh[tr].astype(np.float64).std(0) + 1e-3).astype(np.float32)
+    dev = X.device
+    Xt = torch.tensor(Xh[tr], device=dev)
+    tt = torch.tensor(th[tr] - base[tr], device=dev)
+    Xv = torch.tensor(Xh[hv], device=dev)
+    from .mlp_init import init_params
+    m = rsgdf.Mlp(init_params(Xh.shape[1], seed), mean, std)
+    m.set_base(BASE, lo, hi)
+    loss = m.train(Xt, tt, epochs=epochs, batch=batch, lr=lr, tau=tau, seed=seed)
+    pv = m.forward(Xv).cpu().numpy() + base[hv]
+    cut = le - 1.0
+    keep = traw[hv] >= k
+    short = float((cut - pv[keep]).max()) if keep.any() else -np.inf
+    margin = max(0.0, short + safety)
+    m.set_margin(margin)
+    r = th[hv] - pv
+    return m, {"train_loss": loss, "holdout_rmse": float(np.sqrt(np.mean(r * r))), "max_shortfall": short,
+               "margin": margin, "holdout_pruned": float(np.mean(pv + margin < cut)),
+               "holdout_ideal": float(np.mean(traw[hv] < k)), "n_train": int(n - nh), "n_holdout": int(nh)}

@@ -1,0 +1,137 @@
+"""Learned screening on the GPU: the hand-written training kernels against the
+FP64 reference network (oracle/mlp.py), training convergence, item features
+and magnitudes, and the end-to-end gain at equal accuracy."""
+import numpy as np
+import pytest
+
+from paper_2102_02989_gb300 import inputs
+from rules_ref import gmesh_for, omega_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_02989_gb300 import rsgdf
+    rsgdf.load()
+    return rsgdf
+
+
+def test_gradient_matches_fp64_reference(rs):
+    """FP16 parameters and activations, FP32 accumulation: loss to ~1e-3 and
+    gradients to ~2e-2 of their largest entry, against the FP64 chain rule
+    evaluated with the same (FP16-rounded) parameters."""
+    import torch
+    from oracle import mlp as ref
+    from paper_2102_02989_gb300.mlp_init import init_params
+    F = rs.RSGDF_MLP_NFEAT
+    rng = np.random.default_rng(8)
+    th = init_params(F, 3)
+    mean = rng.normal(size=F).astype(np.float32)
+    std = rng.uniform(0.5, 2.0, size=F).astype(np.float32)
+    X = rng.normal(size=(300, F)).astype(np.float32)
+    t = rng.normal(size=300).astype(np.float32)
+    m = rs.Mlp(th, mean, std)
+    th16 = th.astype(np.float16).astype(np.float64)
+    Xn = (X.astype(np.float64) - mean) / std
+    for tau in (0.5, 0.99):
+        loss, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda"), tau=tau)
+        Lr, gr = ref.loss_and_grad(th16, Xn, t.astype(np.float64), tau)
+        assert abs(loss - Lr) < 2e-3 * max(1.0, Lr), (tau, loss, Lr)
+        assert np.max(np.abs(g - gr)) < 2e-2 * np.max(np.abs(gr)), tau
+    # forward pass against the reference
+    y = m.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    yr = ref.forward(th16, Xn)[0]
+    assert np.max(np.abs(y - yr)) < 1e-2 * max(1.0, np.max(np.abs(yr)))
+
+
+def test_training_reduces_loss(rs):
+    import torch
+    from paper_2102_02989_gb300.mlp_init import init_params
+    F = rs.RSGDF_MLP_NFEAT
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(20000, F)).astype(np.float32)
+    t = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - X[:, 3]).astype(np.float32)
+    m = rs.Mlp(init_params(F, 1), np.zeros(F, np.float32), np.ones(F, np.float32))
+    Xd, td = torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda")
+    l0, _ = m.loss_grad(Xd, td)
+    l1 = m.train(Xd, td, epochs=15, batch=512, lr=3e-3, seed=2)
+    l2, _ = m.loss_grad(Xd, td)
+    assert l2 < 0.1 * l0, (l0, l1, l2)
+
+
+def test_items_features_and_magnitudes(rs):
+    import torch
+    p = inputs.config1()
+    gm = gmesh_for(p.a, p.omega, p.eps_lr, p.kmesh)
+    n, feat, mag = rs.rsgdf_sr_items(p.a, p.kmesh, p.ao, p.aux, features=True, magnitudes=True, omega=p.omega,
+                                     gmesh=gm, eps_screen=p.eps_sr, eps_lr=p.eps_lr)
+    assert n > 1000 and feat.shape == (n, rs.RSGDF_MLP_NFEAT)
+    f = feat.cpu().numpy()
+    mg = mag.cpu().numpy()
+    assert np.all(np.isfinite(f)) and np.all(np.isfinite(mg))
+    assert set(np.unique(f[:, 0])) <= {0.0, 1.0, 2.0}
+    # the largest item magnitude is of the order of the largest SR integral
+    V = rs.rsgdf_j3c_sr(p.a, p.kmesh, p.ao, p.aux, [(0, 0)], omega=p.omega, gmesh=gm, eps_screen=p.eps_sr,
+                        eps_lr=p.eps_lr).cpu().numpy()
+    assert 0.1 < 10 ** mg.max() / np.max(np.abs(V)) < 10.0
+    # the s-type estimate feature correlates with the measured magnitude
+    ok = mg > -29
+    assert np.corrcoef(f[ok, 8], mg[ok])[0, 1] > 0.5
+
+
+def test_learned_screen_gain_at_equal_accuracy(rs, orc):
+    """Train on config 1 items, apply to a config 2 slice: the network skips
+    items the estimates keep, and the result stays within the same 10 eps of
+    the converged oracle as the estimates alone."""
+    import torch
+    from paper_2102_02989_gb300 import screening
+    p1 = inputs.config1()
+    gm1 = gmesh_for(p1.a, p1.omega, p1.eps_lr, p1.kmesh)
+    p2 = inputs.config2()
+    w2 = omega_for(p2.a, p2.gmesh, p2.eps_lr, p2.kmesh)
+    X, t = screening.items_dataset([(p1.a, p1.kmesh, p1.ao, p1.aux, p1.omega, gm1, p1.eps_lr),
+                                    (p2.a, p2.kmesh, p2.ao, p2.aux.subset(range(0, 16)), w2, p2.gmesh, p2.eps_lr)],
+                                   eps_screen=1e-8)
+    m, info = screening.train_screen(X, t, seed=0)
+    kp = [(0, 0), (1, 6), (3, 2)]
+    sh = (16, 32)      # the second atom's aux shells: not in the training data
+    eps = 1e-8
+    base = rs.rsgdf_j3c_sr(p2.a, p2.kmesh, p2.ao, p2.aux, kp, shells=sh, gmesh=p2.gmesh, eps_screen=eps,
+                           eps_lr=p2.eps_lr).cpu().numpy()
+    st0 = rs.rsgdf_last_stats()
+    learned = rs.rsgdf_j3c_sr(p2.a, p2.kmesh, p2.ao, p2.aux, kp, shells=sh, gmesh=p2.gmesh, eps_screen=eps,
+                              eps_lr=p2.eps_lr, screening=rs.RSGDF_SCREEN_LEARNED, mlp=m.h).cpu().numpy()
+    st1 = rs.rsgdf_last_stats()
+    conv = orc.j3c(p2.a, p2.kmesh, p2.ao, p2.aux, w2, kp, eps_sr=1e-13, gmesh=p2.gmesh, shells=sh, lr=False,
+                   eps_lr=p2.eps_lr)
+    err_base = np.max(np.abs(base - conv))
+    err_learned = np.max(np.abs(learned - conv))
+    print("learned screen:", info, "items", st1["sr_items"], "pruned", st1["sr_items_pruned"], "terms", st0["sr_terms"],
+          "->", st1["sr_terms"], "err", err_base, err_learned)
+    assert st1["sr_items_pruned"] > 0.2 * st1["sr_items"], (st1, info)
+    assert st1["sr_terms"] < st0["sr_terms"]
+    assert err_learned < 10 * eps, (err_base, err_learned, info)
+
+
+def test_expectile_training_envelope(rs):
+    """Training with tau = 0.99 on noisy targets lands above the mean fit:
+    the trained constant-feature network approaches the upper expectile."""
+    import torch
+    from oracle import mlp as ref
+    from paper_2102_02989_gb300.mlp_init import init_params
+    F = rs.RSGDF_MLP_NFEAT
+    rng = np.random.default_rng(11)
+    X = np.zeros((8192, F), np.float32)
+    t = rng.normal(size=8192).astype(np.float32)
+    Xd, td = torch.tensor(X, device="cuda"), torch.tensor(t, device="cuda")
+    out = {}
+    for tau in (0.5, 0.99):
+        m = rs.Mlp(init_params(F, 4), np.zeros(F, np.float32), np.ones(F, np.float32))
+        m.train(Xd, td, epochs=40, batch=512, lr=3e-3, tau=tau, seed=1)
+        out[tau] = float(m.forward(Xd[:1]).cpu().numpy()[0])
+    assert abs(out[0.5] - ref.expectile(t, 0.5)) < 0.05, out
+    assert abs(out[0.99] - ref.expectile(t, 0.99)) < 0.1, (out, ref.expectile(t, 0.99))
