@@ -132,6 +132,48 @@ int rsgdf_j3c(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *
               double *V_out);
 
 /*
+ * Batched j3c (SR + G=0 + LR, all aux shells) over many cells at once.  A
+ * handle holds every cell's plan, device tables and buffers, so a run only
+ * issues kernels: the SR lattice sums of all cells go out as ONE persistent
+ * launch per angular-momentum class (lP + lmu + lnu), whose warps draw work
+ * items of every cell from one queue; the G-space and phase steps follow per
+ * cell.  Flags:
+ *   RSGDF_BATCH_GRAPH    : the first run captures the launch sequence into a
+ *                          CUDA graph; later runs with the same V_out pointers
+ *                          replay it (other pointers: captured anew).  With
+ *                          stream NULL the graph runs on an internal stream
+ *                          ordered after and before the legacy stream.
+ *   RSGDF_BATCH_AUTOTUNE : before the first run, each class launch is timed
+ *                          on the real items over its tile choices (bin chunk
+ *                          = BvK cells held per warp, items per queue grab)
+ *                          and the fastest is kept for the handle's life.
+ * Arguments: probs[nprob] (cell, AO, aux; host, read during create only),
+ * opts as for rsgdf_j3c (opts->mlp, if used, must outlive the handle),
+ * npair[nprob], kpairs = the cells' (k1, k2) lists concatenated
+ * ([sum npair][2]).  V_out[p]: device complex [npair[p]][naux_p][nao_p][nao_p],
+ * overwritten.  Device memory is allocated stream-ordered on opts->stream at
+ * create and released by destroy, which first waits for the device.  Errors
+ * as for rsgdf_j3c; create reports the failing cell in rsgdf_last_error.
+ */
+typedef struct {
+    const rsgdf_cell *cell;
+    const rsgdf_basis *ao, *aux;
+} rsgdf_problem;
+#define RSGDF_BATCH_GRAPH 1
+#define RSGDF_BATCH_AUTOTUNE 2
+typedef struct rsgdf_batch rsgdf_batch;
+int rsgdf_j3c_batch_create(int nprob, const rsgdf_problem *probs, const rsgdf_opts *opts, const int *npair,
+                           const int *kpairs, int flags, rsgdf_batch **out);
+int rsgdf_j3c_batch_run(rsgdf_batch *b, double *const *V_out, void *stream);
+int rsgdf_j3c_batch_destroy(rsgdf_batch *b);
+/* per class L = 0..9 of the SR launches: CTAs, bin chunk, items per grab
+ * (0 where the class has no work); each pointer may be NULL */
+int rsgdf_j3c_batch_tiles(const rsgdf_batch *b, int *grid, int *bc, int *grab);
+/* one-shot form: create (no flags), run, destroy */
+int rsgdf_j3c_batch(int nprob, const rsgdf_problem *probs, const rsgdf_opts *opts, const int *npair,
+                    const int *kpairs, double *const *V_out);
+
+/*
  * Bloch-phase contraction of folded lattice sums (Eq. BvK_latsum_LR):
  *   V[pair][i] = sum_{lt, dt} e^{-i k12.lt} e^{+i k2.dt} X[lt][dt][i]
  *   X      : device double [Nk][Nk][m] (BvK cells lt, dt in mesh order)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -30,6 +31,7 @@ struct PhaseTimer {
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind, cls;
     cudaStream_t st = nullptr;
+    bool on = true;   // off while a graph is captured
     void reset(cudaStream_t s)
     {
         for (auto e : ev) cudaEventDestroy(e);
@@ -37,6 +39,7 @@ struct PhaseTimer {
         kind.clear();
         cls.clear();
         st = s;
+        on = true;
     }
     cudaEvent_t mark()
     {
@@ -48,11 +51,15 @@ struct PhaseTimer {
     }
     void begin(int k, int c = -1)
     {
+        if (!on) return;
         kind.push_back(k);
         cls.push_back(c);
         mark();
     }
-    void end() { mark(); }
+    void end()
+    {
+        if (on) mark();
+    }
     void totals(double *ms, double *cls_ms)
     {
         for (int i = 0; i < PH_N; i++) ms[i] = 0.0;
@@ -245,7 +252,11 @@ struct rsgdf_mlp {
 
 namespace rsgdf {
 
-// Launch the SR kernels of a plan into X.
+// ---------------------------------------------------------------------------
+// SR lattice sums: per-problem setup (uploads, per-class descriptors), the
+// per-problem pre-pass (pair Hermite tables, learned screen) and the class
+// launches, which may cover several problems at once.
+// ---------------------------------------------------------------------------
 struct SRExtras {
     const rsgdf_mlp *mlp = nullptr;   // learned screen
     double log10_cut = 0.0;           // prune below this predicted log10 magnitude (after the margin)
@@ -254,11 +265,38 @@ struct SRExtras {
     bool skip_sr = false;             // features only
 };
 
-static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShells &ao, const DevShells &ax,
-                  const HBasis &hao, const HBasis &hax, double omega, double *X, long long s_lt, long long s_dt,
-                  long long s_P, long long s_mu, long long s_nu, int pfunc0, unsigned long long *counts,
-                  cudaStream_t st, int &nlaunch, const SRExtras &ex = SRExtras())
+struct SRSetup {
+    SRArgs A;                        // fields common to every class
+    std::vector<SRArgs> cls;         // per class with work: triple and item ranges, list sizes
+    std::vector<int> cls_L;
+    DevShells ao{};
+    int nshell = 0;
+    PairEntry *dent = nullptr;       // SR pair entries and their Hermite table
+    int nent = 0;
+    int *ddl = nullptr;
+    double *da9 = nullptr, *ptab = nullptr;
+    const rsgdf_mlp *mlp = nullptr;
+    float log10_cut = 0.0f;
+    float *feat = nullptr, *pred = nullptr;
+    unsigned char *skip = nullptr;
+    unsigned long long *counts = nullptr;
+    long long n_items = 0;
+    int ntri = 0;
+    bool skip_sr = false;
+};
+
+static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan, const DevShells &ao,
+                    const DevShells &ax, const HBasis &hao, const HBasis &hax, double omega, double *X, long long s_lt,
+                    long long s_dt, long long s_P, long long s_mu, long long s_nu, int pfunc0,
+                    unsigned long long *counts, const SRExtras &ex = SRExtras())
 {
+    memset(&R.A, 0, sizeof(R.A));
+    R.cls.clear();
+    R.cls_L.clear();
+    R.n_items = plan.n_items;
+    R.ntri = (int)plan.tri.size();
+    R.counts = counts;
+    R.skip_sr = ex.skip_sr;
     if (plan.tri.empty()) return RSGDF_OK;
     for (const SRTriple &t : plan.tri)
         if (hax.nprim[t.P] * hao.nprim[t.mu] * hao.nprim[t.nu] > 64)
@@ -271,11 +309,11 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     }
     SRTripleDev *dtri;
     double *dwin;
-    int *dpoff, *dl, *dsph;
+    int *dpoff, *dsph;
     RC(S.upload(dtri, td));
     RC(S.upload(dwin, plan.win));
     RC(S.upload(dpoff, plan.pair_doff));
-    RC(S.upload(dl, plan.dlist));
+    RC(S.upload(R.ddl, plan.dlist));
     RC(S.upload(dsph, plan.sph));
     // Hermite tables of every (pair, d, primitive pair) of the SR d lists,
     // shared by all aux shells (entries of one d contiguous, ij order)
@@ -295,21 +333,19 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
                 }
         }
     }
-    PairEntry *dent;
     long long *dsrdoff;
-    double *ptab;
-    RC(S.upload(dent, ent));
+    RC(S.upload(R.dent, ent));
+    R.nent = (int)ent.size();
     RC(S.upload(dsrdoff, sr_doff));
-    RC(S.alloc(ptab, (size_t)std::max(off, 1LL)));
-    double a9h[9], bq_unused[9];
-    int nk_unused[3];
-    fill_lattice(L, a9h, bq_unused, nk_unused);
-    double *da9;
-    RC(S.upload(da9, std::vector<double>(a9h, a9h + 9)));
-    t_timer.begin(PH_SR);
-    RC(launch_pair_prep(ao, hao.nshell, dent, (int)ent.size(), dl, da9, ptab, nullptr, nullptr, nullptr, st));
-    t_timer.end();
-    nlaunch++;
+    RC(S.alloc(R.ptab, (size_t)std::max(off, 1LL)));
+    R.ao = ao;
+    R.nshell = hao.nshell;
+    {
+        double a9h[9], bq_unused[9];
+        int nk_unused[3];
+        fill_lattice(L, a9h, bq_unused, nk_unused);
+        RC(S.upload(R.da9, std::vector<double>(a9h, a9h + 9)));
+    }
     // single-centre Hermite coefficients of every aux primitive
     std::vector<double> ec((size_t)hax.exps.size() * (LMAX + 1) * (LMAX + 1), 0.0);
     for (int sh = 0; sh < hax.nshell; sh++)
@@ -319,14 +355,13 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
         }
     double *dec;
     RC(S.upload(dec, ec));
-    SRArgs A;
-    memset(&A, 0, sizeof(A));
+    SRArgs &A = R.A;
     A.ao = ao;
     A.ax = ax;
     A.tri = dtri;
     A.win = dwin;
     A.pair_doff = dpoff;
-    A.dlist = dl;
+    A.dlist = R.ddl;
     A.sph = dsph;
     fill_lattice(L, A.a, A.bq, A.nk);
     A.Nk = L.Nk;
@@ -337,35 +372,26 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
     A.term_count = counts;
     for (int x = 0; x < 9; x++) A.af[x] = (float)A.a[x];
     A.ec_tab = dec;
-    A.ptab = ptab;
+    A.ptab = R.ptab;
     A.sr_doff = dsrdoff;
     A.item_mag = ex.mag_out;
-    // learned screen: features -> prediction -> skip mask, all on the device
-    float *feat = ex.feat_out;
-    if ((ex.mlp || feat) && plan.n_items > 0) {
-        if (!feat) RC(S.alloc(feat, (size_t)plan.n_items * SR_NFEAT));
-        SRArgs F = A;
-        F.tri_begin = 0;
-        F.tri_end = (int)plan.tri.size();
-        F.item_begin = 0;
-        F.item_end = plan.n_items;
-        t_timer.begin(PH_OTHER);
-        RC(launch_sr_features(F, feat, st));
-        nlaunch++;
+    A.tri_begin = 0;
+    A.tri_end = R.ntri;
+    A.item_begin = 0;
+    A.item_end = plan.n_items;
+    // learned screen buffers
+    R.feat = ex.feat_out;
+    if ((ex.mlp || R.feat) && plan.n_items > 0) {
+        if (!R.feat) RC(S.alloc(R.feat, (size_t)plan.n_items * SR_NFEAT));
         if (ex.mlp) {
-            float *pred;
-            unsigned char *skip;
-            RC(S.alloc(pred, (size_t)plan.n_items));
-            RC(S.alloc(skip, (size_t)plan.n_items));
-            RC(launch_mlp_forward(ex.mlp->F, ex.mlp->P16, ex.mlp->mean, ex.mlp->stdv, feat, plan.n_items, pred, st));
-            RC(launch_mlp_mask(plan.n_items, SR_NFEAT, feat, ex.mlp->base, ex.mlp->base_lo, ex.mlp->base_hi, pred, ex.mlp->margin,
-                               (float)ex.log10_cut, skip, counts ? counts + 2 * LTOT_MAX + 4 : nullptr, st));
-            nlaunch += 2;
-            A.item_skip = skip;
+            R.mlp = ex.mlp;
+            R.log10_cut = (float)ex.log10_cut;
+            RC(S.alloc(R.pred, (size_t)plan.n_items));
+            RC(S.alloc(R.skip, (size_t)plan.n_items));
+            A.item_skip = R.skip;
         }
-        t_timer.end();
     }
-    if (ex.skip_sr) return RSGDF_OK;
+    // per-class descriptors
     for (int c = 0; c <= LTOT_MAX; c++) {
         int b = plan.class_tri_begin[c], e = plan.class_tri_begin[c + 1];
         if (b >= e) continue;
@@ -379,103 +405,324 @@ static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShe
             int tot = 0;
             for (int ia = 0; ia < ncart(lm); ia++)
                 for (int ib = 0; ib < ncart(ln); ib++) {
-                    int ax[3], bx[3], n = 0;
+                    int ax3[3], bx3[3], n = 0;
                     for (int x = lm; x >= 0; x--)
-                        for (int y = lm - x; y >= 0; y--) { if (n++ == ia) { ax[0] = x; ax[1] = y; ax[2] = lm - x - y; } }
+                        for (int y = lm - x; y >= 0; y--) { if (n++ == ia) { ax3[0] = x; ax3[1] = y; ax3[2] = lm - x - y; } }
                     n = 0;
                     for (int x = ln; x >= 0; x--)
-                        for (int y = ln - x; y >= 0; y--) { if (n++ == ib) { bx[0] = x; bx[1] = y; bx[2] = ln - x - y; } }
-                    tot += (ax[0] + bx[0] + 1) * (ax[1] + bx[1] + 1) * (ax[2] + bx[2] + 1);
+                        for (int y = ln - x; y >= 0; y--) { if (n++ == ib) { bx3[0] = x; bx3[1] = y; bx3[2] = ln - x - y; } }
+                    tot += (ax3[0] + bx3[0] + 1) * (ax3[1] + bx3[1] + 1) * (ax3[2] + bx3[2] + 1);
                 }
             lmax_list = std::max(lmax_list, tot);
         }
-        A.tri_begin = b;
-        A.tri_end = e;
-        A.item_begin = plan.tri[b].item_off;
-        A.item_end = (e < (int)plan.tri.size()) ? plan.tri[e].item_off : plan.n_items;
-        t_timer.begin(PH_SR, c);
-        RC(launch_sr(c, A, ncmax, wmax, lmax_list, st));
-        t_timer.end();
-        nlaunch++;
+        SRArgs Ac = A;
+        Ac.tri_begin = b;
+        Ac.tri_end = e;
+        Ac.item_begin = plan.tri[b].item_off;
+        Ac.item_end = (e < (int)plan.tri.size()) ? plan.tri[e].item_off : plan.n_items;
+        Ac.ncomp_max = ncmax;
+        Ac.w_max = wmax;
+        Ac.list_max = lmax_list;
+        R.cls.push_back(Ac);
+        R.cls_L.push_back(c);
     }
     return RSGDF_OK;
 }
 
+// Pair Hermite tables, then (learned screen) features -> prediction -> mask.
+static int sr_pre(const SRSetup &R, cudaStream_t st, int &nl)
+{
+    if (R.ntri == 0) return RSGDF_OK;
+    t_timer.begin(PH_SR);
+    RC(launch_pair_prep(R.ao, R.nshell, R.dent, R.nent, R.ddl, R.da9, R.ptab, nullptr, nullptr, nullptr, st));
+    t_timer.end();
+    nl++;
+    if (R.feat && R.n_items > 0) {
+        t_timer.begin(PH_OTHER);
+        RC(launch_sr_features(R.A, R.feat, st));
+        nl++;
+        if (R.mlp) {
+            RC(launch_mlp_forward(R.mlp->F, R.mlp->P16, R.mlp->mean, R.mlp->stdv, R.feat, R.n_items, R.pred, st));
+            RC(launch_mlp_mask(R.n_items, SR_NFEAT, R.feat, R.mlp->base, R.mlp->base_lo, R.mlp->base_hi, R.pred,
+                               R.mlp->margin, R.log10_cut, R.skip, R.counts ? R.counts + 2 * LTOT_MAX + 4 : nullptr,
+                               st));
+            nl += 2;
+        }
+        t_timer.end();
+    }
+    return RSGDF_OK;
+}
+
+// One launch of one class over the items of several problems.
+struct SRClassLaunch {
+    int L = 0;
+    std::vector<SRArgs> desc;
+    std::vector<long long> cum;
+    SRArgs *ddesc = nullptr;
+    long long *dcum = nullptr;
+    int ncmax = 0, wmax = 0, lmax = 0;
+    int bc = 1;
+    size_t warp_bytes = 0;
+    long long ntot = 0;
+    int grid = 1, grab = 1;
+};
+
+static int g_num_sms = 0;
+
+static int sr_set_bc(SRClassLaunch &c, int bc, cudaStream_t st)
+{
+    c.bc = bc;
+    c.warp_bytes = sr_warp_bytes(c.L, bc, c.ncmax, c.wmax, c.lmax);
+    for (SRArgs &a : c.desc) {
+        a.bc = bc;
+        a.warp_bytes = (int)c.warp_bytes;
+        a.ncomp_max = c.ncmax;
+        a.w_max = c.wmax;
+        a.list_max = c.lmax;
+    }
+    CU(cudaMemcpyAsync(c.ddesc, c.desc.data(), sizeof(SRArgs) * c.desc.size(), cudaMemcpyHostToDevice, st));
+    const int occ = sr_occupancy(c.L, sr_launch_smem(c.L, bc, c.ncmax, c.wmax, c.lmax));
+    if (occ < 1) return fail(RSGDF_EDEVICE, "SR kernel does not fit on an SM");
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    c.grid = occ * std::max(g_num_sms, 1);
+    return RSGDF_OK;
+}
+
+// Merge the classes of several problems into one launch per class.
+static int sr_merge(const std::vector<const SRSetup *> &rs, Scratch &S, cudaStream_t st,
+                    std::vector<SRClassLaunch> &out)
+{
+    out.clear();
+    for (int L = 0; L <= LTOT_MAX; L++) {
+        SRClassLaunch c;
+        c.L = L;
+        c.cum.push_back(0);
+        for (const SRSetup *r : rs) {
+            if (r->skip_sr) continue;
+            for (size_t i = 0; i < r->cls.size(); i++) {
+                if (r->cls_L[i] != L) continue;
+                const SRArgs &a = r->cls[i];
+                c.desc.push_back(a);
+                c.cum.push_back(c.cum.back() + (a.item_end - a.item_begin));
+                c.ncmax = std::max(c.ncmax, a.ncomp_max);
+                c.wmax = std::max(c.wmax, a.w_max);
+                c.lmax = std::max(c.lmax, a.list_max);
+            }
+        }
+        if (c.desc.empty()) continue;
+        c.ntot = c.cum.back();
+        RC(S.alloc(c.ddesc, c.desc.size()));
+        RC(S.upload(c.dcum, c.cum));
+        RC(sr_set_bc(c, sr_default_bc(L, c.ncmax, c.wmax), st));
+        out.push_back(std::move(c));
+    }
+    return RSGDF_OK;
+}
+
+static int sr_run(std::vector<SRClassLaunch> &cl, unsigned long long *dqueue, cudaStream_t st, int &nl)
+{
+    for (SRClassLaunch &c : cl) {
+        t_timer.begin(PH_SR, c.L);
+        RC(launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes, dqueue + c.L, c.grid,
+                           c.grab, st));
+        t_timer.end();
+        nl++;
+    }
+    return RSGDF_OK;
+}
+
+// Autotuner of the SR class launches: bin chunk (shared memory per warp and
+// so occupancy) and items per queue grab, each candidate timed on the real
+// items with events.  The launches accumulate into X: callers zero X again.
+static int sr_tune(std::vector<SRClassLaunch> &cl, unsigned long long *dqueue, cudaStream_t st, float *tuned_ms)
+{
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float total = 0.0f;
+    for (SRClassLaunch &c : cl) {
+        const int bc0 = c.bc;
+        int best_bc = bc0, best_grab = 1;
+        float best = 1e30f;
+        const int bcs[3] = {bc0, std::max(1, bc0 / 2), std::min(16, bc0 * 2)};
+        const int grabs[2] = {1, 4};
+        for (int ib = 0; ib < 3; ib++) {
+            if (ib > 0 && bcs[ib] == bcs[0]) continue;
+            if (ib == 2 && bcs[2] == bcs[1]) continue;
+            if (sr_set_bc(c, bcs[ib], st) != RSGDF_OK) continue;
+            for (int g : grabs) {
+                c.grab = g;
+                cudaEventRecord(e0, st);
+                int r = launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes,
+                                        dqueue + c.L, c.grid, c.grab, st);
+                cudaEventRecord(e1, st);
+                if (r != RSGDF_OK) break;
+                float ms = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    return fail(RSGDF_EDEVICE, "autotuner timing failed");
+                if (ms < best) {
+                    best = ms;
+                    best_bc = bcs[ib];
+                    best_grab = g;
+                }
+            }
+        }
+        RC(sr_set_bc(c, best_bc, st));
+        c.grab = best_grab;
+        total += best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (tuned_ms) *tuned_ms = total;
+    return RSGDF_OK;
+}
+
+// Whole SR pass of one problem (setup, pre-pass, class launches).
+static int run_sr(Scratch &S, const Lattice &L, const SRPlan &plan, const DevShells &ao, const DevShells &ax,
+                  const HBasis &hao, const HBasis &hax, double omega, double *X, long long s_lt, long long s_dt,
+                  long long s_P, long long s_mu, long long s_nu, int pfunc0, unsigned long long *counts,
+                  cudaStream_t st, int &nlaunch, const SRExtras &ex = SRExtras())
+{
+    SRSetup R;
+    RC(sr_setup(R, S, L, plan, ao, ax, hao, hax, omega, X, s_lt, s_dt, s_P, s_mu, s_nu, pfunc0, counts, ex));
+    RC(sr_pre(R, st, nlaunch));
+    if (ex.skip_sr) return RSGDF_OK;
+    std::vector<SRClassLaunch> cl;
+    RC(sr_merge({&R}, S, st, cl));
+    unsigned long long *dq;
+    RC(S.alloc(dq, LTOT_MAX + 1));
+    return sr_run(cl, dq, st, nlaunch);
+}
+
 enum { MODE_SR = 1, MODE_LR = 2 };
 
-static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in,
-                    const rsgdf_opts *opts, int npair, const int *kpairs, int s0, int s1, double *V, int mode)
-{
-    t_err.clear();
-    memset(&t_stats, 0, sizeof(t_stats));
-    t_count_valid = false;
-    RC(check_opts(opts));
+// One j3c problem: plan, device buffers and launch parameters.  Everything
+// that allocates or copies from the host happens in j3c_prepare; the
+// j3c_exec_* functions only issue kernels and memsets, so a sequence of them
+// can be captured into a CUDA graph.
+struct J3cProblem {
     Lattice L;
     HBasis ao, ax;
-    RC(make_lattice(cell, L, t_err));
-    RC(load_basis(ao_in, ao, t_err));
-    RC(load_basis(aux_in, ax, t_err));
+    double omega = 0.0;
+    int gm[3] = {0, 0, 0};
+    int s0 = 0, s1 = 0, nP = 0, pfunc0 = 0, nao = 0, Nk = 0, mode = 0;
+    long long m = 0;
+    DevShells dao{}, dax{};
+    double *da9 = nullptr;
+    const void *phk = nullptr;
+    int fp32 = 0;
+    std::vector<int> gkey;
+    int *dplist = nullptr, *dpk2 = nullptr, *dk12 = nullptr, *dgoff = nullptr;
+    // SR
+    SRPlan plan;
+    SRSetup sr;
+    double *X = nullptr;
+    int nlt = 1;   // lt slabs of X: Nk, or 1 when only k12 = 0 is asked (phase 1 is then the plain sum over lt)
+    // AFT pair lists
+    PairEntry *dent = nullptr;
+    int nent = 0;
+    int *dseg = nullptr, *dalist = nullptr;
+    double *ptab = nullptr;
+    float *ptab32 = nullptr;
+    float2 *uph = nullptr, *ph0 = nullptr;
+    double *db9 = nullptr;
+    bool mixed_aft = false;
+    // G = 0 correction
+    double *SP = nullptr, *Sf = nullptr;
+    double g0fac = 0.0;
+    bool g0 = false;
+    // G space
+    int *dg = nullptr;
+    int NG = 0;
+    double *W = nullptr, *Y = nullptr;
+    float *Apl = nullptr, *Bpl = nullptr;
+    long long nbpl = 0;
+    int B = 1;
+    double *T = nullptr;
+    std::vector<GArgs> garg;
+    long long aft_units = 0, lr_flops = 0;
+};
+
+// Host-side checks and derived parameters; touches no device.
+static int j3c_check(J3cProblem &P, const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in,
+                     const rsgdf_opts *opts, int npair, const int *kpairs, int s0, int s1)
+{
+    RC(check_opts(opts));
+    RC(make_lattice(cell, P.L, t_err));
+    RC(load_basis(ao_in, P.ao, t_err));
+    RC(load_basis(aux_in, P.ax, t_err));
     if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
     for (int i = 0; i < 2 * npair; i++)
-        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
-    if (s0 < 0 || s1 > ax.nshell || s0 >= s1) return fail(RSGDF_EINVAL, "aux shell range is empty or out of bounds");
-    if (!V) return fail(RSGDF_EINVAL, "V_out is NULL");
-    double omega;
-    int gm[3];
-    RC(derive_params(L, opts, omega, gm, t_err));
-    RC(check_device());
-    cudaStream_t st = (cudaStream_t)opts->stream;
-    RC(ensure_boys(st));
-    t_timer.reset(st);
-    Scratch S(st);
-    const int nao = ao.nfunc;
-    const int pfunc0 = ax.foff[s0];
-    const int nP = (s1 < ax.nshell ? ax.foff[s1] : ax.nfunc) - pfunc0;
-    const long long m = (long long)nP * nao * nao;
-    const int Nk = L.Nk;
-    int nlaunch = 0;
-    DevShells dao, dax;
-    RC(upload_shells(S, ao, dao));
-    RC(upload_shells(S, ax, dax));
+        if (kpairs[i] < 0 || kpairs[i] >= P.L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    if (s0 < 0 || s1 > P.ax.nshell || s0 >= s1) return fail(RSGDF_EINVAL, "aux shell range is empty or out of bounds");
+    RC(derive_params(P.L, opts, P.omega, P.gm, t_err));
+    P.s0 = s0;
+    P.s1 = s1;
+    return RSGDF_OK;
+}
+
+// Plans and device buffers of a problem that passed j3c_check.
+static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int npair, const int *kpairs, int mode,
+                       unsigned long long *dcnt)
+{
+    const Lattice &L = P.L;
+    const HBasis &ao = P.ao, &ax = P.ax;
+    const int s0 = P.s0, s1 = P.s1;
+    const double omega = P.omega;
+    P.mode = mode;
+    P.nao = ao.nfunc;
+    P.pfunc0 = ax.foff[s0];
+    P.nP = (s1 < ax.nshell ? ax.foff[s1] : ax.nfunc) - P.pfunc0;
+    P.m = (long long)P.nP * P.nao * P.nao;
+    P.Nk = L.Nk;
+    const int Nk = P.Nk, nao = P.nao, nP = P.nP;
+    const long long m = P.m;
+    RC(upload_shells(S, ao, P.dao));
+    RC(upload_shells(S, ax, P.dax));
     double a9[9], bq[9];
     int nk3[3];
     fill_lattice(L, a9, bq, nk3);
-    double *da9;
-    int *dnk;
-    RC(S.upload(da9, std::vector<double>(a9, a9 + 9)));
-    RC(S.upload(dnk, std::vector<int>(nk3, nk3 + 3)));
+    RC(S.upload(P.da9, std::vector<double>(a9, a9 + 9)));
     std::vector<double> ph;
     phase_table(L, ph);
-    double *dph;
-    RC(S.upload(dph, ph));
     // k12 groups
     std::map<int, std::vector<int>> groups;
     for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
     std::vector<int> plist, pk2, goff;
-    std::vector<int> gkey;
+    P.gkey.clear();
     for (auto &kv : groups) {
         goff.push_back((int)plist.size());
-        gkey.push_back(kv.first);
+        P.gkey.push_back(kv.first);
         for (int p : kv.second) {
             plist.push_back(p);
             pk2.push_back(kpairs[2 * p + 1]);
         }
     }
     goff.push_back((int)plist.size());
-    int *dplist, *dpk2;
-    RC(S.upload(dplist, plist));
-    RC(S.upload(dpk2, pk2));
-    unsigned long long *dcnt;
-    RC(S.alloc(dcnt, 2 * LTOT_MAX + 6));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
-
+    RC(S.upload(P.dplist, plist));
+    RC(S.upload(P.dpk2, pk2));
+    RC(S.upload(P.dk12, P.gkey));
+    RC(S.upload(P.dgoff, goff));
+    P.fp32 = (opts->precision == RSGDF_MIXED) ? 1 : 0;
+    if (P.fp32) {
+        std::vector<float> ph32(ph.begin(), ph.end());
+        float *dph32;
+        RC(S.upload(dph32, ph32));
+        P.phk = dph32;
+    } else {
+        double *dph;
+        RC(S.upload(dph, ph));
+        P.phk = dph;
+    }
     // SR folded sums X[lt][dt][P][mu][nu]
-    double *X = nullptr;
-    SRPlan plan;
     if (mode & MODE_SR) {
-        plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, plan);
-        RC(S.alloc(X, (size_t)Nk * Nk * m));
-        CU(cudaMemsetAsync(X, 0, sizeof(double) * Nk * Nk * m, st));
+        plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, P.plan);
+        P.nlt = (P.gkey.size() == 1 && P.gkey[0] == 0) ? 1 : Nk;
+        RC(S.alloc(P.X, (size_t)P.nlt * Nk * m));
         SRExtras ex;
         if (opts->screening == RSGDF_SCREEN_LEARNED) {
             if (!opts->mlp) return fail(RSGDF_EINVAL, "learned screening needs opts->mlp");
@@ -483,9 +730,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
             if (ex.mlp->F != SR_NFEAT) return fail(RSGDF_EINVAL, "network input width does not match the SR features");
             ex.log10_cut = std::log10(opts->eps_screen) - 1.0;
         }
-        RC(run_sr(S, L, plan, dao, dax, ao, ax, omega, X, (long long)Nk * m, m, (long long)nao * nao, nao, 1, pfunc0,
-                  dcnt, st, nlaunch, ex));
-        t_stats.sr_items = plan.n_items;
+        RC(sr_setup(P.sr, S, L, P.plan, P.dao, P.dax, ao, ax, omega, P.X, P.nlt > 1 ? (long long)Nk * m : 0, m,
+                    (long long)nao * nao, nao, 1, P.pfunc0, dcnt, ex));
     }
     // AFT pair lists (also the overlaps of the G = 0 correction): entries
     // (pair, d, primitive pair) grouped by (pair, BvK cell of d)
@@ -514,146 +760,184 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
         }
         seg[(size_t)ao.nshell * ao.nshell * Nk] = (int)ent.size();
     }
-    PairEntry *dent;
-    int *dseg, *dalist;
-    double *ptab;
-    RC(S.upload(dent, ent));
-    RC(S.upload(dseg, seg));
-    RC(S.upload(dalist, alist));
-    RC(S.alloc(ptab, (size_t)tab_len));
-    float *ptab32 = nullptr;
-    float2 *uph = nullptr, *ph0 = nullptr;
-    double *db9 = nullptr;
-    const bool mixed_aft = (opts->precision == RSGDF_MIXED) && (mode & MODE_LR);
-    if (mixed_aft) {
+    RC(S.upload(P.dent, ent));
+    P.nent = (int)ent.size();
+    RC(S.upload(P.dseg, seg));
+    RC(S.upload(P.dalist, alist));
+    RC(S.alloc(P.ptab, (size_t)std::max(tab_len, 1LL)));
+    P.mixed_aft = (opts->precision == RSGDF_MIXED) && (mode & MODE_LR);
+    if (P.mixed_aft) {
         std::vector<double> b9v(9);
         for (int i = 0; i < 3; i++)
             for (int x = 0; x < 3; x++) b9v[3 * i + x] = L.b[i][x];
-        RC(S.upload(db9, b9v));
-        RC(S.alloc(ptab32, (size_t)tab_len));
-        RC(S.alloc(uph, 3 * ent.size()));
-        RC(S.alloc(ph0, ent.size()));
+        RC(S.upload(P.db9, b9v));
+        RC(S.alloc(P.ptab32, (size_t)std::max(tab_len, 1LL)));
+        RC(S.alloc(P.uph, 3 * ent.size() + 1));
+        RC(S.alloc(P.ph0, ent.size() + 1));
     }
-    t_timer.begin(PH_AFT);
-    RC(launch_pair_prep(dao, ao.nshell, dent, (int)ent.size(), dalist, da9, ptab, ptab32, db9, uph, st));
-    t_timer.end();
-    nlaunch++;
-    double *SP = nullptr, *Sf = nullptr;
-    const double g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
-    if ((mode & MODE_SR) && groups.count(0)) {
-        RC(S.alloc(SP, nP));
-        RC(S.alloc(Sf, (size_t)Nk * nao * nao));
-        t_timer.begin(PH_OTHER);
-        k_aux_charge<<<(s1 - s0 + 63) / 64, 64, 0, st>>>(dax, s0, s1, pfunc0, SP);
-        CU(cudaGetLastError());
-        RC(launch_ovlp_fold(dao, ao.nshell, nao, dent, dseg, ptab, Nk, Sf, st));
-        t_timer.end();
-        nlaunch += 2;
+    P.g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
+    P.g0 = (mode & MODE_SR) && groups.count(0);
+    if (P.g0) {
+        RC(S.alloc(P.SP, nP));
+        RC(S.alloc(P.Sf, (size_t)Nk * nao * nao));
     }
     // G-space data
     std::vector<int> gl;
-    gbox(gm, gl);
-    const int NG = (int)(gl.size() / 3);
-    int *dg = nullptr;
-    double *W = nullptr, *Y = nullptr;
-    float *Apl = nullptr, *Bpl = nullptr;
+    gbox(P.gm, gl);
+    P.NG = (int)(gl.size() / 3);
+    const int NG = P.NG;
     if (mode & MODE_LR) {
-        RC(S.upload(dg, gl));
-        RC(S.alloc(W, (size_t)2 * NG * nP));
+        RC(S.upload(P.dg, gl));
+        RC(S.alloc(P.W, (size_t)2 * NG * nP));
         if (opts->precision == RSGDF_MIXED) {
             // split-TF32 operand tiles; the padding of B' stays zero for every k12
-            RC(S.alloc(Apl, (size_t)tc_a_floats(nP, NG)));
-            const long long nb = tc_b_floats(nao * nao, NG, Nk);
-            RC(S.alloc(Bpl, (size_t)nb));
-            CU(cudaMemsetAsync(Bpl, 0, sizeof(float) * nb, st));
+            RC(S.alloc(P.Apl, (size_t)tc_a_floats(nP, NG)));
+            P.nbpl = tc_b_floats(nao * nao, NG, Nk);
+            RC(S.alloc(P.Bpl, (size_t)P.nbpl));
         } else {
-            RC(S.alloc(Y, (size_t)2 * Nk * NG * nao * nao));
+            RC(S.alloc(P.Y, (size_t)2 * Nk * NG * nao * nao));
+        }
+        P.garg.clear();
+        for (int k12 : P.gkey) {
+            GArgs Ga;
+            memset(&Ga, 0, sizeof(Ga));
+            Ga.g = P.dg;
+            Ga.NG = NG;
+            for (int i = 0; i < 3; i++)
+                for (int x = 0; x < 3; x++) Ga.b[3 * i + x] = L.b[i][x];
+            k12_frac(L, k12, Ga.f12);
+            Ga.vol = L.vol;
+            Ga.omega = omega;
+            P.garg.push_back(Ga);
         }
     }
     // k12 groups in batches whose T fits a fixed budget
-    const int G = (int)gkey.size();
+    const int G = (int)P.gkey.size();
     const long long tbytes = (long long)Nk * m * 16;
-    int B = (int)std::max(1LL, std::min<long long>(G, (4LL << 30) / std::max(tbytes, 1LL)));
-    double *T;
-    RC(S.alloc(T, (size_t)2 * B * Nk * m));
-    int *dk12, *dgoff;
-    RC(S.upload(dk12, gkey));
-    RC(S.upload(dgoff, goff));
-    const int fp32 = (opts->precision == RSGDF_MIXED) ? 1 : 0;
-    const void *phk = dph;
-    if (fp32) {
-        std::vector<float> ph32(ph.begin(), ph.end());
-        float *dph32;
-        RC(S.upload(dph32, ph32));
-        phk = dph32;
+    P.B = (int)std::max(1LL, std::min<long long>(G, (4LL << 30) / std::max(tbytes, 1LL)));
+    RC(S.alloc(P.T, (size_t)2 * P.B * Nk * m));
+    P.aft_units = (mode & MODE_LR) ? (long long)ent.size() * NG * (long long)G : 0;
+    P.lr_flops = (mode & MODE_LR) ? 8LL * nP * nao * nao * NG * Nk * (long long)G : 0;
+    return RSGDF_OK;
+}
+
+// Before the SR class launches: zero X, pair tables, learned screen.
+static int j3c_exec_pre(J3cProblem &P, cudaStream_t st, int &nl)
+{
+    if (!(P.mode & MODE_SR)) return RSGDF_OK;
+    CU(cudaMemsetAsync(P.X, 0, sizeof(double) * P.nlt * P.Nk * P.m, st));
+    return sr_pre(P.sr, st, nl);
+}
+
+// After the SR class launches: G = 0 pieces, phases, AFT, LR contraction.
+static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
+{
+    const int Nk = P.Nk, nao = P.nao, nP = P.nP, NG = P.NG;
+    const long long m = P.m;
+    t_timer.begin(PH_AFT);
+    RC(launch_pair_prep(P.dao, P.ao.nshell, P.dent, P.nent, P.dalist, P.da9, P.ptab, P.ptab32, P.db9, P.uph, st));
+    t_timer.end();
+    nl++;
+    if (P.g0) {
+        t_timer.begin(PH_OTHER);
+        k_aux_charge<<<(P.s1 - P.s0 + 63) / 64, 64, 0, st>>>(P.dax, P.s0, P.s1, P.pfunc0, P.SP);
+        CU(cudaGetLastError());
+        RC(launch_ovlp_fold(P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Sf, st));
+        t_timer.end();
+        nl += 2;
     }
-    long long aft_units = 0;
-    for (int gb0 = 0; gb0 < G; gb0 += B) {
-        const int nb = std::min(B, G - gb0);
-        if (mode & MODE_SR) {
+    if (P.Bpl) CU(cudaMemsetAsync(P.Bpl, 0, sizeof(float) * P.nbpl, st));
+    const int G = (int)P.gkey.size();
+    for (int gb0 = 0; gb0 < G; gb0 += P.B) {
+        const int nb = std::min(P.B, G - gb0);
+        if (P.mode & MODE_SR) {
             t_timer.begin(PH_PHASE);
-            RC(launch_phase1_multi(X, m, Nk, dk12 + gb0, nb, phk, T, fp32, st));
-            nlaunch++;
+            RC(launch_phase1_multi(P.X, m, Nk, P.nlt, P.dk12 + gb0, nb, P.phk, P.T, P.fp32, st));
+            nl++;
             for (int j = 0; j < nb; j++)
-                if (gkey[gb0 + j] == 0) {
-                    RC(launch_g0_fold(T + (size_t)2 * j * Nk * m, m, Nk, nP, nao, SP, Sf, g0fac, st));
-                    nlaunch++;
+                if (P.gkey[gb0 + j] == 0) {
+                    RC(launch_g0_fold(P.T + (size_t)2 * j * Nk * m, m, Nk, nP, nao, P.SP, P.Sf, P.g0fac, st));
+                    nl++;
                 }
             t_timer.end();
         } else {
-            CU(cudaMemsetAsync(T, 0, sizeof(double) * 2 * nb * Nk * m, st));
+            CU(cudaMemsetAsync(P.T, 0, sizeof(double) * 2 * nb * Nk * m, st));
         }
-        if (mode & MODE_LR) {
+        if (P.mode & MODE_LR) {
             for (int j = 0; j < nb; j++) {
-                const int k12 = gkey[gb0 + j];
-                double *Tj = T + (size_t)2 * j * Nk * m;
-                GArgs Ga;
-                memset(&Ga, 0, sizeof(Ga));
-                Ga.g = dg;
-                Ga.NG = NG;
-                for (int i = 0; i < 3; i++)
-                    for (int x = 0; x < 3; x++) Ga.b[3 * i + x] = L.b[i][x];
-                k12_frac(L, k12, Ga.f12);
-                Ga.vol = L.vol;
-                Ga.omega = omega;
+                const GArgs &Ga = P.garg[gb0 + j];
+                double *Tj = P.T + (size_t)2 * j * Nk * m;
                 t_timer.begin(PH_AFT);
-                RC(launch_aux_ft(Ga, dax, s0, s1, pfunc0, nP, W, nullptr, st));
-                if (mixed_aft) {
-                    RC(launch_split_a(nP, NG, W, Apl, st));
-                    RC(launch_aft_f32(Ga, dao, ao.nshell, nao, dent, (int)ent.size(), dseg, ptab, ptab32, db9, uph, ph0,
-                                      Nk, Bpl, st));
+                RC(launch_aux_ft(Ga, P.dax, P.s0, P.s1, P.pfunc0, nP, P.W, nullptr, st));
+                if (P.mixed_aft) {
+                    RC(launch_split_a(nP, NG, P.W, P.Apl, st));
+                    RC(launch_aft_f32(Ga, P.dao, P.ao.nshell, nao, P.dent, P.nent, P.dseg, P.ptab, P.ptab32, P.db9,
+                                      P.uph, P.ph0, Nk, P.Bpl, st));
                 } else {
-                    RC(launch_aft(Ga, dao, ao.nshell, nao, dent, dseg, ptab, Nk, Y, st));
+                    RC(launch_aft(Ga, P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Y, st));
                 }
                 t_timer.end();
                 t_timer.begin(PH_GEMM);
-                if (mixed_aft)
-                    RC(launch_zgemm_tc2(nP, nao * nao, NG, Nk, Apl, Bpl, Tj, 2 * m, st));
+                if (P.mixed_aft)
+                    RC(launch_zgemm_tc2(nP, nao * nao, NG, Nk, P.Apl, P.Bpl, Tj, 2 * m, st));
                 else
-                    RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, W, Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
+                    RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, P.W, P.Y, (long long)2 * NG * nao * nao, Tj, 2 * m,
+                                       st));
                 t_timer.end();
-                nlaunch += 3;
+                nl += 3;
             }
         }
         t_timer.begin(PH_PHASE);
-        RC(launch_phase2_multi(T, m, Nk, dgoff + gb0, nb, dplist, dpk2, phk, V, (mode == MODE_LR) ? 1 : 0, fp32, st));
+        RC(launch_phase2_multi(P.T, m, Nk, P.dgoff + gb0, nb, P.dplist, P.dpk2, P.phk, V,
+                               (P.mode == MODE_LR) ? 1 : 0, P.fp32, st));
         t_timer.end();
-        nlaunch++;
-    }
-    if (mode & MODE_LR) {
-        aft_units = (long long)ent.size() * NG * (long long)gkey.size();
+        nl++;
     }
     CU(cudaGetLastError());
-    // statistics
+    return RSGDF_OK;
+}
+
+static int stats_counts(unsigned long long *dcnt, cudaStream_t st)
+{
     if (!t_count_host) CU(cudaMallocHost(&t_count_host, sizeof(unsigned long long) * (2 * LTOT_MAX + 6)));
     CU(cudaMemcpyAsync(t_count_host, dcnt, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), cudaMemcpyDeviceToHost, st));
     t_count_valid = true;
     t_stats_stream = st;
-    t_stats.omega = omega;
-    for (int i = 0; i < 3; i++) t_stats.gmesh[i] = gm[i];
-    t_stats.aft_units = aft_units;
-    t_stats.lr_flops = (mode & MODE_LR) ? 8LL * nP * nao * nao * NG * Nk * (long long)gkey.size() : 0;
-    t_stats.n_launch = nlaunch;
+    return RSGDF_OK;
+}
+
+static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in,
+                    const rsgdf_opts *opts, int npair, const int *kpairs, int s0, int s1, double *V, int mode)
+{
+    t_err.clear();
+    memset(&t_stats, 0, sizeof(t_stats));
+    t_count_valid = false;
+    J3cProblem P;
+    RC(j3c_check(P, cell, ao_in, aux_in, opts, npair, kpairs, s0, s1));
+    if (!V) return fail(RSGDF_EINVAL, "V_out is NULL");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    RC(ensure_boys(st));
+    t_timer.reset(st);
+    Scratch S(st);
+    unsigned long long *dcnt, *dq;
+    RC(S.alloc(dcnt, 2 * LTOT_MAX + 6));
+    RC(S.alloc(dq, LTOT_MAX + 1));
+    RC(j3c_prepare(P, S, opts, npair, kpairs, mode, dcnt));
+    std::vector<SRClassLaunch> cl;
+    if (mode & MODE_SR) RC(sr_merge({&P.sr}, S, st, cl));
+    int nl = 0;
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
+    RC(j3c_exec_pre(P, st, nl));
+    RC(sr_run(cl, dq, st, nl));
+    RC(j3c_exec_post(P, V, st, nl));
+    RC(stats_counts(dcnt, st));
+    t_stats.sr_items = P.plan.n_items;
+    t_stats.omega = P.omega;
+    for (int i = 0; i < 3; i++) t_stats.gmesh[i] = P.gm[i];
+    t_stats.aft_units = P.aft_units;
+    t_stats.lr_flops = P.lr_flops;
+    t_stats.n_launch = nl;
     return RSGDF_OK;
 }
 
@@ -739,9 +1023,216 @@ static int kphase_noalloc_impl(const rsgdf_cell *cell, const double *X, long lon
 
 }  // namespace rsgdf
 
+struct rsgdf_batch {
+    int nprob = 0;
+    int flags = 0;
+    cudaStream_t st0 = nullptr;   // stream of the allocations
+    std::unique_ptr<rsgdf::Scratch> S;
+    std::vector<std::unique_ptr<rsgdf::J3cProblem>> probs;
+    std::vector<rsgdf::SRClassLaunch> cl;
+    unsigned long long *dcnt = nullptr, *dq = nullptr;
+    bool tuned = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double *> graph_V;
+    int graph_nl = 0;
+    cudaStream_t own = nullptr;   // capture stream when the caller passes the legacy stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    long long n_items = 0, aft_units = 0, lr_flops = 0;
+};
+
+namespace rsgdf {
+
+static int batch_exec(rsgdf_batch *b, double *const *V, cudaStream_t st, int &nl)
+{
+    CU(cudaMemsetAsync(b->dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
+    for (auto &P : b->probs) RC(j3c_exec_pre(*P, st, nl));
+    RC(sr_run(b->cl, b->dq, st, nl));
+    for (int p = 0; p < b->nprob; p++) RC(j3c_exec_post(*b->probs[p], V[p], st, nl));
+    return RSGDF_OK;
+}
+
+static void batch_drop_graph(rsgdf_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_V.clear();
+}
+
+}  // namespace rsgdf
+
 using namespace rsgdf;
 
 extern "C" {
+
+int rsgdf_j3c_batch_create(int nprob, const rsgdf_problem *probs, const rsgdf_opts *opts, const int *npair,
+                           const int *kpairs, int flags, rsgdf_batch **out)
+{
+    t_err.clear();
+    if (!out || nprob < 1 || !probs || !npair || !kpairs) return fail(RSGDF_EINVAL, "bad batch argument");
+    if (flags & ~(RSGDF_BATCH_GRAPH | RSGDF_BATCH_AUTOTUNE)) return fail(RSGDF_EINVAL, "unknown batch flag");
+    *out = nullptr;
+    RC(check_opts(opts));
+    std::unique_ptr<rsgdf_batch> b(new rsgdf_batch());
+    b->nprob = nprob;
+    b->flags = flags;
+    long long koff = 0;
+    for (int p = 0; p < nprob; p++) {
+        if (!probs[p].cell || !probs[p].ao || !probs[p].aux) return fail(RSGDF_EINVAL, "NULL member in probs");
+        if (npair[p] < 1) return fail(RSGDF_EINVAL, "every cell needs at least one k pair");
+        std::unique_ptr<J3cProblem> P(new J3cProblem());
+        const int r = j3c_check(*P, probs[p].cell, probs[p].ao, probs[p].aux, opts, npair[p], kpairs + 2 * koff, 0,
+                                probs[p].aux->nshell);
+        if (r != RSGDF_OK) {
+            t_err = "cell " + std::to_string(p) + ": " + t_err;
+            return r;
+        }
+        koff += npair[p];
+        b->probs.push_back(std::move(P));
+    }
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    RC(ensure_boys(st));
+    b->st0 = st;
+    b->S.reset(new Scratch(st));
+    RC(b->S->alloc(b->dcnt, 2 * LTOT_MAX + 6));
+    RC(b->S->alloc(b->dq, LTOT_MAX + 1));
+    koff = 0;
+    std::vector<const SRSetup *> rs;
+    for (int p = 0; p < nprob; p++) {
+        J3cProblem &P = *b->probs[p];
+        const int r = j3c_prepare(P, *b->S, opts, npair[p], kpairs + 2 * koff, MODE_SR | MODE_LR, b->dcnt);
+        if (r != RSGDF_OK) {
+            t_err = "cell " + std::to_string(p) + ": " + t_err;
+            return r;
+        }
+        koff += npair[p];
+        b->n_items += P.plan.n_items;
+        b->aft_units += P.aft_units;
+        b->lr_flops += P.lr_flops;
+    }
+    for (auto &P : b->probs) rs.push_back(&P->sr);
+    RC(sr_merge(rs, *b->S, st, b->cl));
+    CU(cudaStreamSynchronize(st));
+    *out = b.release();
+    return RSGDF_OK;
+}
+
+int rsgdf_j3c_batch_run(rsgdf_batch *b, double *const *V_out, void *stream)
+{
+    t_err.clear();
+    memset(&t_stats, 0, sizeof(t_stats));
+    t_count_valid = false;
+    if (!b || !V_out) return fail(RSGDF_EINVAL, "bad batch argument");
+    for (int p = 0; p < b->nprob; p++)
+        if (!V_out[p]) return fail(RSGDF_EINVAL, "V_out has a NULL entry");
+    cudaStream_t st = (cudaStream_t)stream;
+    int nl = 0;
+    if ((b->flags & RSGDF_BATCH_AUTOTUNE) && !b->tuned) {
+        t_timer.reset(st);
+        t_timer.on = false;
+        for (auto &P : b->probs) RC(j3c_exec_pre(*P, st, nl));
+        RC(sr_tune(b->cl, b->dq, st, nullptr));
+        b->tuned = true;
+        batch_drop_graph(b);
+        nl = 0;
+    }
+    if (b->flags & RSGDF_BATCH_GRAPH) {
+        cudaStream_t cs = st;
+        if (st == nullptr) {
+            if (!b->own) {
+                CU(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
+                CU(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+                CU(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+            }
+            cs = b->own;
+        }
+        bool same = b->exec && (int)b->graph_V.size() == b->nprob;
+        for (int p = 0; same && p < b->nprob; p++) same = (b->graph_V[p] == V_out[p]);
+        if (!same) {
+            batch_drop_graph(b);
+            t_timer.reset(cs);
+            t_timer.on = false;
+            CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+            int r = batch_exec(b, V_out, cs, nl);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (r != RSGDF_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            if (e != cudaSuccess) return fail(RSGDF_EDEVICE, std::string("graph capture: ") + cudaGetErrorString(e));
+            b->graph = g;
+            CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+            b->graph_V.assign(V_out, V_out + b->nprob);
+            b->graph_nl = nl;
+        }
+        if (cs != st) {
+            CU(cudaEventRecord(b->ev_in, st));
+            CU(cudaStreamWaitEvent(cs, b->ev_in, 0));
+        }
+        CU(cudaGraphLaunch(b->exec, cs));
+        if (cs != st) {
+            CU(cudaEventRecord(b->ev_out, cs));
+            CU(cudaStreamWaitEvent(st, b->ev_out, 0));
+        }
+        nl = b->graph_nl;
+    } else {
+        t_timer.reset(st);
+        RC(batch_exec(b, V_out, st, nl));
+    }
+    RC(stats_counts(b->dcnt, st));
+    t_stats.sr_items = b->n_items;
+    t_stats.aft_units = b->aft_units;
+    t_stats.lr_flops = b->lr_flops;
+    t_stats.n_launch = nl;
+    return RSGDF_OK;
+}
+
+int rsgdf_j3c_batch_tiles(const rsgdf_batch *b, int *grid, int *bc, int *grab)
+{
+    t_err.clear();
+    if (!b) return fail(RSGDF_EINVAL, "NULL batch");
+    for (int L = 0; L <= LTOT_MAX; L++) {
+        if (grid) grid[L] = 0;
+        if (bc) bc[L] = 0;
+        if (grab) grab[L] = 0;
+    }
+    for (const SRClassLaunch &c : b->cl) {
+        if (grid) grid[c.L] = c.grid;
+        if (bc) bc[c.L] = c.bc;
+        if (grab) grab[c.L] = c.grab;
+    }
+    return RSGDF_OK;
+}
+
+int rsgdf_j3c_batch_destroy(rsgdf_batch *b)
+{
+    if (!b) return RSGDF_OK;
+    cudaDeviceSynchronize();   // runs may be on any stream; the frees below are ordered on the allocation stream
+    batch_drop_graph(b);
+    if (b->own) {
+        cudaStreamSynchronize(b->own);
+        cudaStreamDestroy(b->own);
+    }
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    b->S.reset();   // stream-ordered frees on the allocation stream
+    delete b;
+    return RSGDF_OK;
+}
+
+int rsgdf_j3c_batch(int nprob, const rsgdf_problem *probs, const rsgdf_opts *opts, const int *npair,
+                    const int *kpairs, double *const *V_out)
+{
+    rsgdf_batch *b = nullptr;
+    RC(rsgdf_j3c_batch_create(nprob, probs, opts, npair, kpairs, 0, &b));
+    const int r = rsgdf_j3c_batch_run(b, V_out, opts->stream);
+    rsgdf_j3c_batch_destroy(b);
+    return r;
+}
 
 int rsgdf_j3c_sr(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux, const rsgdf_opts *opts,
                  int npair, const int *kpairs, int s0, int s1, double *V_out)

@@ -82,7 +82,12 @@ __device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int 
 }
 
 int upload_boys_table(const double *tab, cudaStream_t st);
-int launch_sr(int L, SRArgs args, int ncomp_max, int w_max, int list_max, cudaStream_t st);
+int sr_default_bc(int L, int ncomp_max, int w_max);
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max);
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max);
+int sr_occupancy(int L, size_t smem);
+int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot, size_t warp_bytes,
+                    unsigned long long *queue, int grid, int grab, cudaStream_t st);
 __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S);
 __host__ __device__ void single_E(int lc, double g, double *E);
 __global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,
@@ -188,7 +193,7 @@ long long tc_b_floats(int N, int K, int batch);
 long long tc_a_floats(int M, int K);
 int tc_status_take(int *flag);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
-int launch_phase1_multi(const double *X, long long m, int Nk, const int *k12list, int nk12, const void *ph,
+int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
                         double *T, int fp32, cudaStream_t st);
 int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,
                         const int *pk2, const void *ph, double *V, int accumulate, int fp32, cudaStream_t st);

@@ -735,7 +735,7 @@ template <> struct PhT<double> { typedef double2 type; enum { KB = 8, PB = 8 }; 
 template <> struct PhT<float> { typedef float2 type; enum { KB = 16, PB = 16 }; };
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__ X, long long m, int Nk,
+__global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__ X, long long m, int Nk, int nlt,
                                                       const int *__restrict__ k12list, int nk12,
                                                       const typename PhT<R>::type *__restrict__ ph,
                                                       double2 *__restrict__ T)
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__
             R ar[KB], ai[KB];
 #pragma unroll
             for (int j = 0; j < KB; j++) { ar[j] = 0; ai[j] = 0; }
-            for (int lt = 0; lt < Nk; lt++) {
+            for (int lt = 0; lt < nlt; lt++) {
                 const R x = (R)X[((long long)lt * Nk + dt) * m + i];
 #pragma unroll
                 for (int j = 0; j < KB; j++) {
@@ -820,14 +820,16 @@ static int grid_for(long long n)
     return (int)(g < 1 ? 1 : g);
 }
 
-int launch_phase1_multi(const double *X, long long m, int Nk, const int *k12list, int nk12, const void *ph,
+int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
                         double *T, int fp32, cudaStream_t st)
 {
     const long long n = (long long)Nk * m;
     if (fp32)
-        k_phase1_multi<float><<<grid_for(n), 256, 0, st>>>(X, m, Nk, k12list, nk12, (const float2 *)ph, (double2 *)T);
+        k_phase1_multi<float><<<grid_for(n), 256, 0, st>>>(X, m, Nk, nlt, k12list, nk12, (const float2 *)ph,
+                                                            (double2 *)T);
     else
-        k_phase1_multi<double><<<grid_for(n), 256, 0, st>>>(X, m, Nk, k12list, nk12, (const double2 *)ph, (double2 *)T);
+        k_phase1_multi<double><<<grid_for(n), 256, 0, st>>>(X, m, Nk, nlt, k12list, nk12, (const double2 *)ph,
+                                                             (double2 *)T);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

@@ -20,6 +20,8 @@
 #include <cstdint>
 #include <cstdint>
 
+#include <algorithm>
+
 #include "k_common.cuh"
 #include "rsgdf_internal.h"
 
@@ -179,16 +181,14 @@ __device__ __forceinline__ void tuv_of(int p, int &t, int &u, int &v)
     t = S - w;
 }
 
+// One SR work item (aux shell, AO shell pair, d) by one warp; base is the
+// warp's shared-memory region (laid out from A's bc, ncomp_max, w_max and
+// list_max).  Every branch on the item is warp-uniform.
 template <int L>
-__global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
+__device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item, const int lane, unsigned char *base)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long item = A.item_begin + (long long)blockIdx.x * SR_WARPS + warp;
-    if (item >= A.item_end) return;  // warp-uniform
     if (A.item_skip && A.item_skip[item]) return;   // pruned by the learned screen (warp-uniform)
     constexpr int NR = ntuv(L);
-    unsigned char *base = smem_raw + (size_t)warp * A.warp_bytes;
     double *Tx = (double *)base;            // collected translations (Cartesian)
     double *Ty = Tx + SR_NT, *Tz = Ty + SR_NT;
     double *Sx = Tz + SR_NT, *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
@@ -514,34 +514,80 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(SRArgs A)
     }
 }
 
-typedef void (*SRKern)(SRArgs);
+// Persistent SR kernel of one angular-momentum class: the work items of
+// ndesc problems (one SRArgs descriptor each; descriptor i owns the queue
+// positions [cum[i], cum[i+1]) and maps them onto its items from
+// item_begin) are drawn by warps from one queue, grab items per atomic.
+// Descriptors of one launch share bc, ncomp_max, w_max and list_max, so all
+// warps carve shared memory alike.
+template <int L>
+__global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(const SRArgs *__restrict__ desc, const long long *__restrict__ cum,
+                                                        int ndesc, int warp_bytes, unsigned long long *queue, int grab)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *base = smem_raw + (size_t)warp * warp_bytes;
+    const long long ntot = cum[ndesc];
+    for (;;) {
+        unsigned long long g0 = 0;
+        if (lane == 0) g0 = atomicAdd(queue, (unsigned long long)grab);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        if ((long long)g0 >= ntot) break;   // warp-uniform; the queue only grows
+        for (int j = 0; j < grab; j++) {
+            const long long g = (long long)g0 + j;
+            if (g >= ntot) break;
+            int lo = 0, hi = ndesc - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cum[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            sr3c_item<L>(desc[lo], desc[lo].item_begin + (g - cum[lo]), lane, base);
+            __syncwarp();
+        }
+    }
+}
+
+typedef void (*SRKern)(const SRArgs *, const long long *, int, int, unsigned long long *, int);
 static SRKern sr_kernels[LTOT_MAX + 1] = {k_sr3c<0>, k_sr3c<1>, k_sr3c<2>, k_sr3c<3>, k_sr3c<4>,
                                           k_sr3c<5>, k_sr3c<6>, k_sr3c<7>, k_sr3c<8>, k_sr3c<9>};
 
-int launch_sr(int L, SRArgs args, int ncomp_max, int w_max, int list_max, cudaStream_t st)
+// bin chunk (BvK cells of the aux image held at once) for a class
+int sr_default_bc(int L, int ncomp_max, int w_max)
 {
-    long long n = args.item_end - args.item_begin;
-    if (n <= 0) return RSGDF_OK;
     int bc = 4096 / (ntuv(L) + ncomp_max + w_max);
-    bc = bc < 1 ? 1 : (bc > 16 ? 16 : bc);
-    args.bc = bc;
-    args.ncomp_max = ncomp_max;
-    args.w_max = w_max;
-    args.list_max = list_max;
-    size_t wb = sr_warp_bytes(L, bc, ncomp_max, w_max, list_max);
-    args.warp_bytes = (int)wb;
-    size_t smem = wb * SR_WARPS;
+    return bc < 1 ? 1 : (bc > 16 ? 16 : bc);
+}
+
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max)
+{
+    return sr_warp_bytes(L, bc, ncomp_max, w_max, list_max) * SR_WARPS;
+}
+
+// Resident CTAs per SM of the class-L kernel with the given dynamic shared memory.
+int sr_occupancy(int L, size_t smem)
+{
+    if (cudaFuncSetAttribute(sr_kernels[L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sr_kernels[L], SR_WARPS * 32, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+// Launch of the class-L kernel over descriptors already on the device.  The
+// queue counter is reset on the stream first.  grid = CTAs (persistent).
+int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot, size_t warp_bytes,
+                    unsigned long long *queue, int grid, int grab, cudaStream_t st)
+{
+    if (ntot <= 0) return RSGDF_OK;
+    if (L < 0 || L > LTOT_MAX || grid < 1 || grab < 1) return RSGDF_EINVAL;
+    const size_t smem = warp_bytes * SR_WARPS;
     if (cudaFuncSetAttribute(sr_kernels[L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSGDF_EDEVICE;
-    long long grid = (n + SR_WARPS - 1) / SR_WARPS;
-    while (grid > 0) {
-        long long g = grid > 2000000000LL ? 2000000000LL : grid;
-        sr_kernels[L]<<<(unsigned)g, SR_WARPS * 32, smem, st>>>(args);
-        if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
-        args.item_begin += g * SR_WARPS;
-        grid -= g;
-    }
-    return RSGDF_OK;
+    if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return RSGDF_EDEVICE;
+    const long long need = (ntot + (long long)SR_WARPS * grab - 1) / ((long long)SR_WARPS * grab);
+    const int g = (int)std::min<long long>(grid, need);
+    sr_kernels[L]<<<g, SR_WARPS * 32, smem, st>>>(ddesc, dcum, ndesc, (int)warp_bytes, queue, grab);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
 // single-centre Gaussian x^c e^{-g x^2}: E[c*(LMAX+1) + tau]

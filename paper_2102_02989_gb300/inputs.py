@@ -168,9 +168,13 @@ def config5() -> Problem:
 
 
 def config4(ncell=32) -> list:
-    """32 heterogeneous cells: 1-8 atoms, cubic or FCC lattices with a in
-    U[5, 10] Bohr, 1-3 random AO shells per l <= 3 per atom, an ETB aux of
-    about 3x the AO count with l <= 3, k-meshes from 1x1x1 to 3x3x3."""
+    """32 heterogeneous cells: 1-8 atoms at random positions (at most one
+    per 40 Bohr^3, at least 1.5 Bohr apart), cubic or FCC lattices with a in
+    U[5, 10] Bohr; per atom 2-4 random AO shells (an s
+    shell plus shells of random l <= 3, 1-2 primitives, exponents
+    log-uniform in [0.15, 50]); an ETB aux set (from 0.25, beta 2.0, l <= 3)
+    of about 3x the AO count; k-meshes from 1x1x1 to 3x3x3.  The batched j3c
+    covers the diagonal k pairs (k, k) of each cell."""
     rng = np.random.default_rng(SEED_BASE + 4)
     probs = []
     for ic in range(ncell):
@@ -178,13 +182,23 @@ def config4(ncell=32) -> list:
         A = float(rng.uniform(5.0, 10.0))
         fcc = bool(rng.integers(0, 2))
         a = fcc_cell(A) if fcc else A * np.eye(3)
-        frac = rng.uniform(0, 1, size=(natm, 3))
-        atoms = frac @ a
+        # at least 40 Bohr^3 per atom (solid-state densities) and 1.5 Bohr
+        # between atoms, periodic images included
+        natm = max(1, min(natm, int(abs(np.linalg.det(a)) // 40.0)))
+        atoms = []
+        img = np.array([(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]) @ a
+        while len(atoms) < natm:
+            c = rng.uniform(0, 1, size=3) @ a
+            if all(np.min(np.linalg.norm(c - (b + img), axis=1)) >= 1.5 for b in atoms):
+                atoms.append(c)
+        atoms = np.array(atoms)
         ao, aux = [], []
         for c in atoms:
-            spec = tuple((l, tuple([1] * int(rng.integers(1, 4)))) for l in range(4))
+            nsh = int(rng.integers(2, 5))
+            ls = [0] + [int(rng.integers(0, 4)) for _ in range(nsh - 1)]
+            spec = tuple((l, (int(rng.integers(1, 3)),)) for l in sorted(ls))
             ao += _random_ao_atom(rng, c, spec=spec, lo=0.15, hi=50.0)
-        nao = sum((s[0] + 1) * (s[0] + 2) // 2 for s in ao)
+        nao = sum((s_[0] + 1) * (s_[0] + 2) // 2 for s_ in ao)
         per_atom = max(1, int(round(3 * nao / natm)))
         for c in atoms:
             counts = [0, 0, 0, 0]
@@ -198,6 +212,10 @@ def config4(ncell=32) -> list:
         probs.append(Problem("batch cell %d" % ic, a, (n, n, n), make_basis(ao), make_basis(aux),
                              None, (7, 7, 7), 1e-8, 1e-8, atoms))
     return probs
+
+
+def kpairs_diag(nk: int) -> np.ndarray:
+    return np.array([(i, i) for i in range(nk)], dtype=np.int32)
 
 
 def tiny(kmesh=(1, 1, 1), lmax_ao=1, lmax_aux=2, seed=7, a=3.2, natm=1) -> Problem:

@@ -21,13 +21,15 @@ _lib = None
 RSGDF_OK, RSGDF_EINVAL, RSGDF_ENOMEM, RSGDF_ENOTPD, RSGDF_ETIMEOUT, RSGDF_EDEVICE, RSGDF_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 RSGDF_FP64, RSGDF_MIXED = 0, 1
 RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
+RSGDF_BATCH_GRAPH, RSGDF_BATCH_AUTOTUNE = 1, 2
 
 # names exported by the library (every declaration of include/rsgdf.h)
 EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase", "rsgdf_kphase_noalloc",
            "rsgdf_last_stats", "rsgdf_params", "rsgdf_last_error", "rsgdf_probe_fp64", "rsgdf_sync_status",
            "rsgdf_mlp_nparams", "rsgdf_mlp_create", "rsgdf_mlp_destroy", "rsgdf_mlp_get_params",
            "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
-           "rsgdf_sr_items")
+           "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
+           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -51,6 +53,10 @@ class _Opts(C.Structure):
     _fields_ = [("omega", C.c_double), ("gmesh", C.c_int * 3), ("eps_screen", C.c_double),
                 ("eps_lr", C.c_double), ("precision", C.c_int), ("screening", C.c_int),
                 ("mlp", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("cell", C.c_void_p), ("ao", C.c_void_p), ("aux", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -111,6 +117,11 @@ def load():
         lib.rsgdf_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         lib.rsgdf_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, i, i, C.c_float, C.c_float, C.c_uint, vp, vp]
         lib.rsgdf_sr_items.argtypes = [vp, vp, vp, vp, i, i, vp, vp, vp]
+        lib.rsgdf_j3c_batch_create.argtypes = [i, vp, vp, vp, vp, i, vp]
+        lib.rsgdf_j3c_batch_run.argtypes = [vp, vp, vp]
+        lib.rsgdf_j3c_batch_destroy.argtypes = [vp]
+        lib.rsgdf_j3c_batch_tiles.argtypes = [vp, vp, vp, vp]
+        lib.rsgdf_j3c_batch.argtypes = [i, vp, vp, vp, vp, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -152,6 +163,8 @@ def _cell(a, kmesh):
 
 def _stream_ptr(stream):
     import torch
+    if stream is None and not torch.cuda.is_available():
+        return C.c_void_p(0)   # host-only calls (planning); device calls fail with RSGDF_EDEVICE
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
 
@@ -377,3 +390,87 @@ def rsgdf_sr_items(a, kmesh, ao, aux, shells=None, features=True, magnitudes=Fal
                                   C.c_void_p(feat.data_ptr()) if feat is not None else None,
                                   C.c_void_p(mag.data_ptr()) if mag is not None else None))
     return nn, feat, mag
+
+
+class Batch:
+    """Handle of a batched j3c over many cells (plans and device buffers kept;
+    runs issue kernels only, optionally replaying a captured CUDA graph).
+    problems: list of (a, kmesh, ao, aux); kpairs: list of [npair][2] arrays."""
+
+    def __init__(self, problems, kpairs, flags=0, **opt):
+        lib = load()
+        self.cells = [_cell(a, km) for (a, km, _, _) in problems]
+        self.refs = [(_BasisRef(ao), _BasisRef(aux)) for (_, _, ao, aux) in problems]
+        self.kp = [np.ascontiguousarray(np.asarray(k, dtype=np.int32).reshape(-1, 2)) for k in kpairs]
+        n = len(problems)
+        self.pr = (_Problem * n)()
+        for p in range(n):
+            self.pr[p].cell = C.cast(C.pointer(self.cells[p]), C.c_void_p)
+            self.pr[p].ao = C.cast(C.pointer(self.refs[p][0].s), C.c_void_p)
+            self.pr[p].aux = C.cast(C.pointer(self.refs[p][1].s), C.c_void_p)
+        npair = np.array([len(k) for k in self.kp], dtype=np.int32)
+        kcat = np.ascontiguousarray(np.concatenate(self.kp).reshape(-1))
+        self.opts = _opts(**opt)
+        h = C.c_void_p()
+        _check(lib.rsgdf_j3c_batch_create(n, C.cast(self.pr, C.c_void_p), C.byref(self.opts),
+                                          npair.ctypes.data_as(C.c_void_p), kcat.ctypes.data_as(C.c_void_p),
+                                          int(flags), C.byref(h)))
+        self.h = h
+        self.shapes = [(len(self.kp[p]), self.refs[p][1].nfunc, self.refs[p][0].nfunc, self.refs[p][0].nfunc)
+                       for p in range(n)]
+
+    def outputs(self):
+        import torch
+        return [torch.zeros(s, dtype=torch.complex128, device="cuda") for s in self.shapes]
+
+    def run(self, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = self.outputs()
+        for o, s in zip(outs, self.shapes):
+            assert o.is_cuda and o.dtype == torch.complex128 and tuple(o.shape) == s and o.is_contiguous()
+        ptrs = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        _check(load().rsgdf_j3c_batch_run(self.h, C.cast(ptrs, C.c_void_p), _stream_ptr(stream)))
+        return outs
+
+    def tiles(self):
+        g, b, r = (np.zeros(10, np.int32) for _ in range(3))
+        _check(load().rsgdf_j3c_batch_tiles(self.h, g.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p),
+                                            r.ctypes.data_as(C.c_void_p)))
+        return {"grid": g.tolist(), "bc": b.tolist(), "grab": r.tolist()}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rsgdf_j3c_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsgdf_j3c_batch(problems, kpairs, outs=None, **opt):
+    """One-shot batched j3c; returns the list of outputs."""
+    import torch
+    lib = load()
+    cells = [_cell(a, km) for (a, km, _, _) in problems]
+    refs = [(_BasisRef(ao), _BasisRef(aux)) for (_, _, ao, aux) in problems]
+    kp = [np.ascontiguousarray(np.asarray(k, dtype=np.int32).reshape(-1, 2)) for k in kpairs]
+    n = len(problems)
+    pr = (_Problem * n)()
+    for p in range(n):
+        pr[p].cell = C.cast(C.pointer(cells[p]), C.c_void_p)
+        pr[p].ao = C.cast(C.pointer(refs[p][0].s), C.c_void_p)
+        pr[p].aux = C.cast(C.pointer(refs[p][1].s), C.c_void_p)
+    if outs is None:
+        outs = [torch.zeros((len(kp[p]), refs[p][1].nfunc, refs[p][0].nfunc, refs[p][0].nfunc),
+                            dtype=torch.complex128, device="cuda") for p in range(n)]
+    npair = np.array([len(k) for k in kp], dtype=np.int32)
+    kcat = np.ascontiguousarray(np.concatenate(kp).reshape(-1))
+    o = _opts(**opt)
+    ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in outs])
+    _check(lib.rsgdf_j3c_batch(n, C.cast(pr, C.c_void_p), C.byref(o), npair.ctypes.data_as(C.c_void_p),
+                               kcat.ctypes.data_as(C.c_void_p), C.cast(ptrs, C.c_void_p)))
+    return outs
