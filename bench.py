@@ -6,13 +6,24 @@ One step = the whole path for one cell: j2c with its Cholesky factors, then j3c
 contraction, Bloch-phase contractions) for every k pair of the mesh and every
 aux function.  Default workload: FCC two-atom cell a = 6.74 Bohr, k-mesh 2x2x2
 (64 k pairs), 30 Cartesian AO and 90 aux functions, eps = 1e-8, G box 7^3 with
-omega from the LR cutoff, FP64 throughout.  Synthetic seeded inputs (the
-paper's basis sets are not available).
+omega from the LR cutoff.  Synthetic seeded inputs (the paper's basis sets are
+not available).
 
-Metric: SR shell-triple lattice terms (aux shell, AO shell pair, l, d) per
-second of the whole step; the j3c build time is ms_per_step.
+Paths (--path): learned-mixed (default: learned screening of SR work items,
+FP64 SR lattice sums, split-TF32 tensor-core LR contraction, FP32 phase
+contractions), mixed, fp64.  Plain FP64 is always timed beside it on the same
+workload, and the line reports the speedup and the error against it (max |dV|
+and the first-order HF-energy proxy).
+
+Metric: SR shell-triple lattice terms (aux shell, AO shell pair, l, d) of the
+workload under the bound screening, per second of the whole step: the same
+numerator for every path, so terms the learned screen skips count as speed.
+The j3c build time is ms_per_step.  Besides the headline line: the same cell
+on the 3x3x3 and 4x4x4 meshes (both paths) and the 32-cell batched workload
+(graph replay with autotuned SR tiles vs one call per cell).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--path learned-mixed|mixed|fp64] [--quick] [--no-cpu-baseline]
 
 Under torchrun every rank runs its own copy of the step on its GPU (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -33,6 +44,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "j3c build s and shell-triple integrals/s per k-mesh; learned+mixed vs plain FP64 at 1e-8"
 UNIT = "shell-triple lattice terms/s"
+DTYPES = {"fp64": "f64", "mixed": "f64 SR / tf32x3 LR / f32 phases",
+          "learned-mixed": "f64 SR / tf32x3 LR / f32 phases, f16 screen network"}
 
 
 def parse():
@@ -43,7 +56,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kmesh", default="2,2,2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--path", default="learned-mixed", choices=["learned-mixed", "mixed", "fp64"])
+    ap.add_argument("--quick", action="store_true", help="skip the per-k-mesh and batched measurements")
     return ap.parse_args()
 
 
@@ -56,7 +70,7 @@ def workload(kmesh):
 def describe(p, omega, gmesh):
     return {"workload": "FCC a=6.74 Bohr 2-atom cell, k-mesh %dx%dx%d (%d k pairs), %d AO / %d aux Cartesian "
                         "functions, 3s2p1d AO per atom, ETB aux s8p5d2f1 per atom, eps_screen=eps_lr=%g, "
-                        "G box %dx%dx%d, omega=%.6f; j2c+Cholesky+j3c(SR+G0+LR) FP64"
+                        "G box %dx%dx%d, omega=%.6f; j2c+Cholesky+j3c(SR+G0+LR)"
                         % (*p.kmesh, p.nk * p.nk, p.ao.nfunc, p.aux.nfunc, p.eps_sr, *gmesh, omega),
             "k_mesh": list(p.kmesh), "n_kpairs": p.nk * p.nk, "n_ao": p.ao.nfunc, "n_aux": p.aux.nfunc,
             "eps": p.eps_sr, "gmesh": list(gmesh), "omega": omega,
@@ -155,6 +169,23 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def train_network(rsgdf, screening, inputs):
+    """Learned screen: trained on the SR items of the cubic 2-atom Gamma cell
+    and of an FCC cell with another draw of the basis (not the timed one)."""
+    p1 = inputs.config1()
+    _, gm1 = rsgdf.rsgdf_params(p1.a, p1.kmesh, omega=p1.omega, eps_lr=p1.eps_lr)
+    pt = inputs.config2(seed_offset=12)
+    wt, gmt = rsgdf.rsgdf_params(pt.a, pt.kmesh, gmesh=pt.gmesh, eps_lr=pt.eps_lr)
+    t0 = time.perf_counter()
+    X, t = screening.items_dataset([(p1.a, p1.kmesh, p1.ao, p1.aux, p1.omega, gm1, p1.eps_lr),
+                                    (pt.a, pt.kmesh, pt.ao, pt.aux, wt, gmt, pt.eps_lr)], eps_screen=1e-8)
+    m, info = screening.train_screen(X, t, seed=0, eps_screen=1e-8)
+    info["train_s"] = time.perf_counter() - t0
+    info["data"] = ("SR items of the cubic a=4.0 2-atom Gamma cell and of the FCC a=6.74 cell with another "
+                    "basis draw (seed offset 12), eps 1e-8")
+    return m, info
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -172,55 +203,75 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    from paper_2102_02989_gb300 import rsgdf
+    from paper_2102_02989_gb300 import hfproxy, inputs, rsgdf, screening
     rsgdf.load()
     kmesh = [int(x) for x in args.kmesh.split(",")]
     p = workload(kmesh)
     omega, gmesh = rsgdf.rsgdf_params(p.a, p.kmesh, gmesh=p.gmesh, eps_lr=p.eps_lr)
-    kp = np.array([(i, j) for i in range(p.nk) for j in range(p.nk)], dtype=np.int32)
-    kl = list(range(p.nk))
-    opt = dict(omega=omega, gmesh=gmesh, eps_screen=p.eps_sr, eps_lr=p.eps_lr,
-               precision=rsgdf.RSGDF_MIXED if args.precision == "mixed" else rsgdf.RSGDF_FP64)
-    V = torch.zeros((len(kp), p.aux.nfunc, p.ao.nfunc, p.ao.nfunc), dtype=torch.complex128, device=dev)
+    base = dict(omega=omega, gmesh=gmesh, eps_screen=p.eps_sr, eps_lr=p.eps_lr)
+    mlp, train_info = (None, None)
+    if args.path == "learned-mixed":
+        mlp, train_info = train_network(rsgdf, screening, inputs)
+    paths = {"fp64": dict(base, precision=rsgdf.RSGDF_FP64),
+             "mixed": dict(base, precision=rsgdf.RSGDF_MIXED),
+             "learned-mixed": dict(base, precision=rsgdf.RSGDF_MIXED, screening=rsgdf.RSGDF_SCREEN_LEARNED,
+                                   mlp=mlp.h if mlp else None)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
-        J, L, info = rsgdf.rsgdf_j2c(p.a, p.kmesh, p.aux, kl, **opt)
-        s2 = rsgdf.rsgdf_last_stats()
-        rsgdf.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, out=V, **opt)
-        s3 = rsgdf.rsgdf_last_stats()
-        return (J, L, info), s2, s3
+    def make(prob, opt):
+        kp = np.array([(i, j) for i in range(prob.nk) for j in range(prob.nk)], dtype=np.int32)
+        kl = list(range(prob.nk))
+        V = torch.zeros((len(kp), prob.aux.nfunc, prob.ao.nfunc, prob.ao.nfunc), dtype=torch.complex128, device=dev)
+
+        def step():
+            J, L, info = rsgdf.rsgdf_j2c(prob.a, prob.kmesh, prob.aux, kl, **opt)
+            s2 = rsgdf.rsgdf_last_stats()
+            rsgdf.rsgdf_j3c(prob.a, prob.kmesh, prob.ao, prob.aux, kp, out=V, **opt)
+            s3 = rsgdf.rsgdf_last_stats()
+            return (J, L, info), s2, s3
+        return step, V, kp
+
+    def timed(step, nsteps, nwarm):
+        for _ in range(max(nwarm, 0)):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        stats = []
+        for i in range(nsteps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("timed_step")   # launch lists: ncu --nvtx --nvtx-include timed_step/
+            ev[i][0].record()
+            out, s2, s3 = step()
+            ev[i][1].record()
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            stats.append((s2, s3))
+        return [a.elapsed_time(b) for a, b in ev], stats, out
 
     peak_fp64 = rsgdf.rsgdf_probe_fp64()
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
+    step, V, kp = make(p, paths[args.path])
+    ref_step, Vref, _ = make(p, paths["fp64"])
     clocks = Clocks()
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stats = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev[i][0].record()
-        out, s2, s3 = step()
-        ev[i][1].record()
-        torch.cuda.synchronize()
-        stats.append((s2, s3))
+    times, stats, (J, L, info) = timed(step, args.steps, args.warmup)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop(gpu_index=local)
-    times = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(times)
+    # plain FP64 on the same workload: the comparison and the work count
+    ref_times, ref_stats, _ = timed(ref_step, args.steps, args.warmup) if args.path != "fp64" else (times, stats, None)
+    work = sum(s3["sr_terms"] + s2["sr_terms"] for s2, s3 in ref_stats) / len(ref_stats)   # bound-screened terms
+    own_terms = sum(s3["sr_terms"] + s2["sr_terms"] for s2, s3 in stats) / len(stats)
     # end to end through the public API: host inputs (uploaded by the call) and
     # a device-to-host read of every result into pinned memory
     hV = torch.empty(V.shape, dtype=V.dtype, pin_memory=True)
     h2d = sum(np.asarray(x).nbytes for b in (p.ao, p.aux) for x in (b.l, b.nprim, b.prim_off, b.center, b.exps, b.coeffs))
-    h2d = 2 * h2d + kp.nbytes + 4 * len(kl)
+    h2d = 2 * h2d + kp.nbytes + 4 * p.nk
     e2e_ms = []
     for i in range(args.steps):
         flush.zero_()
@@ -234,17 +285,25 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     d2h = V.numel() * 16 + J.numel() * 16 + L.numel() * 16 + info.numel() * 4
-    terms = sum(s3["sr_terms"] + s2["sr_terms"] for s2, s3 in stats)
     # max over ranks of the timed region; units summed over ranks
-    tmax, ttot, e2e_max = tot_ms, terms, sum(e2e_ms)
+    tmax, ttot, e2e_max = tot_ms, work * args.steps, sum(e2e_ms)
     if dist:
         t = torch.tensor([tot_ms, sum(e2e_ms)], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        n = torch.tensor([float(terms)], dtype=torch.float64, device=dev)
+        n = torch.tensor([float(ttot)], dtype=torch.float64, device=dev)
         dist.all_reduce(n, op=dist.ReduceOp.SUM)
         tmax, e2e_max, ttot = float(t[0]), float(t[1]), float(n[0])
     value = ttot / (tmax * 1e-3)
     e2e_val = ttot / (e2e_max * 1e-3)
+    # accuracy against plain FP64 on the same GPU: max |dV| and the HF-energy proxy
+    ref_step()
+    step()
+    torch.cuda.synchronize()
+    hv, hr, hj = V.cpu().numpy(), Vref.cpu().numpy(), J.cpu().numpy()
+    acc = {"max_abs_vs_fp64": float(np.max(np.abs(hv - hr))), "max_abs_fp64": float(np.max(np.abs(hr)))}
+    acc.update({"hf_proxy_" + k: v for k, v in hfproxy.energy_error(hv, hr, kp, p.kmesh, hj).items()})
+    acc["hf_proxy_note"] = ("first-order HF energy change per cell, Hartree; metric inverted on eigenvalues "
+                            "> 1e-6 of the largest")
     # roofline of the dominant phase (device times measured by the library's events)
     ph = {}
     for key, fl in (("sr_ms", "sr_flops"), ("aft_ms", None), ("lr_gemm_ms", "lr_flops"), ("phase_ms", None),
@@ -254,29 +313,38 @@ def main():
         ph[key] = {"ms": ms, "tflops": (flops / (ms * 1e-3) / 1e12) if (fl and ms > 0) else None}
     dom = max(ph, key=lambda k: ph[k]["ms"])
     names = {"sr_ms": "k_sr3c (SR lattice-sum kernels)", "aft_ms": "k_aft (pair Fourier transforms)",
-             "lr_gemm_ms": "k_zgemm_tn (LR contraction)", "phase_ms": "k_phase1/k_phase2", "other_ms": "other"}
+             "lr_gemm_ms": "LR contraction GEMM", "phase_ms": "k_phase1/k_phase2", "other_ms": "other"}
     ach = ph[dom]["tflops"]
     roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "TFLOP/s",
             "frac": (ach / peak_fp64) if ach else None, "traffic": None,
             "peak_source": "measured live: rsgdf_probe_fp64 (FP64 FMA chains on every SM)",
             "achieved_note": "algorithmic FP64 flops of the phase / its device time (CUDA events on the call's stream)"}
+    ref_ms = sum(ref_times) / len(ref_times)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+tf32x3/f32",
-        "data": "synthetic", "config": dict(describe(p, omega, gmesh), precision=args.precision),
+        "vs_baseline": None, "dtype": DTYPES[args.path], "data": "synthetic",
+        "config": dict(describe(p, omega, gmesh), path=args.path),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_max / args.steps},
         "gpu_launches": int(sum(s2["n_launch"] + s3["n_launch"] for s2, s3 in stats)),
         "clocks": clk, "roofline": roof,
+        "vs_plain_fp64": {"fp64_ms_per_step": ref_ms, "fp64_value": work / (ref_ms * 1e-3),
+                          "speedup": ref_ms / (tmax / args.steps), **acc},
         "phases_ms_per_step": {k: v["ms"] for k, v in ph.items()},
         "phases_tflops": {k: v["tflops"] for k, v in ph.items()},
-        "sr_terms_per_step": int(terms / args.steps), "sr_integrals_per_step": int(stats[0][1]["sr_integrals"]),
-        "sr_primitive_terms_per_step": int(sum(s3["sr_prim_terms"] + s2["sr_prim_terms"] for s2, s3 in stats) / args.steps),
+        "sr_terms_per_step": {"bound_screened": int(work), "computed": int(own_terms)},
+        "sr_items_pruned_per_step": int(stats[-1][1]["sr_items_pruned"]),
+        "sr_items_per_step": int(stats[-1][1]["sr_items"]),
         "j3c_sr_by_L": {"terms": stats[-1][1]["sr_terms_by_L"], "ms": [round(x, 3) for x in stats[-1][1]["sr_ms_by_L"]]},
         "j3c_build_ms": statistics.median([s3["sr_ms"] + s3["aft_ms"] + s3["lr_gemm_ms"] + s3["phase_ms"] +
                                            s3["other_ms"] for _, s3 in stats]),
     }
+    if train_info:
+        line["learned_screen"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in train_info.items()}
+    if rank == 0 and not args.quick:
+        line["per_kmesh"] = per_kmesh(rsgdf, inputs, paths, make, timed, np)
+        line["batch"] = batch_bench(rsgdf, inputs, np, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -287,6 +355,78 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def per_kmesh(rsgdf, inputs, paths, make, timed, np):
+    """The same cell on the 3x3x3 and 4x4x4 meshes: both paths, 2 steps each."""
+    out = {}
+    for km in ((3, 3, 3), (4, 4, 4)):
+        p = inputs.config2(km)
+        w, gm = rsgdf.rsgdf_params(p.a, p.kmesh, gmesh=p.gmesh, eps_lr=p.eps_lr)
+        res = {}
+        Vs = {}
+        for name in ("fp64", "learned-mixed"):
+            opt = dict(paths[name], omega=w, gmesh=gm)
+            if name == "learned-mixed" and opt.get("mlp") is None:
+                continue
+            step, V, _ = make(p, opt)
+            t, st, _ = timed(step, 2, 1)
+            ms = sum(t) / len(t)
+            res[name] = {"ms_per_step": ms, "sr_terms": int(st[-1][1]["sr_terms"] + st[-1][0]["sr_terms"])}
+            Vs[name] = V
+        if "learned-mixed" in Vs:
+            d = (Vs["learned-mixed"] - Vs["fp64"]).abs().max().item()
+            res["max_abs_vs_fp64"] = d
+            res["speedup"] = res["fp64"]["ms_per_step"] / res["learned-mixed"]["ms_per_step"]
+            res["value_learned_mixed"] = res["fp64"]["sr_terms"] / (res["learned-mixed"]["ms_per_step"] * 1e-3)
+        res["value_fp64"] = res["fp64"]["sr_terms"] / (res["fp64"]["ms_per_step"] * 1e-3)
+        del Vs
+        out["%dx%dx%d" % km] = res
+    return out
+
+
+def batch_bench(rsgdf, inputs, np, torch):
+    """32 heterogeneous cells, diagonal k pairs, FP64: batched handle with
+    graph + autotuned SR tiles vs the same cells one call at a time."""
+    cells = inputs.config4()
+    probs = [(c.a, c.kmesh, c.ao, c.aux) for c in cells]
+    kps = [inputs.kpairs_diag(c.nk) for c in cells]
+    opt = dict(gmesh=(7, 7, 7), eps_screen=1e-8, eps_lr=1e-8)
+    s = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    b = rsgdf.Batch(probs, kps, flags=rsgdf.RSGDF_BATCH_GRAPH | rsgdf.RSGDF_BATCH_AUTOTUNE, stream=s, **opt)
+    outs = b.outputs()
+    b.run(outs, stream=s)     # autotune + capture
+    s.synchronize()
+    setup_s = time.perf_counter() - t0
+    st = rsgdf.rsgdf_last_stats()
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        b.run(outs, stream=s)
+        e1.record(s)
+        s.synchronize()
+        times.append(e0.elapsed_time(e1))
+    tiles = b.tiles()
+    b.close()
+    # the same cells, one library call each (plans included, as a user would call)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    terms = 0
+    with torch.cuda.stream(s):
+        for c, kp, o in zip(cells, kps, outs):
+            rsgdf.rsgdf_j3c(c.a, c.kmesh, c.ao, c.aux, kp, out=o, stream=s, **opt)
+            terms += rsgdf.rsgdf_last_stats()["sr_terms"]
+    s.synchronize()
+    seq_ms = 1e3 * (time.perf_counter() - t0)
+    ms = statistics.median(times)
+    return {"workload": "32 cells: 1-8 atoms, cubic/FCC a in [5,10] Bohr, random AO shells l<=3, ETB aux ~3x, "
+                        "k-meshes 1^3-3^3, diagonal k pairs, eps 1e-8, G box 7^3, FP64",
+            "graph_replay_ms": ms, "value": terms / (ms * 1e-3), "unit": UNIT,
+            "sequential_calls_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+            "create_tune_capture_s": setup_s, "sr_items": int(st["sr_items"]), "launches_per_run": int(st["n_launch"]),
+            "sr_tiles": tiles}
 
 
 if __name__ == "__main__":
