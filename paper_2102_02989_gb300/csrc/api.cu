@@ -709,10 +709,16 @@ static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int np
     RC(S.upload(P.dgoff, goff));
     P.fp32 = (opts->precision == RSGDF_MIXED) ? 1 : 0;
     if (P.fp32) {
-        std::vector<float> ph32(ph.begin(), ph.end());
-        float *dph32;
-        RC(S.upload(dph32, ph32));
-        P.phk = dph32;
+        // double-float phase table: (cos hi, cos lo, sin hi, sin lo)
+        std::vector<float> ph4(2 * ph.size());
+        for (size_t e = 0; e < ph.size(); e++) {
+            const float h = (float)ph[e];
+            ph4[2 * e] = h;
+            ph4[2 * e + 1] = (float)(ph[e] - (double)h);
+        }
+        float *dph4;
+        RC(S.upload(dph4, ph4));
+        P.phk = dph4;
     } else {
         double *dph;
         RC(S.upload(dph, ph));
@@ -847,6 +853,12 @@ static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
         nl += 2;
     }
     if (P.Bpl) CU(cudaMemsetAsync(P.Bpl, 0, sizeof(float) * P.nbpl, st));
+    if (P.fp32 && (P.mode & MODE_SR)) {
+        t_timer.begin(PH_PHASE);
+        RC(launch_x_to_df(P.X, (long long)P.nlt * Nk * m, st));   // X to double-float pairs, in place
+        t_timer.end();
+        nl++;
+    }
     const int G = (int)P.gkey.size();
     for (int gb0 = 0; gb0 < G; gb0 += P.B) {
         const int nb = std::min(P.B, G - gb0);

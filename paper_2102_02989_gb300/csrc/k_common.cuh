@@ -193,6 +193,7 @@ long long tc_b_floats(int N, int K, int batch);
 long long tc_a_floats(int M, int K);
 int tc_status_take(int *flag);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
+int launch_x_to_df(double *X, long long n, cudaStream_t st);
 int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
                         double *T, int fp32, cudaStream_t st);
 int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,

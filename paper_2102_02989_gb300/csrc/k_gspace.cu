@@ -726,13 +726,12 @@ namespace rsgdf {
 // Bloch-phase contractions for a batch of k12 values (Eq. BvK_latsum_LR):
 //   T[j][dt][i] = sum_lt e^{-i k12_j.lt} X[lt][dt][i]        (phase1)
 //   V[pair][i]  = sum_dt e^{+i k2.dt} T[j(pair)][dt][i]        (phase2)
-// Register-blocked over PH_KB k12 values (phase1) and PH_PB pairs (phase2) so
-// X and T are read a few times only.  R = double (FP64 path) or float
-// (mixed path: FP32 arithmetic, FP64 storage).
+// Register-blocked over KB k12 values (phase1) and PB pairs (phase2) so X and
+// T are read a few times only.  R = double: the FP64 path.  The mixed path
+// runs the same sums in double-float arithmetic on the FP32 pipes (below).
 // ---------------------------------------------------------------------------
 template <typename R> struct PhT;
 template <> struct PhT<double> { typedef double2 type; enum { KB = 8, PB = 8 }; };
-template <> struct PhT<float> { typedef float2 type; enum { KB = 16, PB = 16 }; };
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__ X, long long m, int Nk, int nlt,
@@ -820,13 +819,149 @@ static int grid_for(long long n)
     return (int)(g < 1 ? 1 : g);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed path: the same contractions in double-float arithmetic.  A
+// double-float is an unevaluated sum h + l of two floats; a product takes the
+// exact rounding error of h1*h2 from one FMA (Dekker's product with a fused
+// multiply-add), a sum takes it from Knuth's TwoSum, so each operation keeps
+// about 44 bits while every instruction runs on the FP32 pipes.  Only the
+// conversions from and to FP64 (once per X element, per T element read and
+// per output) use the FP64 pipe.  The explicit _rn intrinsics keep the
+// compiler from fusing the error-free steps into other FMAs.
+// ---------------------------------------------------------------------------
+struct dflt {
+    float h, l;
+};
+__device__ __forceinline__ dflt df_from(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dflt a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);   // exact: h1*h2 - p
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));   // exact: a.h + b.h - s
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float r = __fadd_rn(s, e);
+    return {r, __fsub_rn(e, __fsub_rn(r, s))};
+}
+__device__ __forceinline__ dflt df_neg(dflt a) { return {-a.h, -a.l}; }
+
+// X (FP64) -> double-float pairs, in place (same 8 bytes per element).
+__global__ void k_x_to_df(double *X, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const dflt d = df_from(X[i]);
+        reinterpret_cast<float2 *>(X)[i] = make_float2(d.h, d.l);
+    }
+}
+
+// phase tables as float4 (cos hi, cos lo, sin hi, sin lo)
+constexpr int DF_KB = 8, DF_PB = 8;
+
+__global__ void __launch_bounds__(256) k_phase1_df(const float2 *__restrict__ X, long long m, int Nk, int nlt,
+                                                   const int *__restrict__ k12list, int nk12,
+                                                   const float4 *__restrict__ ph, double2 *__restrict__ T)
+{
+    const long long n = (long long)Nk * m;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+        const int dt = (int)(id / m);
+        const long long i = id - (long long)dt * m;
+        for (int j0 = 0; j0 < nk12; j0 += DF_KB) {
+            dflt ar[DF_KB], ai[DF_KB];
+#pragma unroll
+            for (int j = 0; j < DF_KB; j++) { ar[j] = {0.0f, 0.0f}; ai[j] = {0.0f, 0.0f}; }
+            for (int lt = 0; lt < nlt; lt++) {
+                const float2 xv = X[((long long)lt * Nk + dt) * m + i];
+                const dflt x = {xv.x, xv.y};
+#pragma unroll
+                for (int j = 0; j < DF_KB; j++) {
+                    if (j0 + j < nk12) {
+                        const float4 p = __ldg(&ph[(long long)k12list[j0 + j] * Nk + lt]);
+                        ar[j] = df_add(ar[j], df_mul({p.x, p.y}, x));
+                        ai[j] = df_add(ai[j], df_neg(df_mul({p.z, p.w}, x)));   // e^{-i k12.lt}
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < DF_KB; j++)
+                if (j0 + j < nk12) T[((long long)(j0 + j) * Nk + dt) * m + i] = make_double2(df_to(ar[j]), df_to(ai[j]));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_phase2_df(const double2 *__restrict__ T, long long m, int Nk,
+                                                   const int *__restrict__ goff, int ngroups,
+                                                   const int *__restrict__ plist, const int *__restrict__ pk2,
+                                                   const float4 *__restrict__ ph, double2 *__restrict__ V,
+                                                   int accumulate)
+{
+    const int g = blockIdx.y;
+    const int p0 = goff[g], p1 = goff[g + 1];
+    const double2 *Tg = T + (long long)g * Nk * m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        for (int q0 = p0; q0 < p1; q0 += DF_PB) {
+            dflt ar[DF_PB], ai[DF_PB];
+#pragma unroll
+            for (int j = 0; j < DF_PB; j++) { ar[j] = {0.0f, 0.0f}; ai[j] = {0.0f, 0.0f}; }
+            for (int dt = 0; dt < Nk; dt++) {
+                const double2 t = Tg[(long long)dt * m + i];
+                const dflt tr = df_from(t.x), ti = df_from(t.y);
+#pragma unroll
+                for (int j = 0; j < DF_PB; j++) {
+                    if (q0 + j < p1) {
+                        const float4 p = __ldg(&ph[(long long)pk2[q0 + j] * Nk + dt]);
+                        const dflt c = {p.x, p.y}, sn = {p.z, p.w};
+                        // (c + i s)(tr + i ti)
+                        ar[j] = df_add(ar[j], df_add(df_mul(c, tr), df_neg(df_mul(sn, ti))));
+                        ai[j] = df_add(ai[j], df_add(df_mul(c, ti), df_mul(sn, tr)));
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < DF_PB; j++) {
+                if (q0 + j < p1) {
+                    const long long o = (long long)plist[q0 + j] * m + i;
+                    if (accumulate) {
+                        double2 v = V[o];
+                        v.x += df_to(ar[j]);
+                        v.y += df_to(ai[j]);
+                        V[o] = v;
+                    } else {
+                        V[o] = make_double2(df_to(ar[j]), df_to(ai[j]));
+                    }
+                }
+            }
+        }
+    }
+}
+
+int launch_x_to_df(double *X, long long n, cudaStream_t st)
+{
+    if (n <= 0) return RSGDF_OK;
+    k_x_to_df<<<grid_for(n), 256, 0, st>>>(X, n);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// fp32 = 1: X already in double-float pairs (launch_x_to_df), ph = float4 table
 int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
                         double *T, int fp32, cudaStream_t st)
 {
     const long long n = (long long)Nk * m;
     if (fp32)
-        k_phase1_multi<float><<<grid_for(n), 256, 0, st>>>(X, m, Nk, nlt, k12list, nk12, (const float2 *)ph,
-                                                            (double2 *)T);
+        k_phase1_df<<<grid_for(n), 256, 0, st>>>((const float2 *)X, m, Nk, nlt, k12list, nk12, (const float4 *)ph,
+                                                 (double2 *)T);
     else
         k_phase1_multi<double><<<grid_for(n), 256, 0, st>>>(X, m, Nk, nlt, k12list, nk12, (const double2 *)ph,
                                                              (double2 *)T);
@@ -838,8 +973,8 @@ int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, i
 {
     dim3 grid((unsigned)std::min<long long>((m + 255) / 256, 4096), ngroups);
     if (fp32)
-        k_phase2_multi<float><<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, goff, ngroups, plist, pk2,
-                                                   (const float2 *)ph, (double2 *)V, accumulate);
+        k_phase2_df<<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, goff, ngroups, plist, pk2, (const float4 *)ph,
+                                          (double2 *)V, accumulate);
     else
         k_phase2_multi<double><<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, goff, ngroups, plist, pk2,
                                                     (const double2 *)ph, (double2 *)V, accumulate);

@@ -88,8 +88,9 @@ def energies(V, kpairs, kmesh, W, D):
         k1, k2 = int(k1), int(k2)
         if k1 == k2:
             rho = rho + np.einsum("pmn,nm->p", B[p], D[k1])
-        # Tr[D1 B_P D2 B_P^H] summed over P
-        EK += np.einsum("mn,pno,ol,pml->", D[k1], B[p], D[k2], np.conj(B[p])).real
+        # sum_P Tr[D1 B_P D2 B_P^H] = sum_P sum_{ml} (D1 B_P D2)_{ml} conj(B_P)_{ml}
+        M = D[k1] @ B[p] @ D[k2]
+        EK += float(np.sum(M * np.conj(B[p])).real)
     EJ = 0.5 * float(np.sum(np.abs(rho) ** 2)) / nk ** 2
     return EJ, -0.25 * EK / nk ** 2
 

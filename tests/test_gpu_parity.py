@@ -191,8 +191,9 @@ def test_config2_mixed_lr_error(rs, orc):
 
 
 def test_config2_mixed_full_all_pairs(rs, orc):
-    """Mixed path end to end (FP64 SR lattice sums, FP32 phase contractions,
-    split-TF32 tensor-core LR) on every k pair of the 2x2x2 mesh."""
+    """Mixed path end to end (FP64 SR lattice sums, double-float phase
+    contractions on the FP32 pipes, split-TF32 tensor-core LR) on every k pair
+    of the 2x2x2 mesh."""
     p = inputs.config2()
     w = omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)
     kp = inputs.kpairs_all(p.nk)
@@ -205,3 +206,21 @@ def test_config2_mixed_full_all_pairs(rs, orc):
     assert np.max(np.abs(got - ref)) < MIXED_REL * np.max(np.abs(ref))
     fp = _np(rs.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, gmesh=p.gmesh, eps_screen=eps, eps_lr=p.eps_lr))
     assert np.max(np.abs(fp - ref)) < TOL
+
+
+@pytest.mark.parametrize("km,sh", [((2, 2, 2), (13, 16)), ((3, 3, 3), (0, 2))])
+def test_mixed_sr_phases_fp64_grade(rs, orc, km, sh):
+    """The mixed path's Bloch-phase contractions run in double-float
+    arithmetic on the FP32 pipes: the SR part (FP64 lattice sums, then both
+    phase steps and the G = 0 correction) stays within the FP64 parity bound."""
+    p = inputs.config2(km)
+    w = omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)
+    kp = inputs.kpairs_all(p.nk)
+    if len(kp) > 100:
+        kp = kp[np.random.default_rng(1).choice(len(kp), 60, replace=False)]
+    eps = 1e-11
+    ref = orc.j3c(p.a, p.kmesh, p.ao, p.aux, w, kp, eps_sr=eps, eps_lr=p.eps_lr, gmesh=p.gmesh, shells=sh, lr=False)
+    got = _np(rs.rsgdf_j3c_sr(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, gmesh=p.gmesh, eps_screen=eps,
+                              eps_lr=p.eps_lr, precision=rs.RSGDF_MIXED))
+    assert np.max(np.abs(ref)) > 0.1
+    assert np.max(np.abs(got - ref)) < TOL
