@@ -231,7 +231,7 @@ def main():
             return (J, L, info), s2, s3
         return step, V, kp
 
-    def timed(step, nsteps, nwarm):
+    def timed(step, nsteps, nwarm, rng="timed_step"):
         for _ in range(max(nwarm, 0)):
             step()
         torch.cuda.synchronize()
@@ -240,7 +240,7 @@ def main():
         for i in range(nsteps):
             flush.zero_()
             torch.cuda.synchronize()
-            torch.cuda.nvtx.range_push("timed_step")   # launch lists: ncu --nvtx --nvtx-include timed_step/
+            torch.cuda.nvtx.range_push(rng)   # launch lists: ncu --nvtx --nvtx-include timed_step/
             ev[i][0].record()
             out, s2, s3 = step()
             ev[i][1].record()
@@ -264,7 +264,8 @@ def main():
     clk = clocks.stop(gpu_index=local)
     tot_ms = sum(times)
     # plain FP64 on the same workload: the comparison and the work count
-    ref_times, ref_stats, _ = timed(ref_step, args.steps, args.warmup) if args.path != "fp64" else (times, stats, None)
+    ref_times, ref_stats, _ = (timed(ref_step, args.steps, args.warmup, "fp64_step") if args.path != "fp64"
+                               else (times, stats, None))
     work = sum(s3["sr_terms"] + s2["sr_terms"] for s2, s3 in ref_stats) / len(ref_stats)   # bound-screened terms
     own_terms = sum(s3["sr_terms"] + s2["sr_terms"] for s2, s3 in stats) / len(stats)
     # end to end through the public API: host inputs (uploaded by the call) and
@@ -370,7 +371,7 @@ def per_kmesh(rsgdf, inputs, paths, make, timed, np):
             if name == "learned-mixed" and opt.get("mlp") is None:
                 continue
             step, V, _ = make(p, opt)
-            t, st, _ = timed(step, 2, 1)
+            t, st, _ = timed(step, 2, 1, "kmesh_step")
             ms = sum(t) / len(t)
             res[name] = {"ms_per_step": ms, "sr_terms": int(st[-1][1]["sr_terms"] + st[-1][0]["sr_terms"])}
             Vs[name] = V

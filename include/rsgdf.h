@@ -188,11 +188,10 @@ int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair
  * rsgdf_kphase without any device allocation (no counterpart in the paper;
  * same arguments, result and ordering as rsgdf_kphase).
  *
- * For callers that must not allocate device memory while they run: code that
- * records the call into a CUDA graph, where allocation calls are not allowed
- * during capture; applications that own all device memory through their own
- * pool and forbid libraries from calling cudaMalloc; steady-state loops that
- * must not risk an allocation failure half way through a step.
+ * For callers that must not allocate device memory while they run:
+ * applications that own all device memory through their own pool and forbid
+ * libraries from calling cudaMalloc; steady-state loops that must not risk an
+ * allocation failure (or an allocator synchronisation) half way through a step.
  *
  * Scratch (the phase table, the k-pair lists and the intermediate T, about
  * 16 Nk m bytes) lives in one static device array of RSGDF_NOALLOC_SCRATCH_BYTES

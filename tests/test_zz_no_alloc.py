@@ -1,9 +1,9 @@
 """The allocation-free k-phase entry point (rsgdf_kphase_noalloc) against the
 ordinary one, through the C ABI, on two calls in a row.
 
-Callers that cannot allocate device memory while they run (graph capture,
-applications that own all device memory, steady-state loops) use the
-no-alloc variant; its scratch is a fixed static device array shared by every
+Callers that cannot allocate device memory while they run (applications that
+own all device memory through their own pool, steady-state loops that must not
+meet an allocation failure mid-step) use the no-alloc variant; its scratch is a fixed static device array shared by every
 call, so a second call must give the same answer as the first.  This file is
 collected last on purpose."""
 import numpy as np
