@@ -461,6 +461,7 @@ struct SRClassLaunch {
     SRArgs *ddesc = nullptr;
     long long *dcum = nullptr;
     int ncmax = 0, wmax = 0, lmax = 0;
+    int nkmax = 1;   // largest k mesh among the descriptors (bin chunks beyond it are useless)
     int bc = 1;
     size_t warp_bytes = 0;
     long long ntot = 0;
@@ -509,6 +510,7 @@ static int sr_merge(const std::vector<const SRSetup *> &rs, Scratch &S, cudaStre
                 c.desc.push_back(a);
                 c.cum.push_back(c.cum.back() + (a.item_end - a.item_begin));
                 c.ncmax = std::max(c.ncmax, a.ncomp_max);
+                c.nkmax = std::max(c.nkmax, a.Nk);
                 c.wmax = std::max(c.wmax, a.w_max);
                 c.lmax = std::max(c.lmax, a.list_max);
             }
@@ -517,7 +519,7 @@ static int sr_merge(const std::vector<const SRSetup *> &rs, Scratch &S, cudaStre
         c.ntot = c.cum.back();
         RC(S.alloc(c.ddesc, c.desc.size()));
         RC(S.upload(c.dcum, c.cum));
-        RC(sr_set_bc(c, sr_default_bc(L, c.ncmax, c.wmax), st));
+        RC(sr_set_bc(c, sr_default_bc(L, c.ncmax, c.wmax, c.nkmax), st));
         out.push_back(std::move(c));
     }
     return RSGDF_OK;
@@ -548,7 +550,7 @@ static int sr_tune(std::vector<SRClassLaunch> &cl, unsigned long long *dqueue, c
         const int bc0 = c.bc;
         int best_bc = bc0, best_grab = 1;
         float best = 1e30f;
-        const int bcs[3] = {bc0, std::max(1, bc0 / 2), std::min(16, bc0 * 2)};
+        const int bcs[3] = {bc0, std::max(1, bc0 / 2), std::min(std::min(16, c.nkmax), bc0 * 2)};
         const int grabs[2] = {1, 4};
         for (int ib = 0; ib < 3; ib++) {
             if (ib > 0 && bcs[ib] == bcs[0]) continue;

@@ -82,7 +82,7 @@ __device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int 
 }
 
 int upload_boys_table(const double *tab, cudaStream_t st);
-int sr_default_bc(int L, int ncomp_max, int w_max);
+int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
 size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max);
 size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max);
 int sr_occupancy(int L, size_t smem);

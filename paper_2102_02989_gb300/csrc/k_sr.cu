@@ -147,7 +147,7 @@ __device__ __forceinline__ int eoff_sr(int a, int b, int ln)
 constexpr int EAB_SZ = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 2) / 2 * 1;   // >= pair_e1(LMAX, LMAX) = 64
 constexpr int EC_SZ = (LMAX + 1) * (LMAX + 1);
 constexpr int SR_WARPS = 2;
-constexpr int SR_NT = 256;   // translations buffered per segment
+constexpr int SR_NT = 256;   // translations buffered per segment (flush above SR_NT - 64)
 constexpr int SR_MAXCOMBO = 64;
 constexpr double SR_SKIP_ST = 70.0;   // erfc terms with s T beyond this vanish   // primitive combinations per triple (aux x AO x AO)
 
@@ -551,11 +551,14 @@ typedef void (*SRKern)(const SRArgs *, const long long *, int, int, unsigned lon
 static SRKern sr_kernels[LTOT_MAX + 1] = {k_sr3c<0>, k_sr3c<1>, k_sr3c<2>, k_sr3c<3>, k_sr3c<4>,
                                           k_sr3c<5>, k_sr3c<6>, k_sr3c<7>, k_sr3c<8>, k_sr3c<9>};
 
-// bin chunk (BvK cells of the aux image held at once) for a class
-int sr_default_bc(int L, int ncomp_max, int w_max)
+// bin chunk (BvK cells of the aux image held at once) for a class: as many
+// as fit 4096 doubles of sums per warp, at most 16 and at most the mesh size
+// (a larger chunk only costs shared memory, hence occupancy)
+int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max)
 {
     int bc = 4096 / (ntuv(L) + ncomp_max + w_max);
-    return bc < 1 ? 1 : (bc > 16 ? 16 : bc);
+    bc = bc < 1 ? 1 : (bc > 16 ? 16 : bc);
+    return bc > nk_max ? (nk_max < 1 ? 1 : nk_max) : bc;
 }
 
 size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max)

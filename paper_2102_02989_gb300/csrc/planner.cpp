@@ -294,11 +294,13 @@ void pair_images(const Lattice &L, Vec3 d0, double rmax, PairImages &out)
     std::sort(out.r.begin(), out.r.end());
 }
 
-// bisection for the outer root of a function that is >= eps at lo and < eps at hi
+// bisection for the outer root of a function that is >= eps at lo and < eps
+// at hi, to 1e-10 relative (the radii are compared with distances of order
+// 1-100 Bohr)
 template <class F>
 double outer_root(F f, double lo, double hi, double eps)
 {
-    for (int it = 0; it < 64; it++) {
+    for (int it = 0; it < 200 && hi - lo > 1e-10 * hi; it++) {
         double mid = 0.5 * (lo + hi);
         if (f(mid) >= eps) lo = mid; else hi = mid;
     }
@@ -321,6 +323,11 @@ struct PairPart {
     double Sh;        // Eq. S_h (with the growth factor), never below the largest term
     double r12min;    // Eq. R12cutmin
     double xm;        // argmax of x e^{-beta x^2} grow(x), the left bracket of Eq. bound_R12_FF
+    // shape(x) = x e^{-beta x^2} grow(x) at x = xm + j dx, j = 0..NSHAPE (decreasing):
+    // brackets the root of every window of Eq. bound_R12_FF (c1 shape(x) = eps)
+    static constexpr int NSHAPE = 256;
+    double dx;
+    double shape[NSHAPE + 1];
 };
 
 void pair_part(const Lattice &L, const HBasis &ao, int mu, int nu, PairPart &Q)
@@ -384,6 +391,8 @@ void pair_part(const Lattice &L, const HBasis &ao, int mu, int nu, PairPart &Q)
         double v = shape(t);
         if (v > vm) { vm = v; Q.xm = t; }
     }
+    Q.dx = 10.0 / std::sqrt(beta) / PairPart::NSHAPE;
+    for (int j = 0; j <= PairPart::NSHAPE; j++) Q.shape[j] = shape(Q.xm + j * Q.dx);
 }
 
 // The bounds for one (aux shell P, AO shell pair) from the pair part.
@@ -429,10 +438,40 @@ void triple_bounds(const Lattice &L, double omega, double eps, const HBasis &aux
         double c1 = A * cells_in_shell(L, R) * fR * grow_rc(lP, lm + ln, aP, p, eta2, R) * 4.0 * PI / L.vol / (2.0 * beta);
         auto g = [&](double x) { return c1 * x * std::exp(-beta * x * x) * grow_r12(lm, ln, am, an, x); };
         double x = 0.0;
-        if (g(Q.xm) >= eps) {
-            double b = Q.xm + 1e-3;
-            while (g(b) >= eps && b < 1e4) b *= 2;
-            x = outer_root(g, Q.xm, b, eps);
+        if (c1 * Q.shape[0] >= eps) {
+            const double target = eps / c1;
+            if (Q.shape[PairPart::NSHAPE] >= target) {   // beyond the table: expand the bracket
+                double a = Q.xm + PairPart::NSHAPE * Q.dx, b = 2.0 * a;
+                while (g(b) >= eps && b < 1e4) { a = b; b *= 2; }
+                x = outer_root(g, a, b, eps);
+            } else {
+                int lo = 0, hi = PairPart::NSHAPE;   // shape[lo] >= target > shape[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) / 2;
+                    if (Q.shape[mid] >= target) lo = mid; else hi = mid;
+                }
+                // safeguarded Newton on log(c1 shape(x)) - log(eps), decreasing on the bracket
+                const double k1 = std::sqrt(4.0 * am) * an / p, k2 = std::sqrt(4.0 * an) * am / p;
+                const double lc = std::log(c1) - std::log(eps);
+                auto h = [&](double y) {
+                    return lc + std::log(y) - beta * y * y + lm * std::log1p(k1 * y) + ln * std::log1p(k2 * y);
+                };
+                auto dh = [&](double y) { return 1.0 / y - 2.0 * beta * y + lm * k1 / (1.0 + k1 * y) + ln * k2 / (1.0 + k2 * y); };
+                double a = Q.xm + lo * Q.dx, b = Q.xm + hi * Q.dx;
+                double ha = std::log(Q.shape[lo] / target), hb = std::log(Q.shape[hi] / target);
+                double y = (ha - hb > 0.0) ? a + (b - a) * ha / (ha - hb) : 0.5 * (a + b);
+                for (int it = 0; it < 60; it++) {
+                    const double hy = h(y);
+                    if (hy >= 0.0) a = y; else b = y;
+                    const double d = dh(y);
+                    double yn = (d < 0.0) ? y - hy / d : 0.5 * (a + b);
+                    if (!(yn > a && yn < b)) yn = 0.5 * (a + b);
+                    const bool done = std::fabs(yn - y) <= 1e-12 * y || b - a <= 1e-12 * b;
+                    y = yn;
+                    if (done) break;
+                }
+                x = y;
+            }
         }
         B.r12[w] = std::max(x, Q.r12min);
         B.r12_max = std::max(B.r12_max, B.r12[w]);
@@ -652,15 +691,9 @@ void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int>
                     for (int k = lo[2]; k <= hi[2]; k++) {
                         Vec3 v = lat(L, i, j, k);
                         double R = len({v.x - c.x, v.y - c.y, v.z - c.z});
-                        bool keep = false;
-                        for (int x = 0; x < ao.nprim[mu] && !keep; x++)
-                            for (int y = 0; y < ao.nprim[nu] && !keep; y++) {
-                                int oi = ao.poff[mu] + x, oj = ao.poff[nu] + y;
-                                double a = ao.exps[oi], b = ao.exps[oj], p = a + b;
-                                double val = std::fabs(ao.cn[oi] * ao.cn[oj]) * std::pow(PI / p, 1.5) * std::exp(-a * b / p * R * R);
-                                keep = val >= eps;
-                            }
-                        if (keep) {
+                        // some primitive pair has |c_i c_j| (pi/p)^{3/2} e^{-ab/p R^2} >= eps
+                        // exactly when R <= rmax (the largest of their radii)
+                        if (rmax > 0.0 && R <= rmax) {
                             dlist.push_back(i);
                             dlist.push_back(j);
                             dlist.push_back(k);
