@@ -83,6 +83,9 @@ __device__ __forceinline__ void bloch_phase(int k, int cell, const int *nk, int 
 
 int upload_boys_table(const double *tab, cudaStream_t st);
 int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
+// rows (BvK cell x primitive combination) of Hermite sums a warp holds for a bin chunk bc:
+// room for up to 4 combinations at once when the chunk is small
+__host__ __device__ constexpr int sr_rb_rows(int bc) { return 4 * bc < 32 ? 4 * bc : (bc > 32 ? bc : 32); }
 size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max);
 size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max);
 int sr_occupancy(int L, size_t smem);

@@ -149,6 +149,7 @@ constexpr int EC_SZ = (LMAX + 1) * (LMAX + 1);
 constexpr int SR_WARPS = 2;
 constexpr int SR_NT = 256;   // translations buffered per segment (flush above SR_NT - 64)
 constexpr int SR_MAXCOMBO = 64;
+constexpr int SR_GMAX = 4;   // primitive combinations summed at once in the term loop
 constexpr double SR_SKIP_ST = 70.0;   // erfc terms with s T beyond this vanish   // primitive combinations per triple (aux x AO x AO)
 
 // per-warp shared memory: term positions (3 doubles) and BvK cells, twice
@@ -161,7 +162,7 @@ size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max)
     b += 64 * sizeof(int);                                        // FP32 survivor queue
     b = (b + 15) & ~(size_t)15;
     b += (3 * EAB_SZ + EC_SZ) * sizeof(double);
-    b += (size_t)bc * (ntuv(L) + ncomp_max + w_max) * sizeof(double);
+    b += ((size_t)sr_rb_rows(bc) * ntuv(L) + (size_t)bc * (ncomp_max + w_max)) * sizeof(double);
     b += (size_t)list_max * (sizeof(double) + sizeof(short));
     b = (b + 15) & ~(size_t)15;
     b += (size_t)SR_MAXCOMBO * 8 * sizeof(double);                    // per-combination constants
@@ -203,7 +204,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                      ~(size_t)15));
     double *Ec = Eab + 3 * EAB_SZ;
     double *Rb = Ec + EC_SZ;
-    double *O = Rb + A.bc * NR;
+    double *O = Rb + sr_rb_rows(A.bc) * NR;
     double *Wb = O + A.bc * A.ncomp_max;
     double *Lc = Wb + A.bc * A.w_max;
     short *Li = (short *)(Lc + A.list_max);
@@ -373,15 +374,31 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                 const int r0 = cnt[c0], r1 = cnt[c0 + nb];
                 if (r0 == r1) continue;
                 for (int o = lane; o < nb * ncomp; o += 32) O[o] = 0.0;
-                for (int k = 0; k < A.ax.nprim[P]; k++) {
-                    const int ok = A.ax.poff[P] + k;
-                    for (int e = lane; e < EC_SZ; e += 32) Ec[e] = A.ec_tab[ok * EC_SZ + e];
-                    for (int ij = 0; ij < A.ao.nprim[mu] * A.ao.nprim[nu]; ij++) {
-                        // Hermite coefficients and constants of (d, primitive pair)
-                        const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
-                        for (int e = lane; e < 3 * n1; e += 32) Eab[e] = en[ENT_HDR + e];
-                        for (int o = lane; o < nb * NR; o += 32) Rb[o] = 0.0;
-                        const double *kc = Kc + 8 * (k * npp + ij);
+                // G primitive combinations at a time, each on 32/G lanes with its
+                // own rows of Hermite sums: G minimises the warp rounds of the
+                // term loop (a chunk holds ~tens of translations, fewer than 32
+                // lanes per combination would leave idle)
+                const int nTc = r1 - r0;
+                int G = 1;
+                {
+                    long long best = (long long)ncombo * ((nTc + 31) >> 5);
+                    for (int g2 = 2; g2 <= SR_GMAX && g2 * nb <= sr_rb_rows(A.bc); g2 *= 2) {
+                        const int lg = 32 / g2;
+                        const long long rounds = (long long)((ncombo + g2 - 1) / g2) * ((nTc + lg - 1) / lg);
+                        if (rounds < best) {
+                            best = rounds;
+                            G = g2;
+                        }
+                    }
+                }
+                const int Lg = 32 / G;
+                const int grp = lane / Lg, sub = lane - grp * Lg;
+                for (int cg = 0; cg < ncombo; cg += G) {
+                    for (int o = lane; o < G * nb * NR; o += 32) Rb[o] = 0.0;
+                    __syncwarp();
+                    const int cmy = cg + grp;
+                    if (cmy < ncombo) {
+                        const double *kc = Kc + 8 * cmy;
                         const double alpha = kc[0], s = kc[1];
                         double sw[L + 1], fw[L + 1];
                         sw[0] = kc[2];
@@ -392,10 +409,10 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             fw[n] = fw[n - 1] * (-2.0 * alpha);
                         }
                         const double Px = kc[4], Py = kc[5], Pz = kc[6];
-                        __syncwarp();
-                        // contiguous slice of the sorted translations per lane
-                        const int per = (r1 - r0 + 31) >> 5;
-                        const int ta = r0 + lane * per, tb = min(ta + per, r1);
+                        double *Rg = Rb + grp * nb * NR;
+                        // contiguous slice of the sorted translations per lane of the group
+                        const int per = (nTc + Lg - 1) / Lg;
+                        const int ta = r0 + sub * per, tb = min(ta + per, r1);
                         double accR[NR];
 #pragma unroll
                         for (int q = 0; q < NR; q++) accR[q] = 0.0;
@@ -406,7 +423,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                 if (cur >= 0) {
 #pragma unroll
                                     for (int q = 0; q < NR; q++) {
-                                        atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
+                                        atomicAdd(&Rg[(cur - c0) * NR + q], accR[q]);
                                         accR[q] = 0.0;
                                     }
                                 }
@@ -424,12 +441,23 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                         }
                         if (cur >= 0) {
 #pragma unroll
-                            for (int q = 0; q < NR; q++) atomicAdd(&Rb[(cur - c0) * NR + q], accR[q]);
+                            for (int q = 0; q < NR; q++) atomicAdd(&Rg[(cur - c0) * NR + q], accR[q]);
                         }
+                    }
+                    __syncwarp();
+                    // contractions, one combination after the other
+                    for (int gg = 0; gg < G && cg + gg < ncombo; gg++) {
+                        const int cc = cg + gg, k = cc / npp, ij = cc - k * npp;
+                        const int ok = A.ax.poff[P] + k;
+                        for (int e = lane; e < EC_SZ; e += 32) Ec[e] = A.ec_tab[ok * EC_SZ + e];
+                        // Hermite coefficients of (d, primitive pair)
+                        const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
+                        for (int e = lane; e < 3 * n1; e += 32) Eab[e] = en[ENT_HDR + e];
                         __syncwarp();
-                        const double pref = kc[3];
+                        const double pref = Kc[8 * cc + 3];
+                        const double *Rg = Rb + gg * nb * NR;
                         // (A) aux side: W[bb][c][tuv] = sum E^c_tau E^c_upsilon E^c_phi R[t+tau, u+upsilon, v+phi]
-                        const double *Wsrc = Rb;
+                        const double *Wsrc = Rg;
                         int wstride = NR, cstride = 0;
                         if (lP > 0) {
                             for (int w = lane; w < nb * ncP * npt; w += 32) {
@@ -437,14 +465,14 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                 const int ic = rem / npt, pq = rem - ic * npt;
                                 int t, u, v;
                                 tuv_of(pq, t, u, v);
-                                const signed char *cc = c_cart[lP][ic];
-                                const double *rb = Rb + bb * NR;
+                                const signed char *cc3 = c_cart[lP][ic];
+                                const double *rb = Rg + bb * NR;
                                 double sum = 0.0;
-                                for (int ta2 = cc[0] & 1; ta2 <= cc[0]; ta2 += 2)
-                                    for (int ua = cc[1] & 1; ua <= cc[1]; ua += 2) {
-                                        const double e2 = Ec[cc[0] * (LMAX + 1) + ta2] * Ec[cc[1] * (LMAX + 1) + ua];
-                                        for (int va = cc[2] & 1; va <= cc[2]; va += 2)
-                                            sum = fma(e2 * Ec[cc[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
+                                for (int ta2 = cc3[0] & 1; ta2 <= cc3[0]; ta2 += 2)
+                                    for (int ua = cc3[1] & 1; ua <= cc3[1]; ua += 2) {
+                                        const double e2 = Ec[cc3[0] * (LMAX + 1) + ta2] * Ec[cc3[1] * (LMAX + 1) + ua];
+                                        for (int va = cc3[2] & 1; va <= cc3[2]; va += 2)
+                                            sum = fma(e2 * Ec[cc3[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
                                     }
                                 Wb[w] = sum;
                             }
@@ -458,13 +486,13 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             const double *ex0 = Eab + eoff_sr(ca[0], cb[0], ln);
                             const double *ey0 = Eab + n1 + eoff_sr(ca[1], cb[1], ln);
                             const double *ez0 = Eab + 2 * n1 + eoff_sr(ca[2], cb[2], ln);
-                            int k = loff[ab];
+                            int kk = loff[ab];
                             for (int t = 0; t <= ca[0] + cb[0]; t++)
                                 for (int u = 0; u <= ca[1] + cb[1]; u++) {
                                     const double exy = ex0[t] * ey0[u];
-                                    for (int v = 0; v <= ca[2] + cb[2]; v++, k++) {
-                                        Lc[k] = exy * ez0[v];
-                                        Li[k] = (short)ridx(t, u, v);
+                                    for (int v = 0; v <= ca[2] + cb[2]; v++, kk++) {
+                                        Lc[kk] = exy * ez0[v];
+                                        Li[kk] = (short)ridx(t, u, v);
                                     }
                                 }
                         }
@@ -475,13 +503,13 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             const int bb = rem / ncP, ic = rem - bb * ncP;
                             const double *w = Wsrc + bb * wstride + ic * cstride;
                             double s0 = 0.0, s1 = 0.0;
-                            int k = loff[ab];
+                            int kk = loff[ab];
                             const int ke = loff[ab + 1];
-                            for (; k + 1 < ke; k += 2) {
-                                s0 = fma(Lc[k], w[Li[k]], s0);
-                                s1 = fma(Lc[k + 1], w[Li[k + 1]], s1);
+                            for (; kk + 1 < ke; kk += 2) {
+                                s0 = fma(Lc[kk], w[Li[kk]], s0);
+                                s1 = fma(Lc[kk + 1], w[Li[kk + 1]], s1);
                             }
-                            if (k < ke) s0 = fma(Lc[k], w[Li[k]], s0);
+                            if (kk < ke) s0 = fma(Lc[kk], w[Li[kk]], s0);
                             const int oo = bb * ncomp + ic * ncm * ncn + ab;
                             O[oo] = fma(pref, s0 + s1, O[oo]);
                         }
