@@ -287,13 +287,8 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     d2h = V.numel() * 16 + J.numel() * 16 + L.numel() * 16 + info.numel() * 4
     # max over ranks of the timed region; units summed over ranks
-    tmax, ttot, e2e_max = tot_ms, work * args.steps, sum(e2e_ms)
-    if dist:
-        t = torch.tensor([tot_ms, sum(e2e_ms)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        n = torch.tensor([float(ttot)], dtype=torch.float64, device=dev)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        tmax, e2e_max, ttot = float(t[0]), float(t[1]), float(n[0])
+    from paper_2102_02989_gb300 import shard
+    (tmax, e2e_max), ttot = shard.reduce_timing(dist, [tot_ms, sum(e2e_ms)], work * args.steps, device=dev)
     value = ttot / (tmax * 1e-3)
     e2e_val = ttot / (e2e_max * 1e-3)
     # accuracy against plain FP64 on the same GPU: max |dV| and the HF-energy proxy

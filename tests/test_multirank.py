@@ -1,0 +1,85 @@
+"""The multi-rank path on CPU (gloo, world size 2): the aux-shell shards of a
+j3c computed independently per rank (here by the oracle, the library's GPU
+calls take the same shell ranges) and gathered equal the whole tensor; the
+batch partition covers every cell once; the timing reduction takes the
+maximum time and the summed units over ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2102_02989_gb300 import inputs, shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    p = inputs.tiny(kmesh=(2, 1, 1), lmax_ao=1, lmax_aux=2, natm=2, seed=4)
+    kp = inputs.kpairs_all(2)
+    s0, s1 = shard.aux_shell_shards(p.aux, world)[rank]
+    part = None
+    if s1 > s0:
+        part = oracle.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9),
+                          shells=(s0, s1))
+    got = [None] * world
+    dist.all_gather_object(got, (s0, s1, part))
+    # timing reduction: rank r took 10 + r ms and processed 100 + r units
+    tm, units = shard.reduce_timing(dist, [10.0 + rank, 1.0], 100 + rank)
+    dist.barrier()
+    dist.destroy_process_group()
+    if rank == 0:
+        q.put((got, tm, units))
+
+
+@pytest.fixture(scope="module")
+def orc_built():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def test_aux_shards_gather_to_the_whole(orc_built):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    got, tm, units = q.get(timeout=600)
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    p = inputs.tiny(kmesh=(2, 1, 1), lmax_ao=1, lmax_aux=2, natm=2, seed=4)
+    kp = inputs.kpairs_all(2)
+    full = orc_built.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9))
+    parts = sorted(got, key=lambda x: x[0])
+    assert parts[0][0] == 0 and parts[-1][1] == len(p.aux.l)
+    cat = np.concatenate([x[2] for x in parts if x[2] is not None], axis=1)
+    assert cat.shape == full.shape
+    assert np.max(np.abs(cat - full)) < 1e-13
+    assert tm == [11.0, 1.0] and units == 201.0
+
+
+def test_shard_partitions():
+    p = inputs.config2()
+    for n in (1, 2, 3, 8, 40):
+        sh = shard.aux_shell_shards(p.aux, n)
+        assert len(sh) == n and sh[0][0] == 0 and sh[-1][1] == len(p.aux.l)
+        assert all(a[1] == b[0] for a, b in zip(sh, sh[1:]))
+        assert all(s0 <= s1 for s0, s1 in sh)
+    cells = inputs.config4()
+    for n in (1, 2, 4, 8):
+        cs = shard.cell_shards(cells, n)
+        assert sorted(i for c in cs for i in c) == list(range(len(cells)))
+    assert shard.aux_func_offset(p.aux, len(p.aux.l)) == p.aux.nfunc
