@@ -3,27 +3,17 @@ j3c computed independently per rank (here by the oracle, the library's GPU
 calls take the same shell ranges) and gathered equal the whole tensor; the
 batch partition covers every cell once; the timing reduction takes the
 maximum time and the summed units over ranks."""
-import os
-import socket
-
 import numpy as np
 import pytest
 
 from paper_2102_02989_gb300 import inputs, shard
 
 
-def _free_port():
-    s = socket.socket()
-    s.bind(("127.0.0.1", 0))
-    p = s.getsockname()[1]
-    s.close()
-    return p
-
-
-def _worker(rank, world, port, q):
+def _worker(rank, world, init_file, q):
     import torch.distributed as dist
     import oracle
-    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    # file rendezvous: no port to race for
+    dist.init_process_group("gloo", init_method="file://" + init_file, rank=rank, world_size=world)
     p = inputs.tiny(kmesh=(2, 1, 1), lmax_ao=1, lmax_aux=2, natm=2, seed=4)
     kp = inputs.kpairs_all(2)
     s0, s1 = shard.aux_shell_shards(p.aux, world)[rank]
@@ -48,12 +38,12 @@ def orc_built():
     return oracle
 
 
-def test_aux_shards_gather_to_the_whole(orc_built):
+def test_aux_shards_gather_to_the_whole(orc_built, tmp_path):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    init_file = str(tmp_path / "rendezvous")
+    procs = [ctx.Process(target=_worker, args=(r, 2, init_file, q)) for r in range(2)]
     for pr in procs:
         pr.start()
     got, tm, units = q.get(timeout=600)
