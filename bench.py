@@ -341,6 +341,8 @@ def main():
     if rank == 0 and not args.quick:
         line["per_kmesh"] = per_kmesh(rsgdf, inputs, paths, make, timed, np)
         line["batch"] = batch_bench(rsgdf, inputs, np, torch)
+        if paths["learned-mixed"].get("mlp") is not None:
+            line["rocksalt_chunk"] = rocksalt_bench(rsgdf, inputs, paths, np, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -379,6 +381,41 @@ def per_kmesh(rsgdf, inputs, paths, make, timed, np):
         del Vs
         out["%dx%dx%d" % km] = res
     return out
+
+
+def rocksalt_bench(rsgdf, inputs, paths, np, torch):
+    """The network applied to the 8-atom rocksalt cell (a = 8.0, 4x4x4 mesh,
+    120 AO, 360 aux): j3c of the first atom's 16 aux shells on the 64 diagonal
+    k pairs, learned+mixed vs plain FP64 (one warm-up, median of 3)."""
+    p = inputs.config5()
+    w, gm = rsgdf.rsgdf_params(p.a, p.kmesh, gmesh=p.gmesh, eps_lr=p.eps_lr)
+    kp = inputs.kpairs_diag(p.nk)
+    sh = (0, 16)
+    res = {}
+    outs = {}
+    for name in ("fp64", "learned-mixed"):
+        opt = dict(paths[name], omega=w, gmesh=gm)
+        out = None
+        times = []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = rsgdf.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, shells=sh, out=out, **opt)
+            e1.record()
+            torch.cuda.synchronize()
+            st = rsgdf.rsgdf_last_stats()
+            if rep:
+                times.append(e0.elapsed_time(e1))
+        res[name] = {"ms": statistics.median(times), "sr_ms": st["sr_ms"], "sr_terms": int(st["sr_terms"]),
+                     "sr_items": int(st["sr_items"]), "sr_items_pruned": int(st["sr_items_pruned"])}
+        outs[name] = out
+    res["speedup"] = res["fp64"]["ms"] / res["learned-mixed"]["ms"]
+    res["sr_speedup"] = res["fp64"]["sr_ms"] / res["learned-mixed"]["sr_ms"]
+    res["max_abs_vs_fp64"] = (outs["learned-mixed"] - outs["fp64"]).abs().max().item()
+    res["workload"] = ("rocksalt a=8.0 8-atom cell, 4x4x4, aux shells [0,16) (45 of 360 aux functions), 64 diagonal "
+                       "k pairs, eps 1e-8, G box 7^3, omega %.4f; network trained on other cells" % w)
+    return res
 
 
 def batch_bench(rsgdf, inputs, np, torch):

@@ -224,7 +224,8 @@ int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, i
  * products FP32.  Features per item (RSGDF_MLP_NFEAT): lP, lmu, lnu, ln of
  * the three most diffuse exponents, R12, the distance of the pair centre to
  * the nearest aux image, log10 of the s-type SR integral of that nearest
- * term summed over the primitive combinations, ln Rc_cut.
+ * term summed over the primitive combinations and scaled by the image sum
+ * of the diffuse s-type kernel within the screening radius, ln Rc_cut.
  */
 #define RSGDF_MLP_NFEAT 10
 typedef struct rsgdf_mlp rsgdf_mlp;
@@ -241,9 +242,14 @@ int rsgdf_mlp_get_params(const rsgdf_mlp *m, float *params_out /* host */);
 int rsgdf_mlp_set_margin(rsgdf_mlp *m, float margin);
 /* Screening prediction = network output + X[feature] clamped to [lo, hi]
  * when feature >= 0 (residual model on a physical estimate), or the network
- * output alone when feature = -1 (the default).  Used by j3c only;
- * rsgdf_mlp_forward returns the bare network output.  EINVAL if lo > hi. */
-int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi);
+ * output alone when feature = -1 (the default).  With a base feature an item
+ * of class L = lP + lmu + lnu (features 0..2) is skipped only if, in
+ * addition, X[feature] + guard[L] is below the cut: the estimate with its
+ * own calibrated margin must agree, so the network cannot drop an item the
+ * estimate calls large (guard[L] = +inf: never skip class L).  guard: host
+ * float[10], NULL = all 0.  Used by j3c only; rsgdf_mlp_forward returns the
+ * bare network output.  EINVAL if lo > hi or a guard entry is NaN. */
+int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi, const float *guard);
 /* y[n] = network(X[n][nfeat]) (device pointers) */
 int rsgdf_mlp_forward(const rsgdf_mlp *m, const float *X, long long n, float *y, void *stream);
 /* Expectile loss over (X, t): L = (1/n) sum_s w_s (y_s - t_s)^2 with

@@ -247,6 +247,7 @@ struct rsgdf_mlp {
     float margin;
     int base;                  // feature added to the network output (-1: none)
     float base_lo, base_hi;    // clamp of that feature
+    float guard[rsgdf::LTOT_MAX + 1];   // per class L: skip only if feature + guard[L] < cut as well
     int step;
 };
 
@@ -443,7 +444,7 @@ static int sr_pre(const SRSetup &R, cudaStream_t st, int &nl)
         nl++;
         if (R.mlp) {
             RC(launch_mlp_forward(R.mlp->F, R.mlp->P16, R.mlp->mean, R.mlp->stdv, R.feat, R.n_items, R.pred, st));
-            RC(launch_mlp_mask(R.n_items, SR_NFEAT, R.feat, R.mlp->base, R.mlp->base_lo, R.mlp->base_hi, R.pred,
+            RC(launch_mlp_mask(R.n_items, SR_NFEAT, R.feat, R.mlp->base, R.mlp->base_lo, R.mlp->base_hi, R.mlp->guard, R.pred,
                                R.mlp->margin, R.log10_cut, R.skip, R.counts ? R.counts + 2 * LTOT_MAX + 4 : nullptr,
                                st));
             nl += 2;
@@ -1440,6 +1441,7 @@ int rsgdf_mlp_create(int nfeat, const float *params, const float *mean, const fl
     m->margin = 0.0f;
     m->base = -1;
     m->base_lo = m->base_hi = 0.0f;
+    for (int L = 0; L <= LTOT_MAX; L++) m->guard[L] = 0.0f;
     m->step = 0;
     cudaGetDevice(&m->dev);
     const size_t fb = sizeof(float) * m->np;
@@ -1497,13 +1499,17 @@ int rsgdf_mlp_set_margin(rsgdf_mlp *m, float margin)
     return RSGDF_OK;
 }
 
-int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi)
+int rsgdf_mlp_set_base(rsgdf_mlp *m, int feature, float lo, float hi, const float *guard)
 {
     t_err.clear();
     if (!m || feature < -1 || feature >= m->F || !(lo <= hi)) return fail(RSGDF_EINVAL, "bad base feature or clamp");
+    if (feature >= 0 && m->F < 3) return fail(RSGDF_EINVAL, "the guard needs the l features 0..2");
+    for (int L = 0; L <= LTOT_MAX; L++)
+        if (guard && guard[L] != guard[L]) return fail(RSGDF_EINVAL, "NaN guard");
     m->base = feature;
     m->base_lo = lo;
     m->base_hi = hi;
+    for (int L = 0; L <= LTOT_MAX; L++) m->guard[L] = guard ? guard[L] : 0.0f;
     return RSGDF_OK;
 }
 

