@@ -669,8 +669,34 @@ static int j3c_check(J3cProblem &P, const rsgdf_cell *cell, const rsgdf_basis *a
 }
 
 // Plans and device buffers of a problem that passed j3c_check.
+// SR plan (host screening) and its device tables; needs the k12 groups.
+static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, unsigned long long *dcnt)
+{
+    const Lattice &L = P.L;
+    const HBasis &ao = P.ao, &ax = P.ax;
+    const int Nk = P.Nk, nao = P.nao;
+    const long long m = P.m;
+    const double omega = P.omega;
+    // SR folded sums X[lt][dt][P][mu][nu]
+    plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan);
+    P.nlt = (P.gkey.size() == 1 && P.gkey[0] == 0) ? 1 : Nk;
+    RC(S.alloc(P.X, (size_t)P.nlt * Nk * m));
+    SRExtras ex;
+    if (opts->screening == RSGDF_SCREEN_LEARNED) {
+        if (!opts->mlp) return fail(RSGDF_EINVAL, "learned screening needs opts->mlp");
+        ex.mlp = (const rsgdf_mlp *)opts->mlp;
+        if (ex.mlp->F != SR_NFEAT) return fail(RSGDF_EINVAL, "network input width does not match the SR features");
+        ex.log10_cut = std::log10(opts->eps_screen) - 1.0;
+    }
+    RC(sr_setup(P.sr, S, L, P.plan, P.dao, P.dax, ao, ax, omega, P.X, P.nlt > 1 ? (long long)Nk * m : 0, m,
+                (long long)nao * nao, nao, 1, P.pfunc0, dcnt, ex));
+    return RSGDF_OK;
+}
+
+// with_sr = false leaves the SR plan to a later j3c_prepare_sr (so that the
+// host screening can overlap device work already enqueued).
 static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int npair, const int *kpairs, int mode,
-                       unsigned long long *dcnt)
+                       unsigned long long *dcnt, bool with_sr = true)
 {
     const Lattice &L = P.L;
     const HBasis &ao = P.ao, &ax = P.ax;
@@ -727,21 +753,7 @@ static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int np
         RC(S.upload(dph, ph));
         P.phk = dph;
     }
-    // SR folded sums X[lt][dt][P][mu][nu]
-    if (mode & MODE_SR) {
-        plan_sr3c(L, ao, ax, s0, s1, omega, opts->eps_screen, P.plan);
-        P.nlt = (P.gkey.size() == 1 && P.gkey[0] == 0) ? 1 : Nk;
-        RC(S.alloc(P.X, (size_t)P.nlt * Nk * m));
-        SRExtras ex;
-        if (opts->screening == RSGDF_SCREEN_LEARNED) {
-            if (!opts->mlp) return fail(RSGDF_EINVAL, "learned screening needs opts->mlp");
-            ex.mlp = (const rsgdf_mlp *)opts->mlp;
-            if (ex.mlp->F != SR_NFEAT) return fail(RSGDF_EINVAL, "network input width does not match the SR features");
-            ex.log10_cut = std::log10(opts->eps_screen) - 1.0;
-        }
-        RC(sr_setup(P.sr, S, L, P.plan, P.dao, P.dax, ao, ax, omega, P.X, P.nlt > 1 ? (long long)Nk * m : 0, m,
-                    (long long)nao * nao, nao, 1, P.pfunc0, dcnt, ex));
-    }
+    if ((mode & MODE_SR) && with_sr) RC(j3c_prepare_sr(P, S, opts, dcnt));
     // AFT pair lists (also the overlaps of the G = 0 correction): entries
     // (pair, d, primitive pair) grouped by (pair, BvK cell of d)
     std::vector<int> apoff, alist;
@@ -838,11 +850,10 @@ static int j3c_exec_pre(J3cProblem &P, cudaStream_t st, int &nl)
     return sr_pre(P.sr, st, nl);
 }
 
-// After the SR class launches: G = 0 pieces, phases, AFT, LR contraction.
-static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
+// Pair tables of the AFT lists (also the overlaps of the G = 0 correction),
+// the G = 0 pieces, and the zero padding of the split-TF32 B' tiles.
+static int j3c_exec_tables(J3cProblem &P, cudaStream_t st, int &nl)
 {
-    const int Nk = P.Nk, nao = P.nao, nP = P.nP, NG = P.NG;
-    const long long m = P.m;
     t_timer.begin(PH_AFT);
     RC(launch_pair_prep(P.dao, P.ao.nshell, P.dent, P.nent, P.dalist, P.da9, P.ptab, P.ptab32, P.db9, P.uph, st));
     t_timer.end();
@@ -851,63 +862,116 @@ static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
         t_timer.begin(PH_OTHER);
         k_aux_charge<<<(P.s1 - P.s0 + 63) / 64, 64, 0, st>>>(P.dax, P.s0, P.s1, P.pfunc0, P.SP);
         CU(cudaGetLastError());
-        RC(launch_ovlp_fold(P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Sf, st));
+        RC(launch_ovlp_fold(P.dao, P.ao.nshell, P.nao, P.dent, P.dseg, P.ptab, P.Nk, P.Sf, st));
         t_timer.end();
         nl += 2;
     }
     if (P.Bpl) CU(cudaMemsetAsync(P.Bpl, 0, sizeof(float) * P.nbpl, st));
+    return RSGDF_OK;
+}
+
+// LR contraction of k12 group g (aux transforms, pair transforms, GEMM) added to Tj.
+static int j3c_exec_lr_group(J3cProblem &P, int g, double *Tj, cudaStream_t st, int &nl)
+{
+    const int Nk = P.Nk, nao = P.nao, nP = P.nP, NG = P.NG;
+    const long long m = P.m;
+    const GArgs &Ga = P.garg[g];
+    t_timer.begin(PH_AFT);
+    RC(launch_aux_ft(Ga, P.dax, P.s0, P.s1, P.pfunc0, nP, P.W, nullptr, st));
+    if (P.mixed_aft) {
+        RC(launch_split_a(nP, NG, P.W, P.Apl, st));
+        RC(launch_aft_f32(Ga, P.dao, P.ao.nshell, nao, P.dent, P.nent, P.dseg, P.ptab, P.ptab32, P.db9, P.uph, P.ph0,
+                          Nk, P.Bpl, st));
+    } else {
+        RC(launch_aft(Ga, P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Y, st));
+    }
+    t_timer.end();
+    t_timer.begin(PH_GEMM);
+    if (P.mixed_aft)
+        RC(launch_zgemm_tc2(nP, nao * nao, NG, Nk, P.Apl, P.Bpl, Tj, 2 * m, st));
+    else
+        RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, P.W, P.Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
+    t_timer.end();
+    nl += 3;
+    return RSGDF_OK;
+}
+
+// Phase 1 of a batch of k12 groups (written, or added when the LR part is
+// already in T), with the G = 0 correction.
+static int j3c_exec_phase1(J3cProblem &P, int gb0, int nb, int accumulate, cudaStream_t st, int &nl)
+{
+    const int Nk = P.Nk;
+    const long long m = P.m;
+    t_timer.begin(PH_PHASE);
+    RC(launch_phase1_multi(P.X, m, Nk, P.nlt, P.dk12 + gb0, nb, P.phk, P.T, P.fp32, accumulate, st));
+    nl++;
+    for (int j = 0; j < nb; j++)
+        if (P.gkey[gb0 + j] == 0) {
+            RC(launch_g0_fold(P.T + (size_t)2 * j * Nk * m, m, Nk, P.nP, P.nao, P.SP, P.Sf, P.g0fac, st));
+            nl++;
+        }
+    t_timer.end();
+    return RSGDF_OK;
+}
+
+static int j3c_exec_x_to_df(J3cProblem &P, cudaStream_t st, int &nl)
+{
     if (P.fp32 && (P.mode & MODE_SR)) {
         t_timer.begin(PH_PHASE);
-        RC(launch_x_to_df(P.X, (long long)P.nlt * Nk * m, st));   // X to double-float pairs, in place
+        RC(launch_x_to_df(P.X, (long long)P.nlt * P.Nk * P.m, st));   // X to double-float pairs, in place
         t_timer.end();
         nl++;
     }
+    return RSGDF_OK;
+}
+
+// After the SR class launches: G = 0 pieces, phases, AFT, LR contraction.
+static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
+{
+    const int Nk = P.Nk;
+    const long long m = P.m;
+    RC(j3c_exec_tables(P, st, nl));
+    RC(j3c_exec_x_to_df(P, st, nl));
     const int G = (int)P.gkey.size();
     for (int gb0 = 0; gb0 < G; gb0 += P.B) {
         const int nb = std::min(P.B, G - gb0);
-        if (P.mode & MODE_SR) {
-            t_timer.begin(PH_PHASE);
-            RC(launch_phase1_multi(P.X, m, Nk, P.nlt, P.dk12 + gb0, nb, P.phk, P.T, P.fp32, st));
-            nl++;
-            for (int j = 0; j < nb; j++)
-                if (P.gkey[gb0 + j] == 0) {
-                    RC(launch_g0_fold(P.T + (size_t)2 * j * Nk * m, m, Nk, nP, nao, P.SP, P.Sf, P.g0fac, st));
-                    nl++;
-                }
-            t_timer.end();
-        } else {
+        if (P.mode & MODE_SR)
+            RC(j3c_exec_phase1(P, gb0, nb, 0, st, nl));
+        else
             CU(cudaMemsetAsync(P.T, 0, sizeof(double) * 2 * nb * Nk * m, st));
-        }
-        if (P.mode & MODE_LR) {
-            for (int j = 0; j < nb; j++) {
-                const GArgs &Ga = P.garg[gb0 + j];
-                double *Tj = P.T + (size_t)2 * j * Nk * m;
-                t_timer.begin(PH_AFT);
-                RC(launch_aux_ft(Ga, P.dax, P.s0, P.s1, P.pfunc0, nP, P.W, nullptr, st));
-                if (P.mixed_aft) {
-                    RC(launch_split_a(nP, NG, P.W, P.Apl, st));
-                    RC(launch_aft_f32(Ga, P.dao, P.ao.nshell, nao, P.dent, P.nent, P.dseg, P.ptab, P.ptab32, P.db9,
-                                      P.uph, P.ph0, Nk, P.Bpl, st));
-                } else {
-                    RC(launch_aft(Ga, P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Y, st));
-                }
-                t_timer.end();
-                t_timer.begin(PH_GEMM);
-                if (P.mixed_aft)
-                    RC(launch_zgemm_tc2(nP, nao * nao, NG, Nk, P.Apl, P.Bpl, Tj, 2 * m, st));
-                else
-                    RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, P.W, P.Y, (long long)2 * NG * nao * nao, Tj, 2 * m,
-                                       st));
-                t_timer.end();
-                nl += 3;
-            }
-        }
+        if (P.mode & MODE_LR)
+            for (int j = 0; j < nb; j++) RC(j3c_exec_lr_group(P, gb0 + j, P.T + (size_t)2 * j * Nk * m, st, nl));
         t_timer.begin(PH_PHASE);
         RC(launch_phase2_multi(P.T, m, Nk, P.dgoff + gb0, nb, P.dplist, P.dpk2, P.phk, V,
                                (P.mode == MODE_LR) ? 1 : 0, P.fp32, st));
         t_timer.end();
         nl++;
     }
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+// LR-first order (every k12 group fits T at once): the LR contractions go
+// into T before the SR plan exists, so the host screening runs while the
+// device computes them; j3c_exec_post_lr_done finishes after the SR launches.
+static int j3c_exec_lr_first(J3cProblem &P, cudaStream_t st, int &nl)
+{
+    const int G = (int)P.gkey.size();
+    RC(j3c_exec_tables(P, st, nl));
+    CU(cudaMemsetAsync(P.T, 0, sizeof(double) * 2 * (size_t)G * P.Nk * P.m, st));
+    for (int g = 0; g < G; g++) RC(j3c_exec_lr_group(P, g, P.T + (size_t)2 * g * P.Nk * P.m, st, nl));
+    return RSGDF_OK;
+}
+
+static int j3c_exec_post_lr_done(J3cProblem &P, double *V, cudaStream_t st, int &nl)
+{
+    const int G = (int)P.gkey.size();
+    RC(j3c_exec_x_to_df(P, st, nl));
+    RC(j3c_exec_phase1(P, 0, G, 1, st, nl));
+    t_timer.begin(PH_PHASE);
+    RC(launch_phase2_multi(P.T, P.m, P.Nk, P.dgoff, G, P.dplist, P.dpk2, P.phk, V, 0, P.fp32, st));
+    t_timer.end();
+    nl++;
     CU(cudaGetLastError());
     return RSGDF_OK;
 }
@@ -938,14 +1002,20 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     unsigned long long *dcnt, *dq;
     RC(S.alloc(dcnt, 2 * LTOT_MAX + 6));
     RC(S.alloc(dq, LTOT_MAX + 1));
-    RC(j3c_prepare(P, S, opts, npair, kpairs, mode, dcnt));
-    std::vector<SRClassLaunch> cl;
-    if (mode & MODE_SR) RC(sr_merge({&P.sr}, S, st, cl));
+    RC(j3c_prepare(P, S, opts, npair, kpairs, mode, dcnt, false));
     int nl = 0;
     CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
+    const bool lr_first = (mode == (MODE_SR | MODE_LR)) && P.B >= (int)P.gkey.size();
+    if (lr_first) RC(j3c_exec_lr_first(P, st, nl));   // device busy while the host plans the SR sums
+    if (mode & MODE_SR) RC(j3c_prepare_sr(P, S, opts, dcnt));
+    std::vector<SRClassLaunch> cl;
+    if (mode & MODE_SR) RC(sr_merge({&P.sr}, S, st, cl));
     RC(j3c_exec_pre(P, st, nl));
     RC(sr_run(cl, dq, st, nl));
-    RC(j3c_exec_post(P, V, st, nl));
+    if (lr_first)
+        RC(j3c_exec_post_lr_done(P, V, st, nl));
+    else
+        RC(j3c_exec_post(P, V, st, nl));
     RC(stats_counts(dcnt, st));
     t_stats.sr_items = P.plan.n_items;
     t_stats.omega = P.omega;

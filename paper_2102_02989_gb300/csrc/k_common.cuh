@@ -199,7 +199,7 @@ int tc_status_take(int *flag);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
 int launch_x_to_df(double *X, long long n, cudaStream_t st);
 int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
-                        double *T, int fp32, cudaStream_t st);
+                        double *T, int fp32, int accumulate, cudaStream_t st);
 int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,
                         const int *pk2, const void *ph, double *V, int accumulate, int fp32, cudaStream_t st);
 

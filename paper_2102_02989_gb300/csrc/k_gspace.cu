@@ -737,7 +737,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__ X, long long m, int Nk, int nlt,
                                                       const int *__restrict__ k12list, int nk12,
                                                       const typename PhT<R>::type *__restrict__ ph,
-                                                      double2 *__restrict__ T)
+                                                      double2 *__restrict__ T, int accumulate)
 {
     const long long n = (long long)Nk * m;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
@@ -761,7 +761,17 @@ __global__ void __launch_bounds__(256) k_phase1_multi(const double *__restrict__
             }
 #pragma unroll
             for (int j = 0; j < KB; j++)
-                if (j0 + j < nk12) T[((long long)(j0 + j) * Nk + dt) * m + i] = make_double2((double)ar[j], (double)ai[j]);
+                if (j0 + j < nk12) {
+                    double2 *t = &T[((long long)(j0 + j) * Nk + dt) * m + i];
+                    if (accumulate) {
+                        double2 v = *t;
+                        v.x += (double)ar[j];
+                        v.y += (double)ai[j];
+                        *t = v;
+                    } else {
+                        *t = make_double2((double)ar[j], (double)ai[j]);
+                    }
+                }
         }
     }
 }
@@ -872,7 +882,8 @@ constexpr int DF_KB = 8, DF_PB = 8;
 
 __global__ void __launch_bounds__(256) k_phase1_df(const float2 *__restrict__ X, long long m, int Nk, int nlt,
                                                    const int *__restrict__ k12list, int nk12,
-                                                   const float4 *__restrict__ ph, double2 *__restrict__ T)
+                                                   const float4 *__restrict__ ph, double2 *__restrict__ T,
+                                                   int accumulate)
 {
     const long long n = (long long)Nk * m;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
@@ -896,7 +907,17 @@ __global__ void __launch_bounds__(256) k_phase1_df(const float2 *__restrict__ X,
             }
 #pragma unroll
             for (int j = 0; j < DF_KB; j++)
-                if (j0 + j < nk12) T[((long long)(j0 + j) * Nk + dt) * m + i] = make_double2(df_to(ar[j]), df_to(ai[j]));
+                if (j0 + j < nk12) {
+                    double2 *t = &T[((long long)(j0 + j) * Nk + dt) * m + i];
+                    if (accumulate) {
+                        double2 v = *t;
+                        v.x += df_to(ar[j]);
+                        v.y += df_to(ai[j]);
+                        *t = v;
+                    } else {
+                        *t = make_double2(df_to(ar[j]), df_to(ai[j]));
+                    }
+                }
         }
     }
 }
@@ -954,17 +975,18 @@ int launch_x_to_df(double *X, long long n, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
-// fp32 = 1: X already in double-float pairs (launch_x_to_df), ph = float4 table
+// fp32 = 1: X already in double-float pairs (launch_x_to_df), ph = float4 table;
+// accumulate = 1: T += (the LR part is already there)
 int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
-                        double *T, int fp32, cudaStream_t st)
+                        double *T, int fp32, int accumulate, cudaStream_t st)
 {
     const long long n = (long long)Nk * m;
     if (fp32)
         k_phase1_df<<<grid_for(n), 256, 0, st>>>((const float2 *)X, m, Nk, nlt, k12list, nk12, (const float4 *)ph,
-                                                 (double2 *)T);
+                                                 (double2 *)T, accumulate);
     else
         k_phase1_multi<double><<<grid_for(n), 256, 0, st>>>(X, m, Nk, nlt, k12list, nk12, (const double2 *)ph,
-                                                             (double2 *)T);
+                                                             (double2 *)T, accumulate);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
