@@ -647,6 +647,12 @@ struct J3cProblem {
     int B = 1;
     double *T = nullptr;
     std::vector<GArgs> garg;
+    // separable-DFT phase contractions (every k12 present, T holds them all)
+    bool dft = false;
+    double *Z = nullptr, *dtw = nullptr;
+    float *dtw4 = nullptr;   // double-float twiddles (mixed path)
+    int *dpk12 = nullptr, *dpk2all = nullptr;
+    int npair = 0;
     long long aft_units = 0, lr_flops = 0;
 };
 
@@ -832,11 +838,45 @@ static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int np
             P.garg.push_back(Ga);
         }
     }
-    // k12 groups in batches whose T fits a fixed budget
+    // k12 groups in batches whose T fits a fixed budget (16 GiB of the device's HBM)
     const int G = (int)P.gkey.size();
     const long long tbytes = (long long)Nk * m * 16;
-    P.B = (int)std::max(1LL, std::min<long long>(G, (4LL << 30) / std::max(tbytes, 1LL)));
+    P.B = (int)std::max(1LL, std::min<long long>(G, (16LL << 30) / std::max(tbytes, 1LL)));
     RC(S.alloc(P.T, (size_t)2 * P.B * Nk * m));
+    // separable DFTs for the phase contractions: every k12 group present, all
+    // in T at once, a mesh large enough to gain, and most k2 per group wanted
+    P.npair = npair;
+    P.dft = (G == Nk) && (P.B >= G) && (Nk >= 16) && ((long long)npair * 4 >= (long long)Nk * Nk) &&
+            L.nk[0] <= DFT_NMAX_HOST && L.nk[1] <= DFT_NMAX_HOST && L.nk[2] <= DFT_NMAX_HOST;
+    if (P.dft) {
+        std::vector<double> tw((size_t)3 * DFT_NMAX_HOST * DFT_NMAX_HOST * 2, 0.0);
+        for (int d = 0; d < 3; d++) {
+            const int N = L.nk[d];
+            for (int q = 0; q < N; q++)
+                for (int n = 0; n < N; n++) {
+                    const long double ang = 2.0L * 3.141592653589793238462643383279502884L * ((q * n) % N) / N;
+                    const size_t o = 2 * ((size_t)d * DFT_NMAX_HOST * DFT_NMAX_HOST + q * N + n);
+                    tw[o] = (double)cosl(ang);
+                    tw[o + 1] = (double)sinl(ang);
+                }
+        }
+        RC(S.upload(P.dtw, tw));
+        std::vector<float> tw4(2 * tw.size());
+        for (size_t e = 0; e < tw.size(); e++) {
+            const float h = (float)tw[e];
+            tw4[2 * e] = h;
+            tw4[2 * e + 1] = (float)(tw[e] - (double)h);
+        }
+        RC(S.upload(P.dtw4, tw4));
+        std::vector<int> a12(npair), a2(npair);
+        for (int p = 0; p < npair; p++) {
+            a12[p] = k12_of(L, kpairs[2 * p], kpairs[2 * p + 1]);
+            a2[p] = kpairs[2 * p + 1];
+        }
+        RC(S.upload(P.dpk12, a12));
+        RC(S.upload(P.dpk2all, a2));
+        if (mode & MODE_SR) RC(S.alloc(P.Z, (size_t)2 * Nk * Nk * m));
+    }
     P.aft_units = (mode & MODE_LR) ? (long long)ent.size() * NG * (long long)G : 0;
     P.lr_flops = (mode & MODE_LR) ? 8LL * nP * nao * nao * NG * Nk * (long long)G : 0;
     return RSGDF_OK;
@@ -903,8 +943,27 @@ static int j3c_exec_phase1(J3cProblem &P, int gb0, int nb, int accumulate, cudaS
     const int Nk = P.Nk;
     const long long m = P.m;
     t_timer.begin(PH_PHASE);
-    RC(launch_phase1_multi(P.X, m, Nk, P.nlt, P.dk12 + gb0, nb, P.phk, P.T, P.fp32, accumulate, st));
-    nl++;
+    if (P.dft) {
+        // T[k12][dt] (+)= sum_lt e^{-i k12.lt} X[lt][dt]: DFT over the lt mesh axes (FP64)
+        double *Zb = accumulate ? P.Z : P.T;
+        const long long n = (long long)Nk * Nk * m;
+        if (P.fp32) {   // double-float passes on the FP32 pipes
+            RC(launch_real_to_df(P.X, Zb, n, st));
+            RC(launch_dft_mesh_df(Zb, P.L.nk, (long long)Nk * m, 1, P.dtw4, 1, st));
+            if (accumulate)
+                RC(launch_add_df(P.T, P.Z, n, st));
+            else
+                RC(launch_convert_df(P.T, n, 0, st));
+        } else {
+            RC(launch_real_to_complex(P.X, Zb, n, st));
+            RC(launch_dft_mesh(Zb, P.L.nk, (long long)Nk * m, 1, P.dtw, 1, st));
+            if (accumulate) RC(launch_add_complex(P.T, P.Z, n, st));
+        }
+        nl += 5;
+    } else {
+        RC(launch_phase1_multi(P.X, m, Nk, P.nlt, P.dk12 + gb0, nb, P.phk, P.T, P.fp32, accumulate, st));
+        nl++;
+    }
     for (int j = 0; j < nb; j++)
         if (P.gkey[gb0 + j] == 0) {
             RC(launch_g0_fold(P.T + (size_t)2 * j * Nk * m, m, Nk, P.nP, P.nao, P.SP, P.Sf, P.g0fac, st));
@@ -916,12 +975,36 @@ static int j3c_exec_phase1(J3cProblem &P, int gb0, int nb, int accumulate, cudaS
 
 static int j3c_exec_x_to_df(J3cProblem &P, cudaStream_t st, int &nl)
 {
-    if (P.fp32 && (P.mode & MODE_SR)) {
+    if (P.fp32 && (P.mode & MODE_SR) && !P.dft) {
         t_timer.begin(PH_PHASE);
         RC(launch_x_to_df(P.X, (long long)P.nlt * P.Nk * P.m, st));   // X to double-float pairs, in place
         t_timer.end();
         nl++;
     }
+    return RSGDF_OK;
+}
+
+// Phase 2 of a batch of k12 groups into V.
+static int j3c_exec_phase2(J3cProblem &P, int gb0, int nb, double *V, cudaStream_t st, int &nl)
+{
+    const int acc = (P.mode == MODE_LR) ? 1 : 0;
+    t_timer.begin(PH_PHASE);
+    if (P.dft) {
+        // V[pair] (+)= sum_dt e^{+i k2.dt} T[k12][dt]: DFT over the dt mesh axes, then the pairs
+        if (P.fp32) {
+            RC(launch_convert_df(P.T, (long long)P.Nk * P.Nk * P.m, 1, st));
+            RC(launch_dft_mesh_df(P.T, P.L.nk, P.m, P.Nk, P.dtw4, 0, st));
+            RC(launch_scatter_pairs_df(P.T, P.m, P.Nk, P.npair, P.dpk12, P.dpk2all, V, acc, st));
+        } else {
+            RC(launch_dft_mesh(P.T, P.L.nk, P.m, P.Nk, P.dtw, 0, st));
+            RC(launch_scatter_pairs(P.T, P.m, P.Nk, P.npair, P.dpk12, P.dpk2all, V, acc, st));
+        }
+        nl += 5;
+    } else {
+        RC(launch_phase2_multi(P.T, P.m, P.Nk, P.dgoff + gb0, nb, P.dplist, P.dpk2, P.phk, V, acc, P.fp32, st));
+        nl++;
+    }
+    t_timer.end();
     return RSGDF_OK;
 }
 
@@ -941,11 +1024,7 @@ static int j3c_exec_post(J3cProblem &P, double *V, cudaStream_t st, int &nl)
             CU(cudaMemsetAsync(P.T, 0, sizeof(double) * 2 * nb * Nk * m, st));
         if (P.mode & MODE_LR)
             for (int j = 0; j < nb; j++) RC(j3c_exec_lr_group(P, gb0 + j, P.T + (size_t)2 * j * Nk * m, st, nl));
-        t_timer.begin(PH_PHASE);
-        RC(launch_phase2_multi(P.T, m, Nk, P.dgoff + gb0, nb, P.dplist, P.dpk2, P.phk, V,
-                               (P.mode == MODE_LR) ? 1 : 0, P.fp32, st));
-        t_timer.end();
-        nl++;
+        RC(j3c_exec_phase2(P, gb0, nb, V, st, nl));
     }
     CU(cudaGetLastError());
     return RSGDF_OK;
@@ -968,10 +1047,7 @@ static int j3c_exec_post_lr_done(J3cProblem &P, double *V, cudaStream_t st, int 
     const int G = (int)P.gkey.size();
     RC(j3c_exec_x_to_df(P, st, nl));
     RC(j3c_exec_phase1(P, 0, G, 1, st, nl));
-    t_timer.begin(PH_PHASE);
-    RC(launch_phase2_multi(P.T, P.m, P.Nk, P.dgoff, G, P.dplist, P.dpk2, P.phk, V, 0, P.fp32, st));
-    t_timer.end();
-    nl++;
+    RC(j3c_exec_phase2(P, 0, G, V, st, nl));
     CU(cudaGetLastError());
     return RSGDF_OK;
 }

@@ -197,6 +197,20 @@ long long tc_b_floats(int N, int K, int batch);
 long long tc_a_floats(int M, int K);
 int tc_status_take(int *flag);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
+constexpr int DFT_NMAX_HOST = 16;   // longest mesh axis of the DFT path
+int launch_dft_mesh(double *T, const int nk[3], long long slab, long long nrep, const double *tw, int conj,
+                    cudaStream_t st);
+int launch_real_to_complex(const double *X, double *Z, long long n, cudaStream_t st);
+int launch_add_complex(double *T, const double *Z, long long n, cudaStream_t st);
+int launch_scatter_pairs(const double *T, long long m, int Nk, int npair, const int *pk12, const int *pk2, double *V,
+                         int accumulate, cudaStream_t st);
+int launch_dft_mesh_df(double *T, const int nk[3], long long slab, long long nrep, const float *tw4, int conj,
+                       cudaStream_t st);
+int launch_real_to_df(const double *X, double *Z, long long n, cudaStream_t st);
+int launch_convert_df(double *T, long long n, int to_df, cudaStream_t st);
+int launch_add_df(double *T, const double *Z, long long n, cudaStream_t st);
+int launch_scatter_pairs_df(const double *T, long long m, int Nk, int npair, const int *pk12, const int *pk2, double *V,
+                            int accumulate, cudaStream_t st);
 int launch_x_to_df(double *X, long long n, cudaStream_t st);
 int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int *k12list, int nk12, const void *ph,
                         double *T, int fp32, int accumulate, cudaStream_t st);

@@ -968,6 +968,246 @@ __global__ void __launch_bounds__(256) k_phase2_df(const double2 *__restrict__ T
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bloch-phase contractions as separable DFTs over the k mesh.  When every k12
+// (phase 1) or every k2 (phase 2) is wanted, sum_{c} e^{-+i k.c} f(c) over the
+// BvK cells c = (c0, c1, c2) factorises into three passes of length-N_d DFTs
+// along the mesh axes: N0 + N1 + N2 complex multiply-adds per output instead
+// of N0 N1 N2.  Each pass is in place on complex FP64 data laid out as
+// [rep][j0][j1][j2][slab]; a thread transforms one line.  tw[q N + n] =
+// e^{+2 pi i q n / N} (host table, exact angle reduction), conj = 1 for the
+// negative exponent.
+// ---------------------------------------------------------------------------
+constexpr int DFT_NMAX = 16;
+
+__global__ void __launch_bounds__(256) k_dft_axis(double2 *__restrict__ T, long long S, long long nouter, int N,
+                                                  const double2 *__restrict__ tw, int conj)
+{
+    const long long nl = nouter * S;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nl; id += (long long)gridDim.x * blockDim.x) {
+        const long long outer = id / S, inner = id - outer * S;
+        double2 *line = T + outer * N * S + inner;
+        double2 v[DFT_NMAX];
+        for (int n = 0; n < N; n++) v[n] = line[n * S];
+        for (int q = 0; q < N; q++) {
+            double re = 0.0, im = 0.0;
+            for (int n = 0; n < N; n++) {
+                const double2 w = __ldg(&tw[q * N + n]);
+                const double wy = conj ? -w.y : w.y;
+                re = fma(w.x, v[n].x, fma(-wy, v[n].y, re));
+                im = fma(w.x, v[n].y, fma(wy, v[n].x, im));
+            }
+            line[q * S] = make_double2(re, im);
+        }
+    }
+}
+
+__global__ void k_real_to_complex(const double *__restrict__ X, double2 *__restrict__ Z, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Z[i] = make_double2(X[i], 0.0);
+}
+
+__global__ void k_add_complex(double2 *__restrict__ T, const double2 *__restrict__ Z, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 t = T[i];
+        const double2 z = Z[i];
+        t.x += z.x;
+        t.y += z.y;
+        T[i] = t;
+    }
+}
+
+// V[p][i] (+)= T[k12(p)][k2(p)][i]
+__global__ void k_scatter_pairs(const double2 *__restrict__ T, long long m, int Nk, const int *__restrict__ pk12,
+                                const int *__restrict__ pk2, double2 *__restrict__ V, int accumulate)
+{
+    const int p = blockIdx.y;
+    const double2 *src = T + ((long long)pk12[p] * Nk + pk2[p]) * m;
+    double2 *dst = V + (long long)p * m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        double2 v = src[i];
+        if (accumulate) {
+            const double2 o = dst[i];
+            v.x += o.x;
+            v.y += o.y;
+        }
+        dst[i] = v;
+    }
+}
+
+// In-place 3-D DFT over the mesh index of T[rep][j0][j1][j2][slab] (complex).
+int launch_dft_mesh(double *T, const int nk[3], long long slab, long long nrep, const double *tw, int conj,
+                    cudaStream_t st)
+{
+    long long inner = slab;
+    for (int d = 2; d >= 0; d--) {
+        const int N = nk[d];
+        if (N > DFT_NMAX) return RSGDF_EINVAL;
+        long long outer = nrep;
+        for (int e = 0; e < d; e++) outer *= nk[e];
+        if (N > 1) {
+            const long long nl = outer * inner;
+            k_dft_axis<<<grid_for(nl), 256, 0, st>>>((double2 *)T, inner, outer, N,
+                                                     (const double2 *)tw + d * DFT_NMAX * DFT_NMAX, conj);
+            if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
+        }
+        inner *= N;
+    }
+    return RSGDF_OK;
+}
+
+int launch_real_to_complex(const double *X, double *Z, long long n, cudaStream_t st)
+{
+    k_real_to_complex<<<grid_for(n), 256, 0, st>>>(X, (double2 *)Z, n);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_add_complex(double *T, const double *Z, long long n, cudaStream_t st)
+{
+    k_add_complex<<<grid_for(n), 256, 0, st>>>((double2 *)T, (const double2 *)Z, n);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_scatter_pairs(const double *T, long long m, int Nk, int npair, const int *pk12, const int *pk2, double *V,
+                         int accumulate, cudaStream_t st)
+{
+    if (npair <= 0) return RSGDF_OK;
+    dim3 grid((unsigned)std::min<long long>((m + 255) / 256, 1024), npair);
+    k_scatter_pairs<<<grid, 256, 0, st>>>((const double2 *)T, m, Nk, pk12, pk2, (double2 *)V, accumulate);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+// Mixed path: the same DFT passes in double-float arithmetic; complex values
+// stored as float4 (re hi, re lo, im hi, im lo) in the same 16 bytes as a
+// double2, so the format changes in place.
+__device__ __forceinline__ float4 df4_from(double2 v)
+{
+    const dflt r = df_from(v.x), i = df_from(v.y);
+    return make_float4(r.h, r.l, i.h, i.l);
+}
+
+__global__ void __launch_bounds__(256) k_dft_axis_df(float4 *__restrict__ T, long long S, long long nouter, int N,
+                                                     const float4 *__restrict__ tw, int conj)
+{
+    const long long nl = nouter * S;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nl; id += (long long)gridDim.x * blockDim.x) {
+        const long long outer = id / S, inner = id - outer * S;
+        float4 *line = T + outer * N * S + inner;
+        float4 v[DFT_NMAX];
+        for (int n = 0; n < N; n++) v[n] = line[n * S];
+        for (int q = 0; q < N; q++) {
+            dflt re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+            for (int n = 0; n < N; n++) {
+                const float4 w = __ldg(&tw[q * N + n]);
+                const dflt c = {w.x, w.y};
+                const dflt sn = conj ? dflt{-w.z, -w.w} : dflt{w.z, w.w};
+                const dflt vr = {v[n].x, v[n].y}, vi = {v[n].z, v[n].w};
+                re = df_add(re, df_add(df_mul(c, vr), df_neg(df_mul(sn, vi))));
+                im = df_add(im, df_add(df_mul(c, vi), df_mul(sn, vr)));
+            }
+            line[q * S] = make_float4(re.h, re.l, im.h, im.l);
+        }
+    }
+}
+
+__global__ void k_real_to_df(const double *__restrict__ X, float4 *__restrict__ Z, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Z[i] = df4_from(make_double2(X[i], 0.0));
+}
+
+// dir = 1: double2 -> double-float in place; dir = 0: back
+__global__ void k_convert_df(double2 *T, long long n, int dir)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (dir) {
+            const double2 v = T[i];
+            reinterpret_cast<float4 *>(T)[i] = df4_from(v);
+        } else {
+            const float4 v = reinterpret_cast<const float4 *>(T)[i];
+            T[i] = make_double2(df_to({v.x, v.y}), df_to({v.z, v.w}));
+        }
+    }
+}
+
+__global__ void k_add_df(double2 *__restrict__ T, const float4 *__restrict__ Z, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 t = T[i];
+        const float4 z = Z[i];
+        t.x += df_to({z.x, z.y});
+        t.y += df_to({z.z, z.w});
+        T[i] = t;
+    }
+}
+
+__global__ void k_scatter_pairs_df(const float4 *__restrict__ T, long long m, int Nk, const int *__restrict__ pk12,
+                                   const int *__restrict__ pk2, double2 *__restrict__ V, int accumulate)
+{
+    const int p = blockIdx.y;
+    const float4 *src = T + ((long long)pk12[p] * Nk + pk2[p]) * m;
+    double2 *dst = V + (long long)p * m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        const float4 z = src[i];
+        double2 v = make_double2(df_to({z.x, z.y}), df_to({z.z, z.w}));
+        if (accumulate) {
+            const double2 o = dst[i];
+            v.x += o.x;
+            v.y += o.y;
+        }
+        dst[i] = v;
+    }
+}
+
+int launch_dft_mesh_df(double *T, const int nk[3], long long slab, long long nrep, const float *tw4, int conj,
+                       cudaStream_t st)
+{
+    long long inner = slab;
+    for (int d = 2; d >= 0; d--) {
+        const int N = nk[d];
+        if (N > DFT_NMAX) return RSGDF_EINVAL;
+        long long outer = nrep;
+        for (int e = 0; e < d; e++) outer *= nk[e];
+        if (N > 1) {
+            const long long nl = outer * inner;
+            k_dft_axis_df<<<grid_for(nl), 256, 0, st>>>((float4 *)T, inner, outer, N,
+                                                        (const float4 *)tw4 + d * DFT_NMAX * DFT_NMAX, conj);
+            if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
+        }
+        inner *= N;
+    }
+    return RSGDF_OK;
+}
+
+int launch_real_to_df(const double *X, double *Z, long long n, cudaStream_t st)
+{
+    k_real_to_df<<<grid_for(n), 256, 0, st>>>(X, (float4 *)Z, n);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_convert_df(double *T, long long n, int to_df, cudaStream_t st)
+{
+    k_convert_df<<<grid_for(n), 256, 0, st>>>((double2 *)T, n, to_df);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_add_df(double *T, const double *Z, long long n, cudaStream_t st)
+{
+    k_add_df<<<grid_for(n), 256, 0, st>>>((double2 *)T, (const float4 *)Z, n);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
+int launch_scatter_pairs_df(const double *T, long long m, int Nk, int npair, const int *pk12, const int *pk2, double *V,
+                            int accumulate, cudaStream_t st)
+{
+    if (npair <= 0) return RSGDF_OK;
+    dim3 grid((unsigned)std::min<long long>((m + 255) / 256, 1024), npair);
+    k_scatter_pairs_df<<<grid, 256, 0, st>>>((const float4 *)T, m, Nk, pk12, pk2, (double2 *)V, accumulate);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
 int launch_x_to_df(double *X, long long n, cudaStream_t st)
 {
     if (n <= 0) return RSGDF_OK;

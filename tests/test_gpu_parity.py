@@ -224,3 +224,33 @@ def test_mixed_sr_phases_fp64_grade(rs, orc, km, sh):
                               eps_lr=p.eps_lr, precision=rs.RSGDF_MIXED))
     assert np.max(np.abs(ref)) > 0.1
     assert np.max(np.abs(got - ref)) < TOL
+
+
+@pytest.mark.parametrize("km", [(3, 3, 2), (4, 2, 2)])
+def test_phase_contractions_as_mesh_dfts(rs, orc, km):
+    """With every k pair requested on a mesh of 16 or more points the phase
+    contractions run as separable DFTs over the mesh axes (odd and even
+    axis lengths here): SR + G0 + LR, the LR-only accumulate path and the
+    mixed path against the oracle."""
+    import torch
+    p = inputs.tiny(kmesh=km, lmax_ao=1, lmax_aux=2, natm=2, seed=6)
+    nk = int(np.prod(km))
+    kp = inputs.kpairs_all(nk)
+    w = 0.9
+    gm = gmesh_for(p.a, w, 1e-14, km)
+    opt = dict(omega=w, gmesh=gm, eps_screen=1e-12, eps_lr=1e-14)
+    ref = orc.j3c(p.a, km, p.ao, p.aux, w, kp, eps_sr=1e-12, eps_lr=1e-14, gmesh=gm)
+    got = _np(rs.rsgdf_j3c(p.a, km, p.ao, p.aux, kp, **opt))
+    assert np.max(np.abs(ref)) > 0.1
+    assert np.max(np.abs(got - ref)) < TOL
+    lref = orc.j3c(p.a, km, p.ao, p.aux, w, kp, eps_lr=1e-14, gmesh=gm, sr=False, g0=False)
+    out = torch.full(ref.shape, 0.5 + 0.25j, dtype=torch.complex128, device="cuda")
+    lgot = _np(rs.rsgdf_j3c_lr(p.a, km, p.ao, p.aux, kp, out=out, **opt)) - (0.5 + 0.25j)
+    assert np.max(np.abs(lgot - lref)) < TOL
+    mix = _np(rs.rsgdf_j3c(p.a, km, p.ao, p.aux, kp, precision=rs.RSGDF_MIXED, **opt))
+    rs.rsgdf_sync_status()
+    assert np.max(np.abs(mix - ref)) < MIXED_REL * np.max(np.abs(ref))
+    # the SR part of the mixed path (double-float DFT passes) stays FP64-grade
+    sref = orc.j3c(p.a, km, p.ao, p.aux, w, kp, eps_sr=1e-12, eps_lr=1e-14, gmesh=gm, lr=False)
+    smix = _np(rs.rsgdf_j3c_sr(p.a, km, p.ao, p.aux, kp, precision=rs.RSGDF_MIXED, **opt))
+    assert np.max(np.abs(smix - sref)) < TOL
