@@ -25,6 +25,7 @@ namespace rsgdf {
 
 constexpr int TC_THREADS = 128;
 constexpr long long TC_SPIN = 1LL << 26;   // bounded mbarrier wait
+constexpr int TC_STAGES = 2;               // operand stages of the bulk-copy pipeline (48 KB each; 2 CTAs per SM)
 
 __device__ int g_tc_status;      // set to 1 when a bounded wait gives up
 
@@ -326,13 +327,14 @@ __device__ __forceinline__ void issue_chunk_mma(uint32_t tmem_acc, uint32_t sa, 
     }
 }
 
-// C[b][m][n] += A^T B from pre-split tiles; 2-stage bulk-copy pipeline and two
-// tensor-memory accumulators (chunk c in accumulator c & 1).
+// C[b][m][n] += A^T B from pre-split tiles; TC_STAGES-stage bulk-copy pipeline
+// (operands requested TC_STAGES - 1 chunks ahead) and two tensor-memory
+// accumulators (chunk c in accumulator c & 1).
 __global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc, const float *Ap, const float *Bp,
                                                           int nnt, double2 *C, long long strideC)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long full[2], done[2];
+    __shared__ __align__(8) unsigned long long full[TC_STAGES], done[TC_STAGES];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < TC_STAGES; s++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&full[s])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&done[s])), "r"(1));
         }
@@ -358,42 +360,52 @@ __global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc,
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
     const float *Ablk = Ap + (long long)mt * nkc * TC_ABLK;
     const float *Bblk = Bp + ((long long)b * nnt + nt) * nkc * TC_BBLK;
+    // chunk c lives in stage c % TC_STAGES; its barriers complete once per use
+    // of the stage, so the k-th use waits on parity k & 1
+    int issued = 0, landed = 0, committed = -1;   // thread 0's bookkeeping for the error path
     auto load_chunk = [&](int c) {
-        const int s = c & 1;
+        const int s = c % TC_STAGES;
         const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&full[s]);
+        issued = c + 1;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(SB));
         bulk_g2s(s0 + s * SB, Ablk + (long long)c * TC_ABLK, TC_ABLK * 4, mb);
         bulk_g2s(s0 + s * SB + TC_ABLK * 4, Bblk + (long long)c * TC_BBLK, TC_BBLK * 4, mb);
     };
+    auto done_of = [&](int c) { return (uint32_t)__cvta_generic_to_shared(&done[c % TC_STAGES]); };
     float sh[TC_N], sc[TC_N];
 #pragma unroll
     for (int j = 0; j < TC_N; j++) { sh[j] = 0.0f; sc[j] = 0.0f; }
     bool ok = true;
-    if (tid == 0) load_chunk(0);
+    if (tid == 0)
+        for (int c = 0; c < TC_STAGES - 1 && c < nkc; c++) load_chunk(c);
     for (int c = 0; c < nkc; c++) {
-        const int s = c & 1;
+        const int s = c % TC_STAGES;
         if (tid == 0) {
             // operands of chunk c have landed
-            if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&full[s]), (c >> 1) & 1)) ok = false;
+            if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&full[s]), (c / TC_STAGES) & 1))
+                ok = false;
+            else
+                landed = c + 1;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            if (ok) issue_chunk_mma(tmem + s * TC_N, s0 + s * SB, s0 + s * SB + TC_ABLK * 4, idesc);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                (uint32_t)__cvta_generic_to_shared(&done[s])));
-            // the other stage is free once chunk c-1's MMAs completed
-            if (c + 1 < nkc) {
-                if (c >= 1 && !mbar_wait((uint32_t)__cvta_generic_to_shared(&done[s ^ 1]), ((c - 1) >> 1) & 1)) ok = false;
-                if (ok) load_chunk(c + 1);
+            if (ok) issue_chunk_mma(tmem + (c & 1) * TC_N, s0 + s * SB, s0 + s * SB + TC_ABLK * 4, idesc);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done_of(c)));
+            committed = c;
+            // chunk c + STAGES - 1 goes into the stage chunk c - 1 used, free once its MMAs completed
+            const int nxt = c + TC_STAGES - 1;
+            if (nxt < nkc) {
+                if (c >= 1 && !mbar_wait(done_of(c - 1), ((c - 1) / TC_STAGES) & 1)) ok = false;
+                if (ok) load_chunk(nxt);
             }
         }
-        // read out chunk c-1 while chunk c runs
+        // read out chunk c-1 (accumulator (c-1) & 1) while chunk c runs
         if (c >= 1) {
-            const int sp = (c - 1) & 1;
-            if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&done[sp]), ((c - 1) >> 1) & 1)) ok = false;
+            const int ap = (c - 1) & 1;
+            if (!mbar_wait(done_of(c - 1), ((c - 1) / TC_STAGES) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
             for (int c0 = 0; c0 < TC_N; c0 += 8) {
                 uint32_t r[8];
-                const uint32_t ta = tmem + sp * TC_N + ((uint32_t)(warp * 32) << 16) + c0;
+                const uint32_t ta = tmem + ap * TC_N + ((uint32_t)(warp * 32) << 16) + c0;
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                                "=r"(r[7])
@@ -412,8 +424,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc,
         }
     }
     if (ok && nkc >= 1) {
-        const int sp = (nkc - 1) & 1;
-        if (!mbar_wait((uint32_t)__cvta_generic_to_shared(&done[sp]), ((nkc - 1) >> 1) & 1)) ok = false;
+        const int sp = (nkc - 1) & 1;   // accumulator of the last chunk
+        if (!mbar_wait(done_of(nkc - 1), ((nkc - 1) / TC_STAGES) & 1)) ok = false;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (__all_sync(0xffffffffu, ok)) {
 #pragma unroll
@@ -433,6 +445,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_zgemm_tc2(int M, int N, int nkc,
         }
     }
     if (!ok && (tid & 31) == 0) atomicExch(&g_tc_status, 1);
+    if (!ok && tid == 0) {
+        // a bounded wait gave up: let this CTA's own bulk copies and its last
+        // committed MMAs finish (bounded again) before the shared and tensor
+        // memory are released
+        for (int c = landed; c < issued; c++) mbar_wait((uint32_t)__cvta_generic_to_shared(&full[c % TC_STAGES]), (c / TC_STAGES) & 1);
+        if (committed >= 0) mbar_wait(done_of(committed), (committed / TC_STAGES) & 1);
+    }
     const int r = warp * 32 + (tid & 31);
     const int m = m0 + (r & (TC_M - 1));
     if (ok && m < M) {
@@ -453,7 +472,7 @@ int launch_zgemm_tc2(int M, int N, int K, int batch, const float *Ap, const floa
 {
     if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return RSGDF_OK;
     const int nkc = (K + TC_KC - 1) / TC_KC, nnt = (N + TC_N - 1) / TC_N, nmt = (M + TC_M - 1) / TC_M;
-    const size_t smem = 2 * (size_t)(TC_ABLK + TC_BBLK) * 4;
+    const size_t smem = TC_STAGES * (size_t)(TC_ABLK + TC_BBLK) * 4;
     if (cudaFuncSetAttribute(k_zgemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSGDF_EDEVICE;
     dim3 grid(nnt, nmt, batch);
