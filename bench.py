@@ -44,6 +44,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "j3c build s and shell-triple integrals/s per k-mesh; learned+mixed vs plain FP64 at 1e-8"
 UNIT = "shell-triple lattice terms/s"
+SR_TRAFFIC_K222 = 101.6e6   # DRAM bytes of the SR launches of one learned+mixed FCC 2x2x2 step
 DTYPES = {"fp64": "f64", "mixed": "f64 SR / tf32x3 LR / f32 phases",
           "learned-mixed": "f64 SR / tf32x3 LR / f32 phases, f16 screen network"}
 
@@ -316,8 +317,12 @@ def main():
     names = {"sr_ms": "k_sr3c (SR lattice-sum kernels)", "aft_ms": "k_aft (pair Fourier transforms)",
              "lr_gemm_ms": "LR contraction GEMM", "phase_ms": "k_phase1/k_phase2", "other_ms": "other"}
     ach = ph[dom]["tflops"]
+    # DRAM bytes of the SR launches of one headline step (j2c and j3c), from one ncu
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels
+    traffic = SR_TRAFFIC_K222 if (dom == "sr_ms" and args.path == "learned-mixed" and list(p.kmesh) == [2, 2, 2]) else None
     roof = {"kernel": names[dom], "bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": (ach / peak_fp64) if ach else None, "traffic": None,
+            "frac": (ach / peak_fp64) if ach else None, "traffic": traffic,
+            "traffic_unit": "bytes per step of the phase (all its launches)",
             "peak_source": "measured live: rsgdf_probe_fp64 (FP64 FMA chains on every SM)",
             "achieved_note": "algorithmic FP64 flops of the phase / its device time (CUDA events on the call's stream)"}
     ref_ms = sum(ref_times) / len(ref_times)
