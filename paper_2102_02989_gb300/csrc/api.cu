@@ -1469,8 +1469,10 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
     int *dg;
     double *W, *F;
     RC(S.upload(dg, gl));
-    RC(S.alloc(W, (size_t)2 * NG * naux));
-    RC(S.alloc(F, (size_t)2 * NG * naux));
+    // weights and transforms of every requested k, contracted by one batched GEMM
+    const long long wsz = (long long)2 * NG * naux;
+    RC(S.alloc(W, (size_t)wsz * nk));
+    RC(S.alloc(F, (size_t)wsz * nk));
     const double g0fac = 3.141592653589793238462643383279502884 / (L.vol * omega * omega);
     // J^k = sum_lt e^{-i k.lt} X2[lt] - [k = 0] fac S_P S_Q + W^T F
     for (int i = 0; i < nk; i++) {
@@ -1494,13 +1496,14 @@ int rsgdf_j2c(const rsgdf_cell *cell, const rsgdf_basis *aux_in, const rsgdf_opt
         G.vol = L.vol;
         G.omega = omega;
         t_timer.begin(PH_AFT);
-        RC(launch_aux_ft(G, dax, 0, ax.nshell, 0, naux, W, F, st));
+        RC(launch_aux_ft(G, dax, 0, ax.nshell, 0, naux, W + i * wsz, F + i * wsz, st));
         t_timer.end();
-        t_timer.begin(PH_GEMM);
-        RC(launch_zgemm_tn(naux, naux, NG, 1, W, F, 0, Jk, 0, st));
-        t_timer.end();
-        nlaunch += 2;
+        nlaunch++;
     }
+    t_timer.begin(PH_GEMM);
+    RC(launch_zgemm_tn(naux, naux, NG, nk, W, F, wsz, J_out, 2 * m, st, wsz));
+    t_timer.end();
+    nlaunch++;
     if (L_out) {
         t_timer.begin(PH_OTHER);
         RC(launch_cholesky(naux, nk, J_out, L_out, info_out, st));

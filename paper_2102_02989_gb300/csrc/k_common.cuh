@@ -137,7 +137,8 @@ int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntr
 int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,
                      int Nk, double *Sf, cudaStream_t st);
 int launch_zgemm_tn(int M, int N, int K, int batch, const double *A, const double *B, long long strideB,
-                    double *C, long long strideC, cudaStream_t st);
+                    double *C, long long strideC, cudaStream_t st,
+                    long long strideA = 0);
 int launch_phase1(const double *X, long long m, int Nk, int ndt, int k12, const double *ph, double *T, int accumulate,
                   cudaStream_t st);
 int launch_g0_outer(double *J, int n, const double *S, double fac, cudaStream_t st);

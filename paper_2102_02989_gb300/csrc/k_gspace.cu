@@ -459,12 +459,13 @@ int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, co
 // C[b][m][n] += sum_k A[k][m] B[b][k][n], complex FP64 (interleaved).
 constexpr int GB_M = 32, GB_N = 32, GB_K = 16;
 
-__global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const double2 *A, const double2 *B,
-                                                  long long strideB, double2 *C, long long strideC)
+__global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const double2 *A, long long strideA,
+                                                  const double2 *B, long long strideB, double2 *C, long long strideC)
 {
     __shared__ double2 As[GB_K][GB_M];
     __shared__ double2 Bs[GB_K][GB_N];
     const int b = blockIdx.z;
+    A += b * strideA;
     const double2 *Bb = B + b * strideB;
     double2 *Cb = C + b * strideC;
     const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
@@ -512,12 +513,12 @@ __global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const dou
 }
 
 int launch_zgemm_tn(int M, int N, int K, int batch, const double *A, const double *B, long long strideB, double *C,
-                    long long strideC, cudaStream_t st)
+                    long long strideC, cudaStream_t st, long long strideA)
 {
     if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return RSGDF_OK;
     dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, batch);
-    k_zgemm_tn<<<grid, 256, 0, st>>>(M, N, K, (const double2 *)A, (const double2 *)B, strideB / 2, (double2 *)C,
-                                     strideC / 2);
+    k_zgemm_tn<<<grid, 256, 0, st>>>(M, N, K, (const double2 *)A, strideA / 2, (const double2 *)B, strideB / 2,
+                                     (double2 *)C, strideC / 2);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
