@@ -19,7 +19,9 @@ below cut = log10(eps) - 1 and, as a guard against extrapolation, the
 estimate itself plus its own calibrated margin for the item's class
 L = lP + lmu + lnu (the guard, the largest cut - estimate over all training
 items of that class with magnitude >= eps 10^-drop, plus ``safety``) is
-below the cut too; a class absent from the training data is never skipped.  The margin is calibrated on held-out items that
+below the cut too; a class with training items but none at that level takes
+the largest calibrated guard, and a class absent from the training data is
+never skipped.  The margin is calibrated on held-out items that
 must be kept (magnitude >= eps 10^-drop; many skipped items can land in one
 output element, so the per-item budget sits well below eps): the largest
 shortfall cut - prediction among them plus ``safety`` decades (zero if
@@ -81,11 +83,17 @@ def train_screen(X, t, epochs=40, batch=2048, lr=2e-3, tau=0.99, seed=0, holdout
     keep_all = traw >= k
     Lc = np.rint(Xh[:, 0] + Xh[:, 1] + Xh[:, 2]).astype(int)
     guard = np.full(10, np.inf, np.float32)
+    calibrated = []
     for L in range(10):
-        inL = Lc == L
-        if inL.any():
-            kk = keep_all & inL
-            guard[L] = (float((cut - Xh[kk, BASE]).max()) if kk.any() else cut - float(Xh[inL, BASE].max())) + safety
+        kk = keep_all & (Lc == L)
+        if kk.any():
+            guard[L] = float((cut - Xh[kk, BASE]).max()) + safety
+            calibrated.append(guard[L])
+    # a class seen in training without any item at the keep level takes the most
+    # conservative calibrated guard; a class never seen is never skipped (inf)
+    for L in range(10):
+        if not np.isfinite(guard[L]) and (Lc == L).any() and calibrated:
+            guard[L] = max(calibrated)
     m.set_base(BASE, lo, hi, guard)
     loss = m.train(Xt, tt, epochs=epochs, batch=batch, lr=lr, tau=tau, seed=seed)
     pv = m.forward(Xv).cpu().numpy() + base[hv]
