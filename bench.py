@@ -353,6 +353,7 @@ def main():
         line["batch"] = batch_bench(rsgdf, inputs, np, torch)
         if paths["learned-mixed"].get("mlp") is not None:
             line["rocksalt_chunk"] = rocksalt_bench(rsgdf, inputs, paths, np, torch)
+            line["auto_omega"] = auto_omega_bench(rsgdf, p, paths, make, timed, np)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -391,6 +392,29 @@ def per_kmesh(rsgdf, inputs, paths, make, timed, np):
         del Vs
         out["%dx%dx%d" % km] = res
     return out
+
+
+def auto_omega_bench(rsgdf, p, paths, make, timed, np):
+    """The same cell and mesh with the G box (hence omega) chosen per path by
+    timing the candidates 5^3..13^3 (tuning.tune_gmesh), then the whole step
+    (j2c + j3c) on the chosen box, learned+mixed and plain FP64."""
+    from paper_2102_02989_gb300 import tuning
+    kp = np.array([(i, j) for i in range(p.nk) for j in range(p.nk)], dtype=np.int32)
+    res = {}
+    Vs = {}
+    for name in ("learned-mixed", "fp64"):
+        opt = {k: v for k, v in paths[name].items() if k not in ("omega", "gmesh")}
+        gm, w, times = tuning.tune_gmesh(p.a, p.kmesh, p.ao, p.aux, kp, candidates=(5, 7, 9, 11, 13), reps=1, **opt)
+        step, V, _ = make(p, dict(opt, omega=w, gmesh=gm))
+        t, st, _ = timed(step, 3, 1, "auto_step")
+        res[name] = {"gmesh": list(gm), "omega": w, "ms_per_step": statistics.median(t),
+                     "j3c_ms_by_box": {str(n): round(ms, 2) for n, (_, ms) in times.items()}}
+        Vs[name] = V
+    res["speedup"] = res["fp64"]["ms_per_step"] / res["learned-mixed"]["ms_per_step"]
+    res["max_abs_vs_fp64"] = (Vs["learned-mixed"] - Vs["fp64"]).abs().max().item()
+    res["note"] = ("the range-separated sum is omega-independent; each path runs on the box that is fastest for it, "
+                   "same cell, mesh and eps as the headline")
+    return res
 
 
 def rocksalt_bench(rsgdf, inputs, paths, np, torch):
