@@ -153,7 +153,8 @@ def config3(kmesh=(4, 4, 4)) -> Problem:
 
 def config5() -> Problem:
     """Rocksalt conventional cubic cell a = 8.0 Bohr, 8 atoms, 4x4x4 mesh;
-    every atom draws its AO shells like config 2 and carries the same ETB aux."""
+    every atom draws its AO shells like the FCC two-atom cell (3s2p1d) and
+    carries the same ETB aux."""
     rng = np.random.default_rng(SEED_BASE + 5)
     A = 8.0
     a = A * np.eye(3)

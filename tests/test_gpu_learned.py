@@ -84,7 +84,8 @@ def test_items_features_and_magnitudes(rs):
 
 
 def test_learned_screen_gain_at_equal_accuracy(rs, orc):
-    """Train on config 1 items, apply to a config 2 slice: the network skips
+    """Train on the items of the cubic Gamma cell and of the first atom's aux
+    shells of the FCC 2x2x2 cell, apply to the second atom's: the network skips
     items the estimates keep, and the result stays within the same 10 eps of
     the converged oracle as the estimates alone."""
     import torch
@@ -138,8 +139,8 @@ def test_expectile_training_envelope(rs):
 
 
 def test_learned_screen_rocksalt_chunk(rs, orc):
-    """The network trained on the magnitudes of configs 1-3 (the cubic Gamma
-    cell, the FCC cell on 2x2x2 and 3x3x3 meshes), applied to the 8-atom
+    """The network trained on the magnitudes of the cubic Gamma cell and the
+    FCC cell on 2x2x2 and 3x3x3 meshes, applied to the 8-atom
     rocksalt cell on a 4x4x4 mesh: the first atom's 16 aux shells and four
     diagonal k pairs.  It skips work items the estimates keep (each below
     eps/10 here, many of them land in one output element), changes the
