@@ -238,3 +238,43 @@ def tiny(kmesh=(1, 1, 1), lmax_ao=1, lmax_aux=2, seed=7, a=3.2, natm=1) -> Probl
 
 def kpairs_all(nk: int) -> np.ndarray:
     return np.array([(i, j) for i in range(nk) for j in range(nk)], dtype=np.int32)
+
+
+def _mesh_neg(k: int, kmesh) -> int:
+    n1, n2 = kmesh[1], kmesh[2]
+    a = (k // (n1 * n2), (k // n2) % n1, k % n2)
+    return ((-a[0]) % kmesh[0] * n1 + (-a[1]) % n1) * n2 + (-a[2]) % n2
+
+
+def df_synthetic(kmesh=(2, 1, 1), naux=24, nao=6, nocc=2, seed=0, cond=1e-7, rank=None):
+    """Seeded inputs of the density-fitting consumers: per k a Hermitian metric
+    J^k = Q diag(lam) Q^H (Q random unitary, real at k = -k; J^{-k} = conj(J^k))
+    with lam log-spaced from 1 down to cond, or, with rank < naux, the last
+    naux - rank eigenvalues exactly zero (a linearly dependent aux set); a
+    random complex j3c tensor V over every k pair ([nk*nk][naux][nao][nao],
+    pairs in kpairs_all order); closed-shell densities D^k = 2 C C^H with C
+    random orthonormal (nao x nocc), D^{-k} = conj(D^k)."""
+    rng = np.random.default_rng(SEED_BASE + 300 + seed)
+    nk = int(np.prod(kmesh))
+    J = np.zeros((nk, naux, naux), dtype=np.complex128)
+    D = np.zeros((nk, nao, nao), dtype=np.complex128)
+    lam = np.logspace(0.0, np.log10(cond), naux)
+    if rank is not None:
+        lam[rank:] = 0.0
+    done = [False] * nk
+    for k in range(nk):
+        if done[k]:
+            continue
+        kn = _mesh_neg(k, kmesh)
+        X = rng.normal(size=(naux, naux)) + (1j * rng.normal(size=(naux, naux)) if kn != k else 0.0)
+        Q, _ = np.linalg.qr(X)
+        M = (Q * lam) @ Q.conj().T
+        J[k] = 0.5 * (M + M.conj().T)
+        C0 = rng.normal(size=(nao, nocc)) + (1j * rng.normal(size=(nao, nocc)) if kn != k else 0.0)
+        C, _ = np.linalg.qr(C0)
+        M = 2.0 * C @ C.conj().T
+        D[k] = 0.5 * (M + M.conj().T)
+        J[kn], D[kn] = np.conj(J[k]), np.conj(D[k])
+        done[k] = done[kn] = True
+    V = rng.normal(size=(nk * nk, naux, nao, nao)) + 1j * rng.normal(size=(nk * nk, naux, nao, nao))
+    return J, V, D
