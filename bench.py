@@ -354,6 +354,7 @@ def main():
         if paths["learned-mixed"].get("mlp") is not None:
             line["rocksalt_chunk"] = rocksalt_bench(rsgdf, inputs, paths, np, torch)
             line["auto_omega"] = auto_omega_bench(rsgdf, p, paths, make, timed, np)
+        line["df_consumers"] = df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -391,6 +392,67 @@ def per_kmesh(rsgdf, inputs, paths, make, timed, np):
         res["value_fp64"] = res["fp64"]["sr_terms"] / (res["fp64"]["ms_per_step"] * 1e-3)
         del Vs
         out["%dx%dx%d" % km] = res
+    return out
+
+
+def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64):
+    """Density-fitting consumers after the step: the fitting transforms of the
+    j2c metrics (automatic Cholesky / eigen choice), the fit B = T V over every
+    k pair and the fitted Coulomb and exchange matrices of a synthetic
+    closed-shell density, each timed alone (CUDA events, median of 3 after one
+    warm-up), on the headline cell at 2x2x2 and 4x4x4.  The energies from the
+    GPU J/K (eigen route, as the host proxy) are checked against the host's
+    FP64 HF-energy proxy of the same tensors."""
+    def ev(f, reps=3):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = {}
+    for km in ((2, 2, 2), (4, 4, 4)):
+        prob = inputs.config2(km)
+        w, gm = rsgdf.rsgdf_params(prob.a, prob.kmesh, gmesh=prob.gmesh, eps_lr=prob.eps_lr)
+        step, V, kp = make(prob, dict(paths["fp64"], omega=w, gmesh=gm))
+        (J, _, _), _, _ = step()
+        nao, naux = V.shape[-1], V.shape[1]
+        D = torch.from_numpy(hfproxy.densities(prob.kmesh, nao, max(1, nao // 4))).to(V.device)
+        res, keep = {}, {}
+
+        def metric(method):
+            keep["m"] = rsgdf.rsgdf_df_metric(J, method, 1e-6)
+        res["metric_ms"] = ev(lambda: metric(rsgdf.RSGDF_FIT_AUTO))
+        info = keep["m"][3].cpu().numpy()
+        res["routes"] = {"cholesky": int(np.sum(info == 0)), "eigen": int(np.sum(info >= 1)),
+                         "max_sweeps": int(info.max())}
+        metric(rsgdf.RSGDF_FIT_EIGEN)
+        T = keep["m"][0]
+        B = torch.empty_like(V)
+        res["fit_ms"] = ev(lambda: rsgdf.rsgdf_df_fit(prob.a, prob.kmesh, T, V, kp, out=B))
+        res["jk_ms"] = ev(lambda: keep.update(jk=rsgdf.rsgdf_df_jk(prob.a, prob.kmesh, B, kp, D)))
+        fit_fl = 8.0 * naux * naux * nao * nao * len(kp)
+        jk_fl = 2 * 8.0 * naux * nao ** 3 * len(kp)
+        res["fit_tflops"] = fit_fl / (res["fit_ms"] * 1e-3) / 1e12
+        res["jk_tflops"] = jk_fl / (res["jk_ms"] * 1e-3) / 1e12
+        res["fp64_peak_tflops"] = peak_fp64
+        Jm, Km = (x.cpu().numpy() for x in keep["jk"])
+        Dh = D.cpu().numpy()
+        ej = float(np.real(sum(np.trace(Dh[k] @ Jm[k]) for k in range(prob.nk)))) / (2 * prob.nk)
+        ek = -float(np.real(sum(np.trace(Dh[k] @ Km[k]) for k in range(prob.nk)))) / (4 * prob.nk)
+        hj, hk = hfproxy.energies(V.cpu().numpy(), kp, prob.kmesh, hfproxy.fit_transforms(J.cpu().numpy(), 1e-6), Dh)
+        res.update({"E_J": ej, "E_K": ek, "dE_J_vs_host": abs(ej - hj), "dE_K_vs_host": abs(ek - hk)})
+        out["%dx%dx%d" % km] = res
+        del V, B, J, keep
+        torch.cuda.empty_cache()
+    out["note"] = ("FP64 throughout; fit and J/K are complex GEMMs on the FP64 pipe (flops 8 naux^2 nao^2 and "
+                   "16 naux nao^3 per k pair); metric = Cholesky + triangular inverse, Jacobi where it fails")
     return out
 
 

@@ -316,6 +316,76 @@ const char *rsgdf_last_error(void);
  * in-bounds microbenchmark, used as the roofline denominator). */
 int rsgdf_probe_fp64(double *tflops_out, void *stream);
 
+/*
+ * Density-fitting consumers of j2c and j3c (Eq. DF_eqn and the fitted ERIs of
+ * Eq. ERI_aux).  All FP64; all arrays DEVICE memory, complex interleaved;
+ * work enqueued on `stream` (cudaStream_t or NULL).
+ *
+ * rsgdf_df_metric: a fitting transform T_k of each metric J^k with
+ * T_k^H T_k = (J^k)^{-1} on the part of J^k it keeps, so B = T V solves the
+ * fitting equation J d = V through d = T^H B.
+ *   RSGDF_FIT_CHOLESKY: J = L L^H (lower triangle of J read), T = L^{-1}
+ *     (lower).  Pivot j fails when L_jj^2 <= rel * max_i J_ii (rel = 0: the
+ *     plain positivity test); T_k is then zero.
+ *   RSGDF_FIT_EIGEN: canonical orthogonalisation of the Hermitian part
+ *     U diag(lam) U^H (lam descending, cyclic Jacobi): row r of T_k is
+ *     lam_r^{-1/2} (column r of U)^H for lam_r > rel * lam_0 and zero for the
+ *     rows past the kept count.  Unique up to a phase per row (and a unitary
+ *     mixing of rows of equal lam): T^H T is unique.
+ *   RSGDF_FIT_AUTO: Cholesky, and the eigen route on the k whose pivots fail
+ *     (a singular or nearly singular metric, e.g. a linearly dependent aux
+ *     set); the choice is made on the device, per k.
+ *   J        : [nk][naux][naux]
+ *   naux     : 1 .. RSGDF_DF_NMAX
+ *   rel      : 0 <= rel < 1
+ *   T_out    : [nk][naux][naux], overwritten; must not overlap J
+ *   lam_out  : double [nk][naux] or NULL: eigenvalues (descending) of the k
+ *              that took the eigen route, zeros for the others
+ *   nkept_out: int [nk] or NULL: rows of T_k that are not zero
+ *   info_out : int [nk] or NULL: 0 = Cholesky route; s >= 1 = eigen route,
+ *              converged after s sweeps; RSGDF_DF_SWEEPS + 1 = eigen route
+ *              still rotating after RSGDF_DF_SWEEPS sweeps (T from the last
+ *              sweep); -1 - j = Cholesky route failed at pivot j (method
+ *              RSGDF_FIT_CHOLESKY only).
+ * Scratch: 3 nk naux^2 complex (stream-ordered, released before return).
+ */
+#define RSGDF_FIT_CHOLESKY 0
+#define RSGDF_FIT_EIGEN 1
+#define RSGDF_FIT_AUTO 2
+#define RSGDF_DF_NMAX 1024
+#define RSGDF_DF_SWEEPS 40
+int rsgdf_df_metric(const double *J, int naux, int nk, int method, double rel, double *T_out, double *lam_out,
+                    int *nkept_out, int *info_out, void *stream);
+
+/*
+ * rsgdf_df_fit: B^{k1k2} = T_{k12} V^{k1k2}, k12 = k2 - k1 on the mesh.
+ *   cell   : its kmesh gives the k indices (host)
+ *   T      : [Nk][naux][naux] from rsgdf_df_metric (all Nk mesh points)
+ *   V      : [npair][naux][nao][nao] (the layout rsgdf_j3c writes)
+ *   kpairs : host int [npair][2]
+ *   B_out  : [npair][naux][nao][nao], overwritten; must not overlap V
+ */
+int rsgdf_df_fit(const rsgdf_cell *cell, const double *T, int naux, int nao, int npair, const int *kpairs,
+                 const double *V, double *B_out, void *stream);
+
+/*
+ * rsgdf_df_jk: fitted Coulomb and exchange matrices of a closed-shell
+ * density D^k (D = 2 C C^H; Hermitian per k):
+ *   rho_P  = sum_{(k,k) in kpairs} sum_{mu nu} B^{kk}_{P mu nu} D^k_{nu mu}
+ *   J^k    = (1/Nk) sum_P B^{kk}_P conj(rho_P)        (zero for k without a pair (k,k))
+ *   K^{k1} = (1/Nk) sum_{(k1,k2) in kpairs} sum_P B^{k1k2}_P D^{k2} (B^{k1k2}_P)^H
+ * so that E_J = (1/2Nk) sum_k Tr[D^k J^k] and E_K = -(1/4Nk) sum_k Tr[D^k K^k]
+ * per cell; with every pair present these are the Hartree and exchange
+ * energies of the fitted ERIs.
+ *   B      : [npair][naux][nao][nao] from rsgdf_df_fit
+ *   kpairs : host int [npair][2], no pair listed twice
+ *   D      : [Nk][nao][nao]
+ *   J_out, K_out : [Nk][nao][nao] or NULL (not both), overwritten
+ * Scratch: naux complex, plus a bounded chunk of B-sized intermediates.
+ */
+int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
+                const double *D, double *J_out, double *K_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

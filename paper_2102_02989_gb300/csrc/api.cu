@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -1865,6 +1866,239 @@ int rsgdf_probe_fp64(double *tflops_out, void *stream)
     cudaEventDestroy(e1);
     double flops = 2.0 * 8 * iters * (double)nsm * 8 * 256;
     *tflops_out = flops / (best * 1e-3) / 1e12;
+    return RSGDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Density-fitting consumers (Eq. DF_eqn, Eq. ERI_aux)
+// ---------------------------------------------------------------------------
+static bool ranges_overlap(const void *a, const void *b, size_t bytes)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+int rsgdf_df_metric(const double *J, int naux, int nk, int method, double rel, double *T_out, double *lam_out,
+                    int *nkept_out, int *info_out, void *stream)
+{
+    static_assert(RSGDF_DF_NMAX == DF_NMAX && RSGDF_DF_SWEEPS == DF_JACOBI_SWEEPS, "DF limits out of step");
+    t_err.clear();
+    if (!J || !T_out) return fail(RSGDF_EINVAL, "J and T_out are required");
+    if (naux < 1 || naux > RSGDF_DF_NMAX) return fail(RSGDF_EINVAL, "naux outside 1..RSGDF_DF_NMAX");
+    if (nk < 1) return fail(RSGDF_EINVAL, "need at least one k");
+    if (method < RSGDF_FIT_CHOLESKY || method > RSGDF_FIT_AUTO) return fail(RSGDF_EINVAL, "unknown fitting method");
+    if (!(rel >= 0.0 && rel < 1.0)) return fail(RSGDF_EINVAL, "rel outside [0, 1)");
+    const size_t nn = (size_t)naux * naux;
+    if (ranges_overlap(J, T_out, 16 * nn * nk)) return fail(RSGDF_EINVAL, "T_out overlaps J");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    int *info = info_out;
+    if (!info) RC(S.alloc(info, nk));
+    double *lam = lam_out;
+    if (!lam) RC(S.alloc(lam, (size_t)naux * nk));
+    CU(cudaMemsetAsync(lam, 0, sizeof(double) * naux * nk, st));
+    if (method != RSGDF_FIT_EIGEN) {
+        double *Lf;
+        int *cinfo;
+        RC(S.alloc(Lf, 2 * nn * nk));
+        RC(S.alloc(cinfo, nk));
+        RC(launch_cholesky(naux, nk, J, Lf, cinfo, st));
+        RC(launch_df_cholesky_route(naux, nk, J, Lf, cinfo, rel, T_out, info, nkept_out, st));
+    }
+    if (method != RSGDF_FIT_CHOLESKY) {
+        double *A, *U;
+        int *order;
+        RC(S.alloc(A, 2 * nn * nk));
+        RC(S.alloc(U, 2 * nn * nk));
+        RC(S.alloc(order, (size_t)naux * nk));
+        RC(launch_df_eigen_route(naux, nk, J, method == RSGDF_FIT_AUTO ? info : nullptr, rel, A, U, lam, order, T_out,
+                                 info, nkept_out, st));
+    }
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+static int df_pairs(const rsgdf_cell *cell, int npair, const int *kpairs, Lattice &L, bool unique)
+{
+    RC(make_lattice(cell, L, t_err));
+    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
+    for (int i = 0; i < 2 * npair; i++)
+        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    if (unique) {
+        std::set<std::pair<int, int>> seen;
+        for (int p = 0; p < npair; p++)
+            if (!seen.insert({kpairs[2 * p], kpairs[2 * p + 1]}).second)
+                return fail(RSGDF_EINVAL, "a k pair is listed twice");
+    }
+    return RSGDF_OK;
+}
+
+static int upload_offsets(Scratch &S, const std::vector<long long> &a, const std::vector<long long> &b,
+                          const std::vector<long long> &c, ZGemmGen &g)
+{
+    long long *da, *db, *dc;
+    RC(S.upload(da, a));
+    RC(S.upload(db, b));
+    RC(S.upload(dc, c));
+    g.aoff = da;
+    g.boff = db;
+    g.coff = dc;
+    return RSGDF_OK;
+}
+
+int rsgdf_df_fit(const rsgdf_cell *cell, const double *T, int naux, int nao, int npair, const int *kpairs,
+                 const double *V, double *B_out, void *stream)
+{
+    t_err.clear();
+    Lattice L;
+    RC(df_pairs(cell, npair, kpairs, L, false));
+    if (!T || !V || !B_out) return fail(RSGDF_EINVAL, "T, V and B_out are required");
+    if (naux < 1 || nao < 1) return fail(RSGDF_EINVAL, "naux and nao must be >= 1");
+    const long long n2 = (long long)nao * nao, blk = (long long)naux * n2;
+    if (ranges_overlap(V, B_out, (size_t)16 * blk * npair)) return fail(RSGDF_EINVAL, "B_out overlaps V");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    std::vector<long long> ao(npair), bo(npair), co(npair);
+    for (int p = 0; p < npair; p++) {
+        ao[p] = (long long)k12_of(L, kpairs[2 * p], kpairs[2 * p + 1]) * naux * naux;
+        bo[p] = co[p] = p * blk;
+    }
+    // B[p](r, x) = sum_P T[k12](r, P) V[p](P, x)
+    ZGemmGen g{};
+    g.M = naux;
+    g.N = (int)n2;
+    g.Q = 1;
+    g.S = naux;
+    g.lda = naux;
+    g.as = 1;
+    g.bs = n2;
+    g.bn = 1;
+    g.ldc = n2;
+    g.alpha = 1.0;
+    RC(upload_offsets(S, ao, bo, co, g));
+    RC(launch_zgemm_gen(g, npair, T, V, B_out, st));
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
+                const double *D, double *J_out, double *K_out, void *stream)
+{
+    t_err.clear();
+    Lattice L;
+    RC(df_pairs(cell, npair, kpairs, L, true));
+    if (!B || !D) return fail(RSGDF_EINVAL, "B and D are required");
+    if (!J_out && !K_out) return fail(RSGDF_EINVAL, "J_out and K_out are both NULL");
+    if (naux < 1 || nao < 1) return fail(RSGDF_EINVAL, "naux and nao must be >= 1");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    const int Nk = L.Nk;
+    const long long n2 = (long long)nao * nao, blk = (long long)naux * n2;
+    if (J_out) {
+        CU(cudaMemsetAsync(J_out, 0, sizeof(double) * 2 * Nk * n2, st));
+        std::vector<long long> pa, pb, pc, ja, jb, jc;
+        for (int p = 0; p < npair; p++)
+            if (kpairs[2 * p] == kpairs[2 * p + 1]) {
+                const int k = kpairs[2 * p];
+                pa.push_back(p * blk);
+                pb.push_back(k * n2);
+                pc.push_back(0);
+                ja.push_back(p * blk);
+                jb.push_back(0);
+                jc.push_back(k * n2);
+            }
+        if (!pa.empty()) {
+            double *rho;
+            RC(S.alloc(rho, 2 * (size_t)naux));
+            CU(cudaMemsetAsync(rho, 0, sizeof(double) * 2 * naux, st));
+            // rho(P) += sum_{mu, nu} B[p](P, mu, nu) D[k](nu, mu)
+            ZGemmGen g{};
+            g.M = naux;
+            g.N = 1;
+            g.Q = nao;
+            g.S = nao;
+            g.lda = n2;
+            g.aq = nao;
+            g.as = 1;
+            g.bq = 1;
+            g.bs = nao;
+            g.ldc = 1;
+            g.atomic = 1;
+            g.alpha = 1.0;
+            RC(upload_offsets(S, pa, pb, pc, g));
+            RC(launch_zgemm_gen(g, (int)pa.size(), B, D, rho, st));
+            // J[k](x) = (1/Nk) sum_P B[p](P, x) conj(rho(P))
+            ZGemmGen h{};
+            h.M = (int)n2;
+            h.N = 1;
+            h.Q = 1;
+            h.S = naux;
+            h.lda = 1;
+            h.as = n2;
+            h.bs = 1;
+            h.ldc = 1;
+            h.conjB = 1;
+            h.alpha = 1.0 / Nk;
+            RC(upload_offsets(S, ja, jb, jc, h));
+            RC(launch_zgemm_gen(h, (int)ja.size(), B, rho, J_out, st));
+        }
+    }
+    if (K_out) {
+        CU(cudaMemsetAsync(K_out, 0, sizeof(double) * 2 * Nk * n2, st));
+        const long long budget = 4LL << 30;
+        const int cp = (int)std::max(1LL, std::min<long long>(npair, budget / (16 * blk)));
+        double *Y;
+        RC(S.alloc(Y, (size_t)2 * blk * cp));
+        for (int c0 = 0; c0 < npair; c0 += cp) {
+            const int nc = std::min(cp, npair - c0);
+            std::vector<long long> a1(nc), b1(nc), c1(nc), a2(nc), b2(nc), c2(nc);
+            for (int b = 0; b < nc; b++) {
+                const int p = c0 + b;
+                a1[b] = p * blk;
+                b1[b] = kpairs[2 * p + 1] * n2;
+                c1[b] = b * blk;
+                a2[b] = b * blk;
+                b2[b] = p * blk;
+                c2[b] = kpairs[2 * p] * n2;
+            }
+            // Y[b]((P, mu), s) = sum_l B[p]((P, mu), l) D[k2](l, s)
+            ZGemmGen g{};
+            g.M = naux * nao;
+            g.N = nao;
+            g.Q = 1;
+            g.S = nao;
+            g.lda = nao;
+            g.as = 1;
+            g.bs = nao;
+            g.bn = 1;
+            g.ldc = nao;
+            g.alpha = 1.0;
+            RC(upload_offsets(S, a1, b1, c1, g));
+            RC(launch_zgemm_gen(g, nc, B, D, Y, st));
+            // K[k1](mu, nu) += (1/Nk) sum_{P, s} Y[b](P, mu, s) conj(B[p](P, nu, s))
+            ZGemmGen h{};
+            h.M = nao;
+            h.N = nao;
+            h.Q = naux;
+            h.S = nao;
+            h.lda = nao;
+            h.aq = n2;
+            h.as = 1;
+            h.bq = n2;
+            h.bs = 1;
+            h.bn = nao;
+            h.ldc = nao;
+            h.conjB = 1;
+            h.atomic = 1;
+            h.alpha = 1.0 / Nk;
+            RC(upload_offsets(S, a2, b2, c2, h));
+            RC(launch_zgemm_gen(h, nc, Y, B, K_out, st));
+        }
+    }
+    CU(cudaGetLastError());
     return RSGDF_OK;
 }
 

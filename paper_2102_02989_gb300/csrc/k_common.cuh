@@ -218,4 +218,21 @@ int launch_phase1_multi(const double *X, long long m, int Nk, int nlt, const int
 int launch_phase2_multi(const double *T, long long m, int Nk, const int *goff, int ngroups, const int *plist,
                         const int *pk2, const void *ph, double *V, int accumulate, int fp32, cudaStream_t st);
 
+// Density-fitting consumers (k_df.cu)
+constexpr int DF_NMAX = 1024;          // largest aux metric of the eigen / Cholesky routes
+constexpr int DF_JACOBI_SWEEPS = 40;   // sweep limit of the Jacobi eigensolver
+int launch_df_cholesky_route(int n, int nk, const double *J, const double *L, const int *cinfo, double rel, double *T,
+                             int *info, int *nkept, cudaStream_t st);
+int launch_df_eigen_route(int n, int nk, const double *J, const int *gate, double rel, double *A, double *U,
+                          double *lam, int *order, double *T, int *info, int *nkept, cudaStream_t st);
+// batched complex GEMM with a split contraction index (layout in k_df.cu)
+struct ZGemmGen {
+    int M, N, Q, S;
+    long long lda, aq, as, bq, bs, bn, ldc;
+    const long long *aoff, *boff, *coff;   // device arrays, one element offset per batch
+    int conjA, conjB, atomic;
+    double alpha;
+};
+int launch_zgemm_gen(const ZGemmGen &g, int batch, const double *A, const double *B, double *C, cudaStream_t st);
+
 }  // namespace rsgdf

@@ -22,6 +22,8 @@ RSGDF_OK, RSGDF_EINVAL, RSGDF_ENOMEM, RSGDF_ENOTPD, RSGDF_ETIMEOUT, RSGDF_EDEVIC
 RSGDF_FP64, RSGDF_MIXED = 0, 1
 RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
 RSGDF_BATCH_GRAPH, RSGDF_BATCH_AUTOTUNE = 1, 2
+RSGDF_FIT_CHOLESKY, RSGDF_FIT_EIGEN, RSGDF_FIT_AUTO = 0, 1, 2
+RSGDF_DF_NMAX, RSGDF_DF_SWEEPS = 1024, 40
 
 # names exported by the library (every declaration of include/rsgdf.h)
 EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kphase", "rsgdf_kphase_noalloc",
@@ -29,7 +31,7 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_mlp_nparams", "rsgdf_mlp_create", "rsgdf_mlp_destroy", "rsgdf_mlp_get_params",
            "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
-           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch")
+           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -122,6 +124,9 @@ def load():
         lib.rsgdf_j3c_batch_destroy.argtypes = [vp]
         lib.rsgdf_j3c_batch_tiles.argtypes = [vp, vp, vp, vp]
         lib.rsgdf_j3c_batch.argtypes = [i, vp, vp, vp, vp, vp]
+        lib.rsgdf_df_metric.argtypes = [vp, i, i, i, C.c_double, vp, vp, vp, vp, vp]
+        lib.rsgdf_df_fit.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp]
+        lib.rsgdf_df_jk.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -284,6 +289,61 @@ def rsgdf_kphase_noalloc(a, kmesh, X, kpairs, out, stream=None):
                                     kp.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
                                     _stream_ptr(stream)))
     return out
+
+
+def _cplx_cuda(x, name):
+    import torch
+    assert x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous(), name + ": complex128 contiguous cuda tensor"
+    return C.c_void_p(x.data_ptr())
+
+
+def rsgdf_df_metric(J, method=RSGDF_FIT_AUTO, rel=1e-6, stream=None):
+    """Fitting transforms of the metrics J [nk][naux][naux] (complex128 cuda):
+    returns (T, lam, nkept, info) with T_k^H T_k = (J^k)^{-1} on the kept part
+    (Cholesky T = L^{-1}; eigen route: canonical orthogonalisation)."""
+    import torch
+    lib = load()
+    Jp = _cplx_cuda(J, "J")
+    nk, naux = int(J.shape[0]), int(J.shape[1])
+    T = torch.empty_like(J)
+    lam = torch.empty((nk, naux), dtype=torch.float64, device=J.device)
+    nkept = torch.empty(nk, dtype=torch.int32, device=J.device)
+    info = torch.empty(nk, dtype=torch.int32, device=J.device)
+    _check(lib.rsgdf_df_metric(Jp, naux, nk, int(method), float(rel), C.c_void_p(T.data_ptr()),
+                               C.c_void_p(lam.data_ptr()), C.c_void_p(nkept.data_ptr()),
+                               C.c_void_p(info.data_ptr()), _stream_ptr(stream)))
+    return T, lam, nkept, info
+
+
+def rsgdf_df_fit(a, kmesh, T, V, kpairs, out=None, stream=None):
+    """B[pair] = T[k12] V[pair]; T [Nk][naux][naux], V [npair][naux][nao][nao] (complex128 cuda)."""
+    import torch
+    lib = load()
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    naux, nao = int(V.shape[1]), int(V.shape[2])
+    if out is None:
+        out = torch.empty_like(V)
+    c = _cell(a, kmesh)
+    _check(lib.rsgdf_df_fit(C.byref(c), _cplx_cuda(T, "T"), naux, nao, len(kp), kp.ctypes.data_as(C.c_void_p),
+                            _cplx_cuda(V, "V"), _cplx_cuda(out, "out"), _stream_ptr(stream)))
+    return out
+
+
+def rsgdf_df_jk(a, kmesh, B, kpairs, D, with_j=True, with_k=True, stream=None):
+    """Fitted Coulomb and exchange matrices (J, K) [Nk][nao][nao] of the
+    densities D [Nk][nao][nao] from B [npair][naux][nao][nao] (complex128 cuda);
+    a matrix not asked for is None."""
+    import torch
+    lib = load()
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    naux, nao = int(B.shape[1]), int(B.shape[2])
+    Jm = torch.empty_like(D) if with_j else None
+    Km = torch.empty_like(D) if with_k else None
+    c = _cell(a, kmesh)
+    _check(lib.rsgdf_df_jk(C.byref(c), _cplx_cuda(B, "B"), naux, nao, len(kp), kp.ctypes.data_as(C.c_void_p),
+                           _cplx_cuda(D, "D"), C.c_void_p(Jm.data_ptr() if with_j else 0),
+                           C.c_void_p(Km.data_ptr() if with_k else 0), _stream_ptr(stream)))
+    return Jm, Km
 
 
 def rsgdf_last_stats() -> dict:

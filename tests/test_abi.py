@@ -73,3 +73,61 @@ def test_argument_errors_without_device(rs, bad):
                        C.c_void_p(16))
     assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
     assert rs.rsgdf_last_error() != ""
+
+
+def test_python_constants_match_header(rs):
+    hdr = open(os.path.join(ROOT, "include", "rsgdf.h")).read()
+    defs = dict(re.findall(r"^#define (RSGDF_\w+) \(?(-?\d+)", hdr, re.M))
+    for name in ("RSGDF_FIT_CHOLESKY", "RSGDF_FIT_EIGEN", "RSGDF_FIT_AUTO", "RSGDF_DF_NMAX", "RSGDF_DF_SWEEPS",
+                 "RSGDF_FP64", "RSGDF_MIXED", "RSGDF_EINVAL"):
+        assert int(defs[name]) == getattr(rs, name), name
+
+
+@pytest.mark.parametrize("bad", ["naux0", "naux_big", "method", "rel", "overlap", "nullT"])
+def test_df_metric_argument_errors_without_device(rs, bad):
+    import ctypes as C
+    lib = rs.load()
+    naux, nk, method, rel = 8, 2, rs.RSGDF_FIT_AUTO, 1e-6
+    J, T = C.c_void_p(1 << 20), C.c_void_p(1 << 30)
+    if bad == "naux0":
+        naux = 0
+    if bad == "naux_big":
+        naux = rs.RSGDF_DF_NMAX + 1
+    if bad == "method":
+        method = 3
+    if bad == "rel":
+        rel = 1.0
+    if bad == "overlap":
+        T = C.c_void_p((1 << 20) + 16)
+    if bad == "nullT":
+        T = C.c_void_p(0)
+    rc = lib.rsgdf_df_metric(J, naux, nk, method, rel, T, None, None, None, None)
+    assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+
+
+@pytest.mark.parametrize("bad", ["kidx", "npair", "overlap", "dup", "noout"])
+def test_df_fit_jk_argument_errors_without_device(rs, bad):
+    import ctypes as C
+    lib = rs.load()
+    c = rs._cell(4.0 * np.eye(3), (2, 1, 1))
+    kp = [(0, 0), (0, 1), (1, 1)]
+    if bad == "kidx":
+        kp = [(0, 2)]
+    if bad == "dup":
+        kp = [(0, 1), (0, 1)]
+    kpa = np.ascontiguousarray(np.asarray(kp, np.int32).reshape(-1, 2))
+    npair = 0 if bad == "npair" else len(kpa)
+    ptr = lambda x: C.c_void_p(x)
+    naux, nao = 8, 3
+    V, Bo = 1 << 20, 1 << 30
+    if bad == "overlap":
+        Bo = V + 16
+    if bad in ("kidx", "npair", "overlap"):
+        rc = lib.rsgdf_df_fit(C.byref(c), ptr(1 << 34), naux, nao, npair, kpa.ctypes.data_as(C.c_void_p), ptr(V),
+                              ptr(Bo), None)
+        assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+    if bad in ("kidx", "npair", "dup", "noout"):
+        out = ptr(0) if bad == "noout" else ptr(1 << 36)
+        rc = lib.rsgdf_df_jk(C.byref(c), ptr(V), naux, nao, npair, kpa.ctypes.data_as(C.c_void_p), ptr(1 << 35),
+                             out, ptr(0), None)
+        assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())

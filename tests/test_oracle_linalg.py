@@ -33,5 +33,9 @@ def test_duplicated_aux_shell_makes_j2c_singular(orc):
                              (int(p.aux.l[0]), p.aux.center[0], [p.aux.exps[0]], [1.0])])
     J = orc.j2c(p.a, (1, 1, 1), aux, 0.9, [0], eps_sr=1e-12, eps_lr=1e-14,
                 gmesh=gmesh_for(p.a, 0.9, 1e-14, (1, 1, 1)))
+    # the two rows agree up to the summation order of the threaded oracle: the
+    # second pivot is zero or a rounding-level positive, never a real one
     L, piv = orc.cholesky(J[0])
-    assert piv == 1
+    assert piv == 1 or (piv == -1 and abs(L[1, 1]) ** 2 <= 1e-12 * J[0][0, 0].real)
+    from oracle import dfjk
+    assert dfjk.cholesky_rel(J[0], rel=1e-12)[1] == 1
