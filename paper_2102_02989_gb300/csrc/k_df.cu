@@ -7,7 +7,7 @@
 // Metric transforms.  Cholesky route: J = L L^H (k_cholesky), T = L^{-1} by
 // forward substitution, one thread per column.  Eigen route (canonical
 // orthogonalisation, the fallback for a singular or nearly singular metric):
-// cyclic Jacobi on the Hermitian part of J, one CTA per k.  A sweep visits
+// cyclic Jacobi on the Hermitian part of J, one CTA cluster per k.  A sweep visits
 // every index pair once in m - 1 steps of the round-robin (circle) ordering
 // (m = n rounded up to even), so the m/2 pairs of a step are disjoint and
 // their rotations commute: all column updates (A J, U J) of a step run in
@@ -30,7 +30,8 @@
 namespace rsgdf {
 
 constexpr int DF_THREADS = 256;
-constexpr int JAC_THREADS = 1024;
+constexpr int JAC_THREADS = 256;
+constexpr int JAC_CL = 8;   // CTAs per k (portable cluster size)
 constexpr double DF_JACOBI_TOL = 1e-14;
 constexpr double DF_JACOBI_ABS = 1e-15;
 
@@ -39,39 +40,60 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_doub
 // player at position x of step s of the circle ordering on m (even) players
 __device__ __forceinline__ int circle_player(int x, int s, int m) { return x == 0 ? 0 : ((x - 1 + s) % (m - 1)) + 1; }
 
+// One thread-block cluster of JAC_CL CTAs per k (the FP64 work of a step
+// spread over JAC_CL SMs).  Every CTA computes the rotation parameters of all
+// pairs of a step from the same values of A, so all CTAs agree bit for bit
+// (and on the rotation count) without exchanging anything; the column and row
+// updates are split over the cluster.  Phases are separated by hardware cluster
+// barriers (every thread of every CTA reaches each one: the control flow is
+// uniform, the early exit included).  A and U live in global memory.
 // gate: NULL (every k) or info[k]; k with info[k] == 0 (Cholesky route taken) are skipped.
 // info_out[k] = sweeps run (>= 1), or DF_JACOBI_SWEEPS + 1 when the last sweep still rotated.
-__global__ void __launch_bounds__(JAC_THREADS) k_jacobi_herm(const double2 *__restrict__ J, int n, const int *gate,
-                                                           double2 *Awork, double2 *Uwork, double *lam, int *order,
-                                                           int *info_out)
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(JAC_CL, 1, 1) __launch_bounds__(JAC_THREADS)
+    k_jacobi_herm(const double2 *__restrict__ J, int n, const int *gate, double2 *Awork, double2 *Uwork, double *lam,
+                  int *order, int *info_out)
 {
     __shared__ double cs_c[DF_NMAX / 2], cs_s[DF_NMAX / 2];
     __shared__ double2 cs_e[DF_NMAX / 2];   // e^{i phi} of each pair
     __shared__ int pp_[DF_NMAX / 2], qq_[DF_NMAX / 2];
     __shared__ int nrot;
     __shared__ double red[JAC_THREADS];
-    const int k = blockIdx.x, tid = threadIdx.x;
-    if (gate && gate[k] == 0) return;
+    const int k = blockIdx.x / JAC_CL, rank = blockIdx.x % JAC_CL, tid = threadIdx.x;
+    const int gtid = rank * JAC_THREADS + tid, gstride = JAC_CL * JAC_THREADS;
+    if (gate && gate[k] == 0) return;   // uniform over the cluster
     const long long nn = (long long)n * n;
     const double2 *Jk = J + k * nn;
     double2 *A = Awork + k * nn, *U = Uwork + k * nn;
+    // every CTA: the Frobenius norm of the Hermitian part (for the absolute floor)
     double f2 = 0.0;
     for (long long e = tid; e < nn; e += JAC_THREADS) {
         const int r = (int)(e / n), c = (int)(e - (long long)r * n);
         const double2 a = Jk[(long long)r * n + c], b = Jk[(long long)c * n + r];
-        const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));   // (J + J^H) / 2
-        A[e] = h;
-        U[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
-        f2 += h.x * h.x + h.y * h.y;
+        const double hx = 0.5 * (a.x + b.x), hy = 0.5 * (a.y - b.y);
+        f2 += hx * hx + hy * hy;
     }
     red[tid] = f2;
+    // the cluster's slice of A = (J + J^H) / 2 and U = 1
+    for (long long e = gtid; e < nn; e += gstride) {
+        const int r = (int)(e / n), c = (int)(e - (long long)r * n);
+        const double2 a = Jk[(long long)r * n + c], b = Jk[(long long)c * n + r];
+        A[e] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        U[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    }
     __syncthreads();
     for (int w = JAC_THREADS / 2; w > 0; w >>= 1) {
         if (tid < w) red[tid] += red[tid + w];
         __syncthreads();
     }
     const double gabs = DF_JACOBI_ABS * sqrt(red[0]);
+    cluster_barrier();
     const int m = n + (n & 1), npair = m / 2;
+    const long long nwork = (long long)npair * n;
     int sweep = 0, converged = 0;
     while (sweep < DF_JACOBI_SWEEPS && !converged) {
         if (tid == 0) nrot = 0;
@@ -90,9 +112,9 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi_herm(const double2 *__re
                 double c = 1.0, sn = 0.0;
                 double2 e = make_double2(1.0, 0.0);
                 if (q < n) {
-                    const double2 apq = A[(long long)p * n + q];
+                    const double2 apq = __ldcg(A + (long long)p * n + q);
                     const double g = sqrt(apq.x * apq.x + apq.y * apq.y);
-                    const double app = A[(long long)p * n + p].x, aqq = A[(long long)q * n + q].x;
+                    const double app = __ldcg(A + (long long)p * n + p).x, aqq = __ldcg(A + (long long)q * n + q).x;
                     if (g > fmax(DF_JACOBI_TOL * sqrt(fabs(app * aqq)), gabs) && g > 1e-300) {
                         e = make_double2(apq.x / g, apq.y / g);
                         const double tau = (aqq - app) / (2.0 * g);
@@ -107,53 +129,53 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi_herm(const double2 *__re
                 cs_e[j] = e;
             }
             if (my_rot) atomicAdd(&nrot, my_rot);
-            __syncthreads();
+            cluster_barrier();   // every CTA has read A for the parameters
             // columns: A <- A J, U <- U J; J_pp = c, J_qp = -s e*, J_pq = s, J_qq = c e*
-            for (long long w = tid; w < (long long)npair * n; w += JAC_THREADS) {
+            for (long long w = gtid; w < nwork; w += gstride) {
                 const int j = (int)(w / n), r = (int)(w - (long long)j * n);
                 if (cs_s[j] == 0.0) continue;
                 const int p = pp_[j], q = qq_[j];
                 const double c = cs_c[j], sn = cs_s[j];
                 const double2 ec = make_double2(cs_e[j].x, -cs_e[j].y);
                 double2 *row = A + (long long)r * n;
-                const double2 ap = row[p], aq = zmul(row[q], ec);
+                const double2 ap = __ldcg(row + p), aq = zmul(__ldcg(row + q), ec);
                 row[p] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
                 row[q] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
                 double2 *ur = U + (long long)r * n;
-                const double2 up = ur[p], uq = zmul(ur[q], ec);
+                const double2 up = __ldcg(ur + p), uq = zmul(__ldcg(ur + q), ec);
                 ur[p] = make_double2(c * up.x - sn * uq.x, c * up.y - sn * uq.y);
                 ur[q] = make_double2(sn * up.x + c * uq.x, sn * up.y + c * uq.y);
             }
-            __syncthreads();
+            cluster_barrier();
             // rows: A <- J^H A; (J^H)_pp = c, (J^H)_pq = -s e, (J^H)_qp = s, (J^H)_qq = c e
-            for (long long w = tid; w < (long long)npair * n; w += JAC_THREADS) {
+            for (long long w = gtid; w < nwork; w += gstride) {
                 const int j = (int)(w / n), col = (int)(w - (long long)j * n);
                 if (cs_s[j] == 0.0) continue;
                 const int p = pp_[j], q = qq_[j];
                 const double c = cs_c[j], sn = cs_s[j];
-                const double2 ap = A[(long long)p * n + col], aq = zmul(A[(long long)q * n + col], cs_e[j]);
+                const double2 ap = __ldcg(A + (long long)p * n + col), aq = zmul(__ldcg(A + (long long)q * n + col), cs_e[j]);
                 A[(long long)p * n + col] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
                 A[(long long)q * n + col] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
             }
-            __syncthreads();
+            cluster_barrier();
         }
         sweep++;
         converged = nrot == 0;
         __syncthreads();
     }
-    if (tid == 0) info_out[k] = converged ? sweep : DF_JACOBI_SWEEPS + 1;
+    if (rank == 0 && tid == 0) info_out[k] = converged ? sweep : DF_JACOBI_SWEEPS + 1;
     // eigenvalues descending, ties by index, by rank counting
     double *lk = lam + (long long)k * n;
     int *ok = order + (long long)k * n;
-    for (int i = tid; i < n; i += JAC_THREADS) {
-        const double v = A[(long long)i * n + i].x;
-        int rank = 0;
+    for (int i = gtid; i < n; i += gstride) {
+        const double v = __ldcg(A + (long long)i * n + i).x;
+        int rk = 0;
         for (int j = 0; j < n; j++) {
-            const double u = A[(long long)j * n + j].x;
-            rank += (u > v) || (u == v && j < i);
+            const double u = __ldcg(A + (long long)j * n + j).x;
+            rk += (u > v) || (u == v && j < i);
         }
-        lk[rank] = v;
-        ok[rank] = i;
+        lk[rk] = v;
+        ok[rk] = i;
     }
 }
 
@@ -254,10 +276,10 @@ int launch_df_eigen_route(int n, int nk, const double *J, const int *gate, doubl
                           double *lam, int *order, double *T, int *info, int *nkept, cudaStream_t st)
 {
     if (n < 1 || n > DF_NMAX || nk < 1) return RSGDF_EINVAL;
-    k_jacobi_herm<<<nk, JAC_THREADS, 0, st>>>((const double2 *)J, n, gate, (double2 *)A, (double2 *)U, lam, order,
-                                               info);
-    if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
     const long long nn = (long long)n * n;
+    k_jacobi_herm<<<nk * JAC_CL, JAC_THREADS, 0, st>>>((const double2 *)J, n, gate, (double2 *)A, (double2 *)U, lam,
+                                                       order, info);
+    if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
     dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), nk);
     // the gate is read before the Jacobi kernel overwrote it: eigen k now hold
     // a sweep count (>= 1), Cholesky k still 0
@@ -276,26 +298,30 @@ int launch_df_eigen_route(int n, int nk, const double *J, const int *gate, doubl
 // ---------------------------------------------------------------------------
 constexpr int GG_M = 32, GG_N = 32, GG_K = 16;
 
+// ksplit > 1 (atomic accumulation only): blockIdx.z = batch * ksplit + part,
+// each part summing its own kper-long slice of the contraction index.
 __global__ void __launch_bounds__(256) k_zgemm_gen(ZGemmGen g, const double2 *__restrict__ A,
-                                                   const double2 *__restrict__ B, double2 *C)
+                                                   const double2 *__restrict__ B, double2 *C, int ksplit,
+                                                   long long kper)
 {
     __shared__ double2 As[GG_K][GG_M + 1];
     __shared__ double2 Bs[GG_K][GG_N + 1];
-    const int b = blockIdx.z;
+    const int b = blockIdx.z / ksplit, part = blockIdx.z - b * ksplit;
     const long long ao = g.aoff[b], bo = g.boff[b], co = g.coff[b];
     const int m0 = blockIdx.y * GG_M, n0 = blockIdx.x * GG_N;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const long long KT = (long long)g.Q * g.S;
+    const long long kbeg = part * kper, kend = kbeg + kper < KT ? kbeg + kper : KT;
     const bool a_kfast = g.lda != 1, b_kfast = g.bn != 1;
     const double sa = g.conjA ? -1.0 : 1.0, sb = g.conjB ? -1.0 : 1.0;
     double cr[2][2] = {{0, 0}, {0, 0}}, ci[2][2] = {{0, 0}, {0, 0}};
-    for (long long k0 = 0; k0 < KT; k0 += GG_K) {
+    for (long long k0 = kbeg; k0 < kend; k0 += GG_K) {
         for (int e = threadIdx.x; e < GG_K * GG_M; e += 256) {
             const int kk = a_kfast ? e % GG_K : e / GG_M, mm = a_kfast ? e / GG_K : e % GG_M;
             const long long gk = k0 + kk;
             const int gm = m0 + mm;
             double2 v = make_double2(0.0, 0.0);
-            if (gk < KT && gm < g.M) {
+            if (gk < kend && gm < g.M) {
                 const long long q = gk / g.S, s = gk - q * g.S;
                 v = A[ao + gm * g.lda + q * g.aq + s * g.as];
                 v.y *= sa;
@@ -307,7 +333,7 @@ __global__ void __launch_bounds__(256) k_zgemm_gen(ZGemmGen g, const double2 *__
             const long long gk = k0 + kk;
             const int gn = n0 + nn;
             double2 v = make_double2(0.0, 0.0);
-            if (gk < KT && gn < g.N) {
+            if (gk < kend && gn < g.N) {
                 const long long q = gk / g.S, s = gk - q * g.S;
                 v = B[bo + q * g.bq + s * g.bs + gn * g.bn];
                 v.y *= sb;
@@ -350,13 +376,25 @@ __global__ void __launch_bounds__(256) k_zgemm_gen(ZGemmGen g, const double2 *__
 int launch_zgemm_gen(const ZGemmGen &g, int batch, const double *A, const double *B, double *C, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0 || batch <= 0) return RSGDF_OK;
-    for (int b0 = 0; b0 < batch; b0 += 65535) {
+    const long long tiles = (long long)((g.N + GG_N - 1) / GG_N) * ((g.M + GG_M - 1) / GG_M);
+    const long long KT = (long long)g.Q * g.S;
+    // split the contraction over more CTAs when the output alone would not fill
+    // two waves of the SMs (atomic accumulation only), keeping >= 4 chunks per part
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int ksplit = 1;
+    if (g.atomic && tiles * batch < 2LL * nsm)
+        ksplit = (int)std::max(1LL, std::min((2LL * nsm + tiles * batch - 1) / (tiles * batch), KT / (4 * GG_K)));
+    const long long kper = ((KT + ksplit - 1) / ksplit + GG_K - 1) / GG_K * GG_K;
+    ksplit = (int)((KT + kper - 1) / kper);
+    const int bmax = 65535 / ksplit;
+    for (int b0 = 0; b0 < batch; b0 += bmax) {
         ZGemmGen h = g;
         h.aoff += b0;
         h.boff += b0;
         h.coff += b0;
-        dim3 grid((g.N + GG_N - 1) / GG_N, (g.M + GG_M - 1) / GG_M, std::min(65535, batch - b0));
-        k_zgemm_gen<<<grid, 256, 0, st>>>(h, (const double2 *)A, (const double2 *)B, (double2 *)C);
+        dim3 grid((g.N + GG_N - 1) / GG_N, (g.M + GG_M - 1) / GG_M, std::min(bmax, batch - b0) * ksplit);
+        k_zgemm_gen<<<grid, 256, 0, st>>>(h, (const double2 *)A, (const double2 *)B, (double2 *)C, ksplit, kper);
         if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
     }
     return RSGDF_OK;
