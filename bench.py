@@ -448,6 +448,16 @@ def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64):
         ek = -float(np.real(sum(np.trace(Dh[k] @ Km[k]) for k in range(prob.nk)))) / (4 * prob.nk)
         hj, hk = hfproxy.energies(V.cpu().numpy(), kp, prob.kmesh, hfproxy.fit_transforms(J.cpu().numpy(), 1e-6), Dh)
         res.update({"E_J": ej, "E_K": ek, "dE_J_vs_host": abs(ej - hj), "dE_K_vs_host": abs(ek - hk)})
+        # Cartesian -> spherical transform of the whole j3c tensor (HBM-bound gather)
+        Vs = rsgdf.rsgdf_cart2sph_j3c(prob.ao, prob.aux, V)
+        res["cart2sph_ms"] = ev(lambda: rsgdf.rsgdf_cart2sph_j3c(prob.ao, prob.aux, V))
+        nbytes = V.numel() * 16 + Vs.numel() * 16
+        res["cart2sph_gbs"] = nbytes / (res["cart2sph_ms"] * 1e-3) / 1e9
+        res["cart2sph_bytes"] = int(nbytes)
+        peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(peaks):
+            res["cart2sph_frac_of_measured_hbm"] = res["cart2sph_gbs"] / json.load(open(peaks))["hbm_gbs"]
+        del Vs
         out["%dx%dx%d" % km] = res
         del V, B, J, keep
         torch.cuda.empty_cache()

@@ -386,6 +386,32 @@ int rsgdf_df_fit(const rsgdf_cell *cell, const double *T, int naux, int nao, int
 int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
                 const double *D, double *J_out, double *K_out, void *stream);
 
+/*
+ * Spherical (pure) functions.  The paper's bases are spherical; every integral
+ * here is computed over Cartesian shells and converted afterwards.  A spherical
+ * function is chi_{lm} = sum_c s_{mc} chi_c over its shell's Cartesian functions,
+ * s the monomial coefficients of the real regular solid harmonics in Racah
+ * normalisation without the Condon-Shortley phase (C_l^m for m >= 0, S_l^|m| for
+ * m < 0), ordered m = -l .. l; for l = 1 that is (y, z, x).  With the Cartesian
+ * shells normalised on their x^l component (see the conventions above) every
+ * spherical function has unit norm.
+ *
+ * rsgdf_sph_coefficients (host): s_out [(2l+1)][(l+1)(l+2)/2], 0 <= l <= RSGDF_LMAX.
+ * rsgdf_sph_nfunc (host): number of spherical functions of a basis.
+ * rsgdf_cart2sph_j3c: V_sph[pair][P'][mu'][nu'] = sum s s s V_cart[pair][P][mu][nu]
+ *   over aux shells [s0, s1) (the layout rsgdf_j3c writes for that range);
+ *   device complex arrays, V_sph must not overlap V_cart.  V_cart must hold
+ *   [npair][Cartesian functions of the range][nao][nao]: the call reads it
+ *   by that layout.
+ * rsgdf_cart2sph_j2c: J_sph[k] = s J_cart[k] s^T; device complex [nk][naux][naux]
+ *   in, [nk][nsph][nsph] out, no overlap.
+ */
+int rsgdf_sph_coefficients(int l, double *s_out);
+int rsgdf_sph_nfunc(const rsgdf_basis *b, int *nsph_out);
+int rsgdf_cart2sph_j3c(const rsgdf_basis *ao, const rsgdf_basis *aux, int s0, int s1, int npair,
+                       const double *V_cart, double *V_sph, void *stream);
+int rsgdf_cart2sph_j2c(const rsgdf_basis *aux, int nk, const double *J_cart, double *J_sph, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

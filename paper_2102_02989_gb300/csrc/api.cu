@@ -2102,4 +2102,107 @@ int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int 
     return RSGDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Cartesian -> real solid harmonic transforms
+// ---------------------------------------------------------------------------
+int rsgdf_sph_coefficients(int l, double *s_out)
+{
+    t_err.clear();
+    if (l < 0 || l > RSGDF_LMAX) return fail(RSGDF_EINVAL, "l outside 0..RSGDF_LMAX");
+    if (!s_out) return fail(RSGDF_EINVAL, "s_out is NULL");
+    std::vector<double> s;
+    sph_coefficients(l, s);
+    std::copy(s.begin(), s.end(), s_out);
+    return RSGDF_OK;
+}
+
+int rsgdf_sph_nfunc(const rsgdf_basis *b, int *nsph_out)
+{
+    t_err.clear();
+    HBasis h;
+    RC(load_basis(b, h, t_err));
+    if (!nsph_out) return fail(RSGDF_EINVAL, "nsph_out is NULL");
+    int n = 0;
+    for (int l : h.l) n += 2 * l + 1;
+    *nsph_out = n;
+    return RSGDF_OK;
+}
+
+static int upload_sph_map(Scratch &S, const std::vector<int> &ls, SphMapDev &m, int &nsph, int &ncart)
+{
+    std::vector<int> off, idx;
+    std::vector<double> coef;
+    sph_map(ls, off, idx, coef);
+    nsph = (int)off.size() - 1;
+    ncart = 0;
+    for (int l : ls) ncart += (l + 1) * (l + 2) / 2;
+    int *doff, *didx;
+    double *dcoef;
+    RC(S.upload(doff, off));
+    RC(S.upload(didx, idx));
+    RC(S.upload(dcoef, coef));
+    m.off = doff;
+    m.idx = didx;
+    m.coef = dcoef;
+    return RSGDF_OK;
+}
+
+int rsgdf_cart2sph_j3c(const rsgdf_basis *ao_in, const rsgdf_basis *aux_in, int s0, int s1, int npair,
+                       const double *V_cart, double *V_sph, void *stream)
+{
+    t_err.clear();
+    HBasis ao, ax;
+    RC(load_basis(ao_in, ao, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    if (s0 < 0 || s1 > ax.nshell || s0 >= s1) return fail(RSGDF_EINVAL, "aux shell range outside the basis");
+    if (npair < 1) return fail(RSGDF_EINVAL, "need at least one k pair");
+    if (!V_cart || !V_sph) return fail(RSGDF_EINVAL, "V_cart and V_sph are required");
+    const std::vector<int> lx(ax.l.begin() + s0, ax.l.begin() + s1);
+    int ncx = 0, nsx = 0;
+    for (int l : lx) {
+        ncx += (l + 1) * (l + 2) / 2;
+        nsx += 2 * l + 1;
+    }
+    int nsa = 0;
+    for (int l : ao.l) nsa += 2 * l + 1;
+    const size_t in_bytes = (size_t)16 * npair * ncx * ao.nfunc * ao.nfunc;
+    const size_t out_bytes = (size_t)16 * npair * nsx * nsa * nsa;
+    const char *a = (const char *)V_cart, *b = (const char *)V_sph;
+    if (a < b + out_bytes && b < a + in_bytes) return fail(RSGDF_EINVAL, "V_sph overlaps V_cart");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    SphMapDev mx, ma;
+    int nsph_x, ncart_x, nsph_a, ncart_a;
+    RC(upload_sph_map(S, lx, mx, nsph_x, ncart_x));
+    RC(upload_sph_map(S, ao.l, ma, nsph_a, ncart_a));
+    RC(launch_cart2sph(V_cart, V_sph, npair, nsph_x, nsph_a, nsph_a, ncart_x, ncart_a, ncart_a, mx, ma, ma, st));
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+int rsgdf_cart2sph_j2c(const rsgdf_basis *aux_in, int nk, const double *J_cart, double *J_sph, void *stream)
+{
+    t_err.clear();
+    HBasis ax;
+    RC(load_basis(aux_in, ax, t_err));
+    if (nk < 1) return fail(RSGDF_EINVAL, "need at least one k");
+    if (!J_cart || !J_sph) return fail(RSGDF_EINVAL, "J_cart and J_sph are required");
+    int ns = 0;
+    for (int l : ax.l) ns += 2 * l + 1;
+    const size_t in_bytes = (size_t)16 * nk * ax.nfunc * ax.nfunc, out_bytes = (size_t)16 * nk * ns * ns;
+    const char *a = (const char *)J_cart, *b = (const char *)J_sph;
+    if (a < b + out_bytes && b < a + in_bytes) return fail(RSGDF_EINVAL, "J_sph overlaps J_cart");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    SphMapDev mx, one;
+    int nsph_x, ncart_x, n1, c1;
+    RC(upload_sph_map(S, ax.l, mx, nsph_x, ncart_x));
+    RC(upload_sph_map(S, std::vector<int>{0}, one, n1, c1));   // identity on a trailing unit index
+    RC(launch_cart2sph(J_cart, J_sph, nk, nsph_x, nsph_x, 1, ncart_x, ncart_x, 1, mx, mx, one, st));
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
 }  // extern "C"

@@ -235,4 +235,14 @@ struct ZGemmGen {
 };
 int launch_zgemm_gen(const ZGemmGen &g, int batch, const double *A, const double *B, double *C, cudaStream_t st);
 
+// Cartesian -> real solid harmonic transform (k_sph.cu)
+void sph_coefficients(int l, std::vector<double> &s);
+void sph_map(const std::vector<int> &ls, std::vector<int> &off, std::vector<int> &idx, std::vector<double> &coef);
+struct SphMapDev {
+    const int *off, *idx;   // CSR rows per spherical function
+    const double *coef;
+};
+int launch_cart2sph(const double *in, double *out, long long nb, int n1, int n2, int n3, int c1, int c2, int c3,
+                    SphMapDev m1, SphMapDev m2, SphMapDev m3, cudaStream_t st);
+
 }  // namespace rsgdf

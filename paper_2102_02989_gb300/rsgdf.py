@@ -31,7 +31,8 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_mlp_nparams", "rsgdf_mlp_create", "rsgdf_mlp_destroy", "rsgdf_mlp_get_params",
            "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
-           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk")
+           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk",
+           "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -127,6 +128,10 @@ def load():
         lib.rsgdf_df_metric.argtypes = [vp, i, i, i, C.c_double, vp, vp, vp, vp, vp]
         lib.rsgdf_df_fit.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp]
         lib.rsgdf_df_jk.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp]
+        lib.rsgdf_sph_coefficients.argtypes = [i, vp]
+        lib.rsgdf_sph_nfunc.argtypes = [vp, vp]
+        lib.rsgdf_cart2sph_j3c.argtypes = [vp, vp, i, i, i, vp, vp, vp]
+        lib.rsgdf_cart2sph_j2c.argtypes = [vp, i, vp, vp, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -344,6 +349,46 @@ def rsgdf_df_jk(a, kmesh, B, kpairs, D, with_j=True, with_k=True, stream=None):
                            _cplx_cuda(D, "D"), C.c_void_p(Jm.data_ptr() if with_j else 0),
                            C.c_void_p(Km.data_ptr() if with_k else 0), _stream_ptr(stream)))
     return Jm, Km
+
+
+def rsgdf_sph_coefficients(l):
+    """[(2l+1)][ncart] monomial coefficients of the real solid harmonics (host)."""
+    out = np.zeros((2 * l + 1, (l + 1) * (l + 2) // 2))
+    _check(load().rsgdf_sph_coefficients(int(l), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def rsgdf_sph_nfunc(basis):
+    n = C.c_int(0)
+    _check(load().rsgdf_sph_nfunc(_BasisRef(basis).ref(), C.byref(n)))
+    return n.value
+
+
+def rsgdf_cart2sph_j3c(ao, aux, V, shells=None, stream=None):
+    """V [npair][nP][nao][nao] over Cartesian functions -> the same over spherical ones."""
+    import torch
+    ra, rx = _BasisRef(ao), _BasisRef(aux)
+    s0, s1 = shells if shells else (0, len(rx.l))
+    nsx = sum(2 * int(l) + 1 for l in rx.l[s0:s1])
+    nsa = sum(2 * int(l) + 1 for l in ra.l)
+    ncx = sum((int(l) + 1) * (int(l) + 2) // 2 for l in rx.l[s0:s1])
+    assert tuple(V.shape[1:]) == (ncx, ra.nfunc, ra.nfunc), "V must be [npair][nP][nao][nao] over Cartesian functions"
+    out = torch.empty((V.shape[0], nsx, nsa, nsa), dtype=torch.complex128, device=V.device)
+    _check(load().rsgdf_cart2sph_j3c(ra.ref(), rx.ref(), s0, s1, int(V.shape[0]), _cplx_cuda(V, "V"),
+                                     _cplx_cuda(out, "out"), _stream_ptr(stream)))
+    return out
+
+
+def rsgdf_cart2sph_j2c(aux, J, stream=None):
+    """J [nk][naux][naux] over Cartesian functions -> the same over spherical ones."""
+    import torch
+    rx = _BasisRef(aux)
+    ns = sum(2 * int(l) + 1 for l in rx.l)
+    assert tuple(J.shape[1:]) == (rx.nfunc, rx.nfunc), "J must be [nk][naux][naux] over Cartesian functions"
+    out = torch.empty((J.shape[0], ns, ns), dtype=torch.complex128, device=J.device)
+    _check(load().rsgdf_cart2sph_j2c(rx.ref(), int(J.shape[0]), _cplx_cuda(J, "J"), _cplx_cuda(out, "out"),
+                                     _stream_ptr(stream)))
+    return out
 
 
 def rsgdf_last_stats() -> dict:

@@ -131,3 +131,34 @@ def test_df_fit_jk_argument_errors_without_device(rs, bad):
         rc = lib.rsgdf_df_jk(C.byref(c), ptr(V), naux, nao, npair, kpa.ctypes.data_as(C.c_void_p), ptr(1 << 35),
                              out, ptr(0), None)
         assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+
+
+def test_sph_coefficients_match_the_oracle(rs):
+    from oracle import sph
+    for l in range(4):
+        assert np.max(np.abs(rs.rsgdf_sph_coefficients(l) - sph.coefficients(l))) < 1e-13
+    p = inputs.tiny(lmax_ao=2, lmax_aux=3)
+    assert rs.rsgdf_sph_nfunc(p.aux) == sum(2 * int(l) + 1 for l in p.aux.l)
+
+
+@pytest.mark.parametrize("bad", ["l", "range", "npair", "overlap", "nk"])
+def test_cart2sph_argument_errors_without_device(rs, bad):
+    import ctypes as C
+    lib = rs.load()
+    if bad == "l":
+        assert lib.rsgdf_sph_coefficients(4, C.c_void_p(16)) == rs.RSGDF_EINVAL
+        return
+    p = inputs.tiny(lmax_ao=1, lmax_aux=2)
+    ra, rx = rs._BasisRef(p.ao), rs._BasisRef(p.aux)
+    if bad == "nk":
+        assert lib.rsgdf_cart2sph_j2c(rx.ref(), 0, C.c_void_p(1 << 20), C.c_void_p(1 << 30), None) == rs.RSGDF_EINVAL
+        return
+    s0, s1, npair, out = 0, len(rx.l), 2, 1 << 30
+    if bad == "range":
+        s1 = len(rx.l) + 1
+    if bad == "npair":
+        npair = 0
+    if bad == "overlap":
+        out = (1 << 20) + 32
+    rc = lib.rsgdf_cart2sph_j3c(ra.ref(), rx.ref(), s0, s1, npair, C.c_void_p(1 << 20), C.c_void_p(out), None)
+    assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
