@@ -380,11 +380,19 @@ int rsgdf_df_fit(const rsgdf_cell *cell, const double *T, int naux, int nao, int
  *   B      : [npair][naux][nao][nao] from rsgdf_df_fit
  *   kpairs : host int [npair][2], no pair listed twice
  *   D      : [Nk][nao][nao]
+ *   rho_in : [naux] or NULL (then rho from the listed pairs).  A caller that
+ *            splits the pairs over processes sums rsgdf_df_rho over all of
+ *            them and passes the total: J^k then needs only the local (k, k)
+ *            pairs, and J and K are sums of the processes' results.
  *   J_out, K_out : [Nk][nao][nao] or NULL (not both), overwritten
  * Scratch: naux complex, plus a bounded chunk of B-sized intermediates.
+ *
+ * rsgdf_df_rho: rho_P above over the listed pairs; rho_out [naux], overwritten.
  */
+int rsgdf_df_rho(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
+                 const double *D, double *rho_out, void *stream);
 int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
-                const double *D, double *J_out, double *K_out, void *stream);
+                const double *D, const double *rho_in, double *J_out, double *K_out, void *stream);
 
 /*
  * Spherical (pure) functions.  The paper's bases are spherical; every integral

@@ -129,16 +129,19 @@ def fit(T, V, kpairs, kmesh):
     return B
 
 
-def jk(B, kpairs, kmesh, D):
-    """(J, K, rho): J, K complex [Nk][nao][nao] as defined in the header."""
+def jk(B, kpairs, kmesh, D, rho=None):
+    """(J, K, rho): J, K complex [Nk][nao][nao] as defined in the header; rho
+    given (the fitted density over more pairs than these) replaces the one
+    summed from the listed diagonal pairs in J."""
     B = np.asarray(B)
     D = np.asarray(D)
     nk = int(np.prod(kmesh))
     npair, naux, nao, _ = B.shape
-    rho = np.zeros(naux, dtype=np.complex128)
-    for p, (k1, k2) in enumerate(np.asarray(kpairs)):
-        if k1 == k2:
-            rho += np.einsum("pmn,nm->p", B[p], D[k1])
+    if rho is None:
+        rho = np.zeros(naux, dtype=np.complex128)
+        for p, (k1, k2) in enumerate(np.asarray(kpairs)):
+            if k1 == k2:
+                rho += np.einsum("pmn,nm->p", B[p], D[k1])
     Jm = np.zeros((nk, nao, nao), dtype=np.complex128)
     Km = np.zeros((nk, nao, nao), dtype=np.complex128)
     for p, (k1, k2) in enumerate(np.asarray(kpairs)):

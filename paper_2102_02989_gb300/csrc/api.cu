@@ -1983,8 +1983,55 @@ int rsgdf_df_fit(const rsgdf_cell *cell, const double *T, int naux, int nao, int
     return RSGDF_OK;
 }
 
+// rho(P) = sum over the diagonal pairs of sum_{mu, nu} B[p](P, mu, nu) D[k](nu, mu); overwrites rho
+static int df_rho_launch(Scratch &S, const double *B, const double *D, int naux, int nao, int npair, const int *kpairs,
+                         double *rho, cudaStream_t st)
+{
+    const long long n2 = (long long)nao * nao, blk = (long long)naux * n2;
+    CU(cudaMemsetAsync(rho, 0, sizeof(double) * 2 * naux, st));
+    std::vector<long long> pa, pb, pc;
+    for (int p = 0; p < npair; p++)
+        if (kpairs[2 * p] == kpairs[2 * p + 1]) {
+            pa.push_back(p * blk);
+            pb.push_back(kpairs[2 * p] * n2);
+            pc.push_back(0);
+        }
+    if (pa.empty()) return RSGDF_OK;
+    ZGemmGen g{};
+    g.M = naux;
+    g.N = 1;
+    g.Q = nao;
+    g.S = nao;
+    g.lda = n2;
+    g.aq = nao;
+    g.as = 1;
+    g.bq = 1;
+    g.bs = nao;
+    g.ldc = 1;
+    g.atomic = 1;
+    g.alpha = 1.0;
+    RC(upload_offsets(S, pa, pb, pc, g));
+    return launch_zgemm_gen(g, (int)pa.size(), B, D, rho, st);
+}
+
+int rsgdf_df_rho(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
+                 const double *D, double *rho_out, void *stream)
+{
+    t_err.clear();
+    Lattice L;
+    RC(df_pairs(cell, npair, kpairs, L, true));
+    if (!B || !D || !rho_out) return fail(RSGDF_EINVAL, "B, D and rho_out are required");
+    if (naux < 1 || nao < 1) return fail(RSGDF_EINVAL, "naux and nao must be >= 1");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    RC(df_rho_launch(S, B, D, naux, nao, npair, kpairs, rho_out, st));
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
 int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int npair, const int *kpairs,
-                const double *D, double *J_out, double *K_out, void *stream)
+                const double *D, const double *rho_in, double *J_out, double *K_out, void *stream)
 {
     t_err.clear();
     Lattice L;
@@ -1999,37 +2046,21 @@ int rsgdf_df_jk(const rsgdf_cell *cell, const double *B, int naux, int nao, int 
     const long long n2 = (long long)nao * nao, blk = (long long)naux * n2;
     if (J_out) {
         CU(cudaMemsetAsync(J_out, 0, sizeof(double) * 2 * Nk * n2, st));
-        std::vector<long long> pa, pb, pc, ja, jb, jc;
+        std::vector<long long> ja, jb, jc;
         for (int p = 0; p < npair; p++)
             if (kpairs[2 * p] == kpairs[2 * p + 1]) {
-                const int k = kpairs[2 * p];
-                pa.push_back(p * blk);
-                pb.push_back(k * n2);
-                pc.push_back(0);
                 ja.push_back(p * blk);
                 jb.push_back(0);
-                jc.push_back(k * n2);
+                jc.push_back(kpairs[2 * p] * n2);
             }
-        if (!pa.empty()) {
-            double *rho;
-            RC(S.alloc(rho, 2 * (size_t)naux));
-            CU(cudaMemsetAsync(rho, 0, sizeof(double) * 2 * naux, st));
-            // rho(P) += sum_{mu, nu} B[p](P, mu, nu) D[k](nu, mu)
-            ZGemmGen g{};
-            g.M = naux;
-            g.N = 1;
-            g.Q = nao;
-            g.S = nao;
-            g.lda = n2;
-            g.aq = nao;
-            g.as = 1;
-            g.bq = 1;
-            g.bs = nao;
-            g.ldc = 1;
-            g.atomic = 1;
-            g.alpha = 1.0;
-            RC(upload_offsets(S, pa, pb, pc, g));
-            RC(launch_zgemm_gen(g, (int)pa.size(), B, D, rho, st));
+        if (!ja.empty()) {
+            const double *rho = rho_in;
+            if (!rho) {
+                double *r;
+                RC(S.alloc(r, 2 * (size_t)naux));
+                RC(df_rho_launch(S, B, D, naux, nao, npair, kpairs, r, st));
+                rho = r;
+            }
             // J[k](x) = (1/Nk) sum_P B[p](P, x) conj(rho(P))
             ZGemmGen h{};
             h.M = (int)n2;

@@ -31,7 +31,7 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_mlp_nparams", "rsgdf_mlp_create", "rsgdf_mlp_destroy", "rsgdf_mlp_get_params",
            "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
-           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk",
+           "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk", "rsgdf_df_rho",
            "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c")
 RSGDF_MLP_NFEAT = 10
 
@@ -127,7 +127,8 @@ def load():
         lib.rsgdf_j3c_batch.argtypes = [i, vp, vp, vp, vp, vp]
         lib.rsgdf_df_metric.argtypes = [vp, i, i, i, C.c_double, vp, vp, vp, vp, vp]
         lib.rsgdf_df_fit.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp]
-        lib.rsgdf_df_jk.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp]
+        lib.rsgdf_df_jk.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, vp, vp]
+        lib.rsgdf_df_rho.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp]
         lib.rsgdf_sph_coefficients.argtypes = [i, vp]
         lib.rsgdf_sph_nfunc.argtypes = [vp, vp]
         lib.rsgdf_cart2sph_j3c.argtypes = [vp, vp, i, i, i, vp, vp, vp]
@@ -334,10 +335,24 @@ def rsgdf_df_fit(a, kmesh, T, V, kpairs, out=None, stream=None):
     return out
 
 
-def rsgdf_df_jk(a, kmesh, B, kpairs, D, with_j=True, with_k=True, stream=None):
+def rsgdf_df_rho(a, kmesh, B, kpairs, D, stream=None):
+    """rho_P = sum over the listed (k, k) pairs of Tr[B^kk_P D^k] (complex128 cuda [naux])."""
+    import torch
+    lib = load()
+    kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
+    naux, nao = int(B.shape[1]), int(B.shape[2])
+    rho = torch.empty(naux, dtype=torch.complex128, device=B.device)
+    c = _cell(a, kmesh)
+    _check(lib.rsgdf_df_rho(C.byref(c), _cplx_cuda(B, "B"), naux, nao, len(kp), kp.ctypes.data_as(C.c_void_p),
+                            _cplx_cuda(D, "D"), C.c_void_p(rho.data_ptr()), _stream_ptr(stream)))
+    return rho
+
+
+def rsgdf_df_jk(a, kmesh, B, kpairs, D, with_j=True, with_k=True, rho=None, stream=None):
     """Fitted Coulomb and exchange matrices (J, K) [Nk][nao][nao] of the
     densities D [Nk][nao][nao] from B [npair][naux][nao][nao] (complex128 cuda);
-    a matrix not asked for is None."""
+    a matrix not asked for is None.  rho: the fitted density summed over all
+    pairs (e.g. over processes), else taken from the listed pairs."""
     import torch
     lib = load()
     kp = np.ascontiguousarray(np.asarray(kpairs, dtype=np.int32).reshape(-1, 2))
@@ -346,7 +361,8 @@ def rsgdf_df_jk(a, kmesh, B, kpairs, D, with_j=True, with_k=True, stream=None):
     Km = torch.empty_like(D) if with_k else None
     c = _cell(a, kmesh)
     _check(lib.rsgdf_df_jk(C.byref(c), _cplx_cuda(B, "B"), naux, nao, len(kp), kp.ctypes.data_as(C.c_void_p),
-                           _cplx_cuda(D, "D"), C.c_void_p(Jm.data_ptr() if with_j else 0),
+                           _cplx_cuda(D, "D"), C.c_void_p(rho.data_ptr() if rho is not None else 0),
+                           C.c_void_p(Jm.data_ptr() if with_j else 0),
                            C.c_void_p(Km.data_ptr() if with_k else 0), _stream_ptr(stream)))
     return Jm, Km
 

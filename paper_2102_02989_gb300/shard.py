@@ -1,8 +1,10 @@
-"""Partitioning of the RSGDF work over ranks (one GPU each), with no exchange
-on the data path: aux-shell ranges of one j3c (rows P of V are independent:
-each needs the full lattice sums and G sum for its own aux functions only),
-or the cells of a batch.  Host logic only; every rank then calls the library
-on its own shard, and a consumer that wants the whole tensor gathers it.
+"""Partitioning of the RSGDF work over ranks (one GPU each).  The integrals
+need no exchange on the data path: aux-shell ranges of one j3c (rows P of V
+are independent: each needs the full lattice sums and G sum for its own aux
+functions only), or the cells of a batch.  The fitted J/K matrices of a
+pair-sharded B do have one: the fitted density rho sums over every diagonal
+pair before J can be formed, and K^{k1} sums over every k2 (df_jk_sharded).
+Host logic only; every rank calls the library on its own shard.
 """
 from __future__ import annotations
 
@@ -60,3 +62,35 @@ def reduce_timing(dist, times_ms, units, device=None):
     n = torch.tensor([float(units)], dtype=torch.float64, device=device)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return [float(x) for x in t.cpu()], float(n.item())
+
+
+def pair_shards(npair, nranks):
+    """k-pair indices per rank for the DF fit and J/K (equal counts to within
+    one, round robin, so diagonal pairs spread over the ranks); every pair
+    belongs to exactly one rank."""
+    return [list(range(r, npair, nranks)) for r in range(nranks)]
+
+
+def _sum_over_ranks(dist, x):
+    import torch
+    if x is None:
+        return None
+    r = torch.view_as_real(x) if x.is_complex() else x
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return x
+
+
+def df_jk_sharded(dist, rho_fn, jk_fn):
+    """Fitted J and K over k pairs split across ranks.  rho_fn() gives this
+    rank's fitted density (its diagonal pairs), jk_fn(rho) this rank's J/K
+    contributions given the total density; the exchange is one sum of rho
+    (naux numbers) before J and one sum of J and K (Nk nao^2 each) after.
+    With dist None the local results are returned unchanged."""
+    rho = rho_fn()
+    if dist is not None:
+        rho = _sum_over_ranks(dist, rho)
+    J, K = jk_fn(rho)
+    if dist is not None:
+        J = _sum_over_ranks(dist, J)
+        K = _sum_over_ranks(dist, K)
+    return J, K

@@ -129,7 +129,12 @@ def test_df_fit_jk_argument_errors_without_device(rs, bad):
     if bad in ("kidx", "npair", "dup", "noout"):
         out = ptr(0) if bad == "noout" else ptr(1 << 36)
         rc = lib.rsgdf_df_jk(C.byref(c), ptr(V), naux, nao, npair, kpa.ctypes.data_as(C.c_void_p), ptr(1 << 35),
-                             out, ptr(0), None)
+                             ptr(0), out, ptr(0), None)
+        assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+        if bad == "noout":
+            return
+        rc = lib.rsgdf_df_rho(C.byref(c), ptr(V), naux, nao, npair, kpa.ctypes.data_as(C.c_void_p), ptr(1 << 35),
+                              ptr(1 << 36), None)
         assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
 
 

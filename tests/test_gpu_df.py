@@ -164,3 +164,27 @@ def test_physical_metric_needs_the_fallback(rs, orc):
     ej, ek = dfjk.energies(Jm, Km, D)
     oj, ok = dfjk.energies(Jo, Ko, D)
     assert abs(ej - oj) < 1e-9 * abs(oj) and abs(ek - ok) < 1e-9 * abs(ok)
+
+
+def test_jk_from_pair_shards_with_summed_rho(rs):
+    """Two pair shards processed one after the other on one GPU, as two ranks
+    would (rho summed, then J and K summed), equal J/K over every pair; the
+    library's rho equals the oracle's."""
+    from paper_2102_02989_gb300 import shard
+    kmesh = (2, 2, 1)
+    J, V, D = inputs.df_synthetic(kmesh, naux=30, nao=7, nocc=2, cond=1e-5, seed=80)
+    kp = inputs.kpairs_all(4)
+    To, _, _, _ = dfjk.metric_transforms(J, "cholesky", rel=0.0)
+    Jo, Ko, rho_o = dfjk.jk(dfjk.fit(To, V, kp, kmesh), kp, kmesh, D)
+    a = np.eye(3) * 5.0
+    T = _dev(To)
+    Dd = _dev(D)
+    parts = shard.pair_shards(len(kp), 2)
+    Bs = [rs.rsgdf_df_fit(a, kmesh, T, _dev(V[s]), kp[s]) for s in parts]
+    rhos = [rs.rsgdf_df_rho(a, kmesh, B, kp[s], Dd) for B, s in zip(Bs, parts)]
+    rho = rhos[0] + rhos[1]
+    assert _rel(rho.cpu().numpy(), rho_o) < 1e-12
+    out = [rs.rsgdf_df_jk(a, kmesh, B, kp[s], Dd, rho=rho) for B, s in zip(Bs, parts)]
+    Jm = (out[0][0] + out[1][0]).cpu().numpy()
+    Km = (out[0][1] + out[1][1]).cpu().numpy()
+    assert _rel(Jm, Jo) < 1e-12 and _rel(Km, Ko) < 1e-12

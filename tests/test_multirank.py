@@ -73,3 +73,60 @@ def test_shard_partitions():
         cs = shard.cell_shards(cells, n)
         assert sorted(i for c in cs for i in c) == list(range(len(cells)))
     assert shard.aux_func_offset(p.aux, len(p.aux.l)) == p.aux.nfunc
+
+
+def _df_worker(rank, world, init_file, q):
+    import torch
+    import torch.distributed as dist
+    from oracle import dfjk
+    dist.init_process_group("gloo", init_method="file://" + init_file, rank=rank, world_size=world)
+    kmesh = (3, 1, 1)
+    J, V, D = inputs.df_synthetic(kmesh, naux=10, nao=4, nocc=2, cond=1e-4, seed=70)
+    kp = inputs.kpairs_all(3)
+    mine = shard.pair_shards(len(kp), world)[rank]
+    T, _, _, _ = dfjk.metric_transforms(J, "auto", rel=1e-10)
+    B = dfjk.fit(T, V[mine], kp[mine], kmesh)          # this rank's pairs only
+
+    def rho_fn():
+        return torch.from_numpy(dfjk.jk(B, kp[mine], kmesh, D)[2].copy())
+
+    def jk_fn(rho):
+        Jm, Km, _ = dfjk.jk(B, kp[mine], kmesh, D, rho=rho.numpy())
+        return torch.from_numpy(Jm), torch.from_numpy(Km)
+    Jt, Kt = shard.df_jk_sharded(dist, rho_fn, jk_fn)
+    dist.barrier()
+    dist.destroy_process_group()
+    if rank == 0:
+        q.put((Jt.numpy(), Kt.numpy()))
+
+
+def test_df_jk_over_pair_shards_equals_the_whole(orc_built, tmp_path):
+    """J/K from pairs split over two ranks (one sum of rho, one of J and K)
+    equal J/K from every pair in one process."""
+    import torch.multiprocessing as mp
+    from oracle import dfjk
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    init_file = str(tmp_path / "rendezvous_df")
+    procs = [ctx.Process(target=_df_worker, args=(r, 2, init_file, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    Jt, Kt = q.get(timeout=600)
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    kmesh = (3, 1, 1)
+    J, V, D = inputs.df_synthetic(kmesh, naux=10, nao=4, nocc=2, cond=1e-4, seed=70)
+    kp = inputs.kpairs_all(3)
+    T, _, _, _ = dfjk.metric_transforms(J, "auto", rel=1e-10)
+    Jo, Ko, _ = dfjk.jk(dfjk.fit(T, V, kp, kmesh), kp, kmesh, D)
+    assert np.max(np.abs(Jt - Jo)) < 1e-12 * np.max(np.abs(Jo))
+    assert np.max(np.abs(Kt - Ko)) < 1e-12 * np.max(np.abs(Ko))
+
+
+def test_pair_shards_cover_every_pair_once():
+    for npair, world in [(1, 2), (64, 3), (4096, 8), (5, 8)]:
+        sh = shard.pair_shards(npair, world)
+        flat = sorted(i for s in sh for i in s)
+        assert flat == list(range(npair))
+        assert max(len(s) for s in sh) - min(len(s) for s in sh) <= 1
