@@ -420,6 +420,32 @@ int rsgdf_cart2sph_j3c(const rsgdf_basis *ao, const rsgdf_basis *aux, int s0, in
                        const double *V_cart, double *V_sph, void *stream);
 int rsgdf_cart2sph_j2c(const rsgdf_basis *aux, int nk, const double *J_cart, double *J_sph, void *stream);
 
+/*
+ * Compact/diffuse split (Fig. 1 of the paper; host only, no device work).
+ * rsgdf_split_basis: every shell becomes a compact sub-shell (its primitives
+ * with exponent > alpha_cut, raw coefficients kept) and/or a diffuse one, in
+ * shell order, compact first; each sub-shell is normalised like any shell, so
+ * parent function = sum over its sub-shells of weight x sub-shell function.
+ *   nshell_out, nprim_total_out : sizes of the split basis (required)
+ *   l_out, nprim_out, prim_off_out, parent_out, kind_out : int [nshell] or NULL
+ *     (kind 0 = compact, 1 = diffuse; parent = shell of the input basis)
+ *   center_out : double [nshell][3] or NULL; weight_out : double [nshell] or NULL
+ *   exps_out, coeffs_out : double [nprim_total] or NULL
+ * Call once with NULL arrays for the sizes.
+ * rsgdf_sr_items_split: SR work the planner keeps (opts: omega / G box and
+ *   eps_screen as for rsgdf_j3c; all aux shells), n_items_out[6]: work items
+ *   (aux shell, AO shell pair, d) for [0] the input bases, [1] the split bases,
+ *   [2] the split bases restricted to the range-separated types (compact aux
+ *   function, pair not both diffuse); [3..5] the same as candidate primitive
+ *   terms (items x aux images within the triple's Rc cutoff x primitive
+ *   combinations; the kernel's per-term tests drop some of them).
+ */
+int rsgdf_split_basis(const rsgdf_basis *b, double alpha_cut, int *nshell_out, int *nprim_total_out, int *l_out,
+                      int *nprim_out, int *prim_off_out, double *center_out, double *exps_out, double *coeffs_out,
+                      int *parent_out, int *kind_out, double *weight_out);
+int rsgdf_sr_items_split(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux,
+                         const rsgdf_opts *opts, double alpha_cut, long long *n_items_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2236,4 +2236,77 @@ int rsgdf_cart2sph_j2c(const rsgdf_basis *aux_in, int nk, const double *J_cart, 
     return RSGDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Compact/diffuse split (host only)
+// ---------------------------------------------------------------------------
+int rsgdf_split_basis(const rsgdf_basis *b, double alpha_cut, int *nshell_out, int *nprim_total_out, int *l_out,
+                      int *nprim_out, int *prim_off_out, double *center_out, double *exps_out, double *coeffs_out,
+                      int *parent_out, int *kind_out, double *weight_out)
+{
+    t_err.clear();
+    if (!nshell_out || !nprim_total_out) return fail(RSGDF_EINVAL, "nshell_out and nprim_total_out are required");
+    SplitBasis sb;
+    RC(split_basis(b, alpha_cut, sb, t_err));
+    *nshell_out = (int)sb.l.size();
+    *nprim_total_out = (int)sb.exps.size();
+    auto put = [](auto *dst, const auto &v) {
+        if (dst) std::copy(v.begin(), v.end(), dst);
+    };
+    put(l_out, sb.l);
+    put(nprim_out, sb.nprim);
+    put(prim_off_out, sb.prim_off);
+    put(center_out, sb.center);
+    put(exps_out, sb.exps);
+    put(coeffs_out, sb.coeffs);
+    put(parent_out, sb.parent);
+    put(kind_out, sb.kind);
+    put(weight_out, sb.weight);
+    return RSGDF_OK;
+}
+
+int rsgdf_sr_items_split(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgdf_basis *aux_in,
+                         const rsgdf_opts *opts, double alpha_cut, long long *n_items_out)
+{
+    t_err.clear();
+    RC(check_opts(opts));
+    if (!n_items_out) return fail(RSGDF_EINVAL, "n_items_out is NULL");
+    Lattice L;
+    HBasis ao, ax;
+    RC(make_lattice(cell, L, t_err));
+    RC(load_basis(ao_in, ao, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    double omega;
+    int gm[3];
+    RC(derive_params(L, opts, omega, gm, t_err));
+    SplitBasis sa, sx;
+    RC(split_basis(ao_in, alpha_cut, sa, t_err));
+    RC(split_basis(aux_in, alpha_cut, sx, t_err));
+    const rsgdf_basis va = sa.view(), vx = sx.view();
+    HBasis hsa, hsx;
+    RC(load_basis(&va, hsa, t_err));
+    RC(load_basis(&vx, hsx, t_err));
+    SRPlan p0, p1, p2;
+    plan_sr3c(L, ao, ax, 0, ax.nshell, omega, opts->eps_screen, p0);
+    plan_sr3c(L, hsa, hsx, 0, hsx.nshell, omega, opts->eps_screen, p1);
+    // range-separated types only: compact aux function, pair not both diffuse
+    plan_sr3c(L, hsa, hsx, 0, hsx.nshell, omega, opts->eps_screen, p2, [&](int P, int mu, int nu) {
+        return sx.kind[P] == 0 && !(sa.kind[mu] == 1 && sa.kind[nu] == 1);
+    });
+    // candidate primitive terms: d items x aux images within the triple's
+    // Rc cutoff x primitive combinations (the kernel's per-term tests drop some)
+    auto terms = [](const SRPlan &p, const HBasis &a, const HBasis &x) {
+        long long t = 0;
+        for (const SRTriple &tr : p.tri)
+            t += (long long)tr.nd * tr.nsph * x.nprim[tr.P] * a.nprim[tr.mu] * a.nprim[tr.nu];
+        return t;
+    };
+    n_items_out[0] = p0.n_items;
+    n_items_out[1] = p1.n_items;
+    n_items_out[2] = p2.n_items;
+    n_items_out[3] = terms(p0, ao, ax);
+    n_items_out[4] = terms(p1, hsa, hsx);
+    n_items_out[5] = terms(p2, hsa, hsx);
+    return RSGDF_OK;
+}
+
 }  // extern "C"

@@ -555,7 +555,7 @@ void finish_plan(const Lattice &L, SRPlan &plan)
 }  // namespace
 
 void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, int s1, double omega, double eps,
-               SRPlan &plan)
+               SRPlan &plan, const std::function<bool(int, int, int)> &keep)
 {
     plan = SRPlan();
     int ns = ao.nshell;
@@ -569,7 +569,8 @@ void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, in
     });
     for (int P = s0; P < s1; P++)
         for (int pr = 0; pr < ns * ns; pr++)
-            pair_rmax[pr] = std::max(pair_rmax[pr], bnd[(size_t)(P - s0) * ns * ns + pr].r12_max);
+            if (!keep || keep(P, pr / ns, pr % ns))
+                pair_rmax[pr] = std::max(pair_rmax[pr], bnd[(size_t)(P - s0) * ns * ns + pr].r12_max);
     // per AO shell pair: d vectors with R12 <= max over P, sorted by R12
     plan.pair_doff.assign(ns * ns + 1, 0);
     std::vector<std::vector<double>> pair_r12(ns * ns);
@@ -602,6 +603,7 @@ void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, in
     for (int P = s0; P < s1; P++)
         for (int mu = 0; mu < ns; mu++)
             for (int nu = 0; nu < ns; nu++) {
+                if (keep && !keep(P, mu, nu)) continue;
                 Bounds &B = bnd[((size_t)(P - s0) * ns + mu) * ns + nu];
                 int pr = mu * ns + nu;
                 SRTriple t;
@@ -769,6 +771,62 @@ long long sr_term_flops(int L)
                 }
     f += ntuv(L);
     return f;
+}
+
+}  // namespace rsgdf
+
+namespace rsgdf {
+
+// Compact/diffuse split (Fig. 1 of the paper): every shell becomes a compact
+// sub-shell (its primitives with exponent > alpha_cut) and/or a diffuse one,
+// with the parent's raw coefficients; each sub-shell is normalised on its own,
+// so the parent function is sum_S (n_parent / n_S) chi_S, n the contraction
+// norm factor (1/sqrt of the self-overlap of the x^l component).
+static double contracted_norm(int l, const double *e, const double *c, int np)
+{
+    double self = 0.0;
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < np; j++) {
+            const double p = e[i] + e[j];
+            self += c[i] * xl_norm(e[i], l) * c[j] * xl_norm(e[j], l) * dfact_odd(2 * l - 1) / std::pow(2.0 * p, l) *
+                    std::pow(PI / p, 1.5);
+        }
+    return 1.0 / std::sqrt(self);
+}
+
+int split_basis(const rsgdf_basis *b, double acut, SplitBasis &out, std::string &err)
+{
+    HBasis h;
+    const int rc = load_basis(b, h, err);
+    if (rc != RSGDF_OK) return rc;
+    if (!(acut >= 0.0) || !std::isfinite(acut)) {
+        err = "alpha_cut must be finite and >= 0";
+        return RSGDF_EINVAL;
+    }
+    out = SplitBasis();
+    for (int s = 0; s < b->nshell; s++) {
+        const int l = b->l[s], np = b->nprim[s], o = b->prim_off[s];
+        const double npar = contracted_norm(l, b->exps + o, b->coeffs + o, np);
+        for (int kind = 0; kind < 2; kind++) {   // 0 compact, 1 diffuse
+            std::vector<double> e, c;
+            for (int i = 0; i < np; i++)
+                if ((b->exps[o + i] > acut) == (kind == 0)) {
+                    e.push_back(b->exps[o + i]);
+                    c.push_back(b->coeffs[o + i]);
+                }
+            if (e.empty()) continue;
+            out.l.push_back(l);
+            out.nprim.push_back((int)e.size());
+            out.prim_off.push_back((int)out.exps.size());
+            for (int x = 0; x < 3; x++) out.center.push_back(b->center[3 * s + x]);
+            out.exps.insert(out.exps.end(), e.begin(), e.end());
+            out.coeffs.insert(out.coeffs.end(), c.begin(), c.end());
+            out.parent.push_back(s);
+            out.kind.push_back(kind);
+            out.weight.push_back(npar / contracted_norm(l, e.data(), c.data(), (int)e.size()));
+        }
+    }
+    return RSGDF_OK;
 }
 
 }  // namespace rsgdf

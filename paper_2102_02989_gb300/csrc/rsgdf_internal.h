@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/rsgdf.h"
@@ -80,8 +81,27 @@ int load_basis(const rsgdf_basis *b, HBasis &h, std::string &err, bool allow_emp
 void unit_partner_basis(const HBasis &aux, HBasis &out);
 int derive_params(const Lattice &L, const rsgdf_opts *o, double &omega, int gmesh[3], std::string &err);
 // j3c SR plan for aux shells [s0, s1)
+// keep(P, mu, nu), when given, restricts the plan to the triples it accepts
 void plan_sr3c(const Lattice &L, const HBasis &ao, const HBasis &aux, int s0, int s1, double omega,
-               double eps, SRPlan &plan);
+               double eps, SRPlan &plan, const std::function<bool(int, int, int)> &keep = {});
+// compact/diffuse split of a basis at alpha_cut (primitives with exponent > alpha_cut are compact)
+struct SplitBasis {
+    std::vector<int> l, nprim, prim_off, parent, kind;   // kind 0 compact, 1 diffuse
+    std::vector<double> center, exps, coeffs, weight;    // weight: coefficient of the sub-shell in its parent
+    rsgdf_basis view() const
+    {
+        rsgdf_basis b;
+        b.nshell = (int)l.size();
+        b.l = l.data();
+        b.nprim = nprim.data();
+        b.prim_off = prim_off.data();
+        b.center = center.data();
+        b.exps = exps.data();
+        b.coeffs = coeffs.data();
+        return b;
+    }
+};
+int split_basis(const rsgdf_basis *b, double acut, SplitBasis &out, std::string &err);
 // j2c SR plan: "AO" basis = aux + unit partner, pairs (Q, unit)
 void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double omega, double eps,
                SRPlan &plan);

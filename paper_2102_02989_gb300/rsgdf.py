@@ -32,7 +32,8 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_mlp_set_margin", "rsgdf_mlp_set_base", "rsgdf_mlp_forward", "rsgdf_mlp_loss_grad", "rsgdf_mlp_train",
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
            "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk", "rsgdf_df_rho",
-           "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c")
+           "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c",
+           "rsgdf_split_basis", "rsgdf_sr_items_split")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -133,6 +134,8 @@ def load():
         lib.rsgdf_sph_nfunc.argtypes = [vp, vp]
         lib.rsgdf_cart2sph_j3c.argtypes = [vp, vp, i, i, i, vp, vp, vp]
         lib.rsgdf_cart2sph_j2c.argtypes = [vp, i, vp, vp, vp]
+        lib.rsgdf_split_basis.argtypes = [vp, C.c_double] + [vp] * 11
+        lib.rsgdf_sr_items_split.argtypes = [vp, vp, vp, vp, C.c_double, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -405,6 +408,37 @@ def rsgdf_cart2sph_j2c(aux, J, stream=None):
     _check(load().rsgdf_cart2sph_j2c(rx.ref(), int(J.shape[0]), _cplx_cuda(J, "J"), _cplx_cuda(out, "out"),
                                      _stream_ptr(stream)))
     return out
+
+
+def rsgdf_split_basis(basis, alpha_cut):
+    """Compact/diffuse split (host): dict of the split basis' arrays (l, nprim,
+    prim_off, center, exps, coeffs) plus parent, kind (0 compact, 1 diffuse)
+    and weight per sub-shell."""
+    lib = load()
+    rb = _BasisRef(basis)
+    ns, npt = C.c_int(0), C.c_int(0)
+    nul = [None] * 9
+    _check(lib.rsgdf_split_basis(rb.ref(), float(alpha_cut), C.byref(ns), C.byref(npt), *nul))
+    n, m = ns.value, npt.value
+    out = {"l": np.zeros(n, np.int32), "nprim": np.zeros(n, np.int32), "prim_off": np.zeros(n, np.int32),
+           "center": np.zeros((n, 3)), "exps": np.zeros(m), "coeffs": np.zeros(m), "parent": np.zeros(n, np.int32),
+           "kind": np.zeros(n, np.int32), "weight": np.zeros(n)}
+    p = lambda k: out[k].ctypes.data_as(C.c_void_p)
+    _check(lib.rsgdf_split_basis(rb.ref(), float(alpha_cut), C.byref(ns), C.byref(npt), p("l"), p("nprim"),
+                                 p("prim_off"), p("center"), p("exps"), p("coeffs"), p("parent"), p("kind"),
+                                 p("weight")))
+    return out
+
+
+def rsgdf_sr_items_split(a, kmesh, ao, aux, alpha_cut, **opt):
+    """Host planner only: {"items": (unsplit, split, split range-separated types),
+    "terms": the same as candidate primitive terms}."""
+    lib = load()
+    ra, rx = _BasisRef(ao), _BasisRef(aux)
+    n = (C.c_longlong * 6)()
+    o = _opts(**opt)
+    _check(lib.rsgdf_sr_items_split(C.byref(_cell(a, kmesh)), ra.ref(), rx.ref(), C.byref(o), float(alpha_cut), n))
+    return {"items": tuple(int(x) for x in n[:3]), "terms": tuple(int(x) for x in n[3:])}
 
 
 def rsgdf_last_stats() -> dict:
