@@ -6,7 +6,7 @@ the synthetic density, a zero error for identical tensors, and the removal
 of an exactly linearly dependent aux function."""
 import numpy as np
 
-from paper_2102_02989_gb300 import hfproxy
+from paper_2102_02989_gb300 import hfproxy, inputs
 
 
 def _problem(kmesh, naux=5, nao=4, seed=0):
@@ -77,3 +77,17 @@ def test_density_k_symmetry():
         assert abs(np.trace(D[k]).real - 4.0) < 1e-12
         assert np.min(np.linalg.eigvalsh(D[k])) > -1e-12
     assert hfproxy.k12(1, 0, km) == hfproxy.kneg(1, km)
+
+
+def test_energies_equal_the_df_oracle_jk():
+    """The proxy's energies (eigen-route fit, energies from B directly) equal
+    those of the DF oracle's J/K matrices on the same tensors and metric."""
+    from oracle import dfjk
+    kmesh = (2, 2, 1)
+    J, V, D = inputs.df_synthetic(kmesh, naux=14, nao=5, nocc=2, cond=1e-4, seed=90)
+    kp = inputs.kpairs_all(4)
+    ej, ek = hfproxy.energies(V, kp, kmesh, hfproxy.fit_transforms(J, 1e-6), D)
+    T, _, _, _ = dfjk.metric_transforms(J, "eigen", rel=1e-6)
+    Jm, Km, _ = dfjk.jk(dfjk.fit(T, V, kp, kmesh), kp, kmesh, D)
+    oj, ok = dfjk.energies(Jm, Km, D)
+    assert abs(ej - oj) < 1e-10 * abs(oj) and abs(ek - ok) < 1e-10 * abs(ok)
