@@ -137,6 +137,27 @@ def oracle_sample(p, omega, gmesh, shells):
     return cnt["terms"], dt, oracle.num_threads()
 
 
+def df_oracle_sample(J, V, D, kp, kmesh, ao_l, aux_l):
+    """The DF and spherical oracles (numpy) on the same tensors as the GPU:
+    metric transforms (automatic route), fit, J/K, and the Cartesian -> spherical
+    transform of V.  Returns {step: seconds} and the threads numpy may use."""
+    from oracle import dfjk, sph
+    out = {}
+    t0 = time.perf_counter()
+    T, _, _, _ = dfjk.metric_transforms(J, "auto", rel=1e-6)
+    out["metric_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    B = dfjk.fit(T, V, kp, kmesh)
+    out["fit_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dfjk.jk(B, kp, kmesh, D)
+    out["jk_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sph.j3c(V, ao_l, aux_l)
+    out["cart2sph_s"] = time.perf_counter() - t0
+    return out, os.cpu_count()
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -354,7 +375,8 @@ def main():
         if paths["learned-mixed"].get("mlp") is not None:
             line["rocksalt_chunk"] = rocksalt_bench(rsgdf, inputs, paths, np, torch)
             line["auto_omega"] = auto_omega_bench(rsgdf, p, paths, make, timed, np)
-        line["df_consumers"] = df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64)
+        line["df_consumers"] = df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64,
+                                        cpu_baseline=world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -391,11 +413,15 @@ def per_kmesh(rsgdf, inputs, paths, make, timed, np):
             res["value_learned_mixed"] = res["fp64"]["sr_terms"] / (res["learned-mixed"]["ms_per_step"] * 1e-3)
         res["value_fp64"] = res["fp64"]["sr_terms"] / (res["fp64"]["ms_per_step"] * 1e-3)
         del Vs
+        if cpu_baseline and km == (2, 2, 2):
+            t, cores = df_oracle_sample(J.cpu().numpy(), V.cpu().numpy(), Dh, kp, prob.kmesh, prob.ao.l, prob.aux.l)
+            res["cpu_baseline"] = {"kind": "oracle", "cores": cores, "unit": "s",
+                                   "sample": "the same tensors, numpy FP64 (LAPACK eigh, matmul)", **t}
         out["%dx%dx%d" % km] = res
     return out
 
 
-def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64):
+def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64, cpu_baseline=True):
     """Density-fitting consumers after the step: the fitting transforms of the
     j2c metrics (automatic Cholesky / eigen choice), the fit B = T V over every
     k pair and the fitted Coulomb and exchange matrices of a synthetic
@@ -458,6 +484,10 @@ def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64):
         if os.path.exists(peaks):
             res["cart2sph_frac_of_measured_hbm"] = res["cart2sph_gbs"] / json.load(open(peaks))["hbm_gbs"]
         del Vs
+        if cpu_baseline and km == (2, 2, 2):
+            t, cores = df_oracle_sample(J.cpu().numpy(), V.cpu().numpy(), Dh, kp, prob.kmesh, prob.ao.l, prob.aux.l)
+            res["cpu_baseline"] = {"kind": "oracle", "cores": cores, "unit": "s",
+                                   "sample": "the same tensors, numpy FP64 (LAPACK eigh, matmul)", **t}
         out["%dx%dx%d" % km] = res
         del V, B, J, keep
         torch.cuda.empty_cache()
