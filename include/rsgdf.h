@@ -84,7 +84,14 @@ typedef struct {
     int screening;      /* RSGDF_SCREEN_BOUND or RSGDF_SCREEN_LEARNED */
     const void *mlp;    /* learned screening: handle from rsgdf_mlp_create, or NULL */
     void *stream;       /* cudaStream_t or NULL */
+    double split_alpha; /* > 0: SR sums and the G = 0 term only for range-separated
+                           types (compact aux shell, AO pair not both diffuse; a shell
+                           is diffuse when every exponent is <= split_alpha); 0: all */
+    int kernel;         /* RSGDF_KERNEL_ERF, or RSGDF_KERNEL_PLAIN (rsgdf_j3c_lr only) */
 } rsgdf_opts;
+
+#define RSGDF_KERNEL_ERF 0     /* erf(omega r)/r in the G sum (Eq. VPmunu_LR) */
+#define RSGDF_KERNEL_PLAIN 1   /* 1/r in the G sum, no range separation (Eq. VPmunu_FT) */
 
 /*
  * j2c (Eq. JPQ with the split of Eq. Coulomb_RS, "readily adapted" to the
@@ -119,7 +126,10 @@ int rsgdf_j3c_sr(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basi
 /*
  * LR part of j3c (Eqs. VPmunu_LR and AFT_pairden): analytic Fourier transforms
  * of the AO pair densities on the G box, weighted by the transformed aux
- * functions and 4 pi/Omega e^{-q^2/4 omega^2}/q^2, q = G + k12 != 0.
+ * functions and 4 pi/Omega e^{-q^2/4 omega^2}/q^2, q = G + k12 != 0.  With
+ * opts->kernel = RSGDF_KERNEL_PLAIN the weight is 4 pi/Omega 1/q^2: the whole
+ * Coulomb integral in reciprocal space on that box (Eq. VPmunu_FT), the route
+ * of the diffuse integral types of the compact/diffuse split.
  * Same arguments as rsgdf_j3c_sr; the result is ADDED to V_out.
  */
 int rsgdf_j3c_lr(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux,
@@ -432,6 +442,13 @@ int rsgdf_cart2sph_j2c(const rsgdf_basis *aux, int nk, const double *J_cart, dou
  *   center_out : double [nshell][3] or NULL; weight_out : double [nshell] or NULL
  *   exps_out, coeffs_out : double [nprim_total] or NULL
  * Call once with NULL arrays for the sizes.
+ * rsgdf_split_combine: V_out[pair][P][mu][nu] over the input bases from two
+ *   tensors over the split bases ([npair][split aux][split AO][split AO],
+ *   device complex): V_rs, computed by rsgdf_j3c with opts->split_alpha =
+ *   alpha_cut, supplies the (C|cc) and (C|cd) blocks, V_g, the plain-kernel
+ *   rsgdf_j3c_lr on the same box, the other four; the sub-functions are summed
+ *   into their parents with the split's weights.  All aux shells.  V_out must
+ *   not overlap the inputs.
  * rsgdf_sr_items_split: SR work the planner keeps (opts: omega / G box and
  *   eps_screen as for rsgdf_j3c; all aux shells), n_items_out[6]: work items
  *   (aux shell, AO shell pair, d) for [0] the input bases, [1] the split bases,
@@ -445,6 +462,8 @@ int rsgdf_split_basis(const rsgdf_basis *b, double alpha_cut, int *nshell_out, i
                       int *parent_out, int *kind_out, double *weight_out);
 int rsgdf_sr_items_split(const rsgdf_cell *cell, const rsgdf_basis *ao, const rsgdf_basis *aux,
                          const rsgdf_opts *opts, double alpha_cut, long long *n_items_out);
+int rsgdf_split_combine(const rsgdf_basis *ao, const rsgdf_basis *aux, double alpha_cut, int npair,
+                        const double *V_rs, const double *V_g, double *V_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -236,6 +236,9 @@ static int check_opts(const rsgdf_opts *o)
     if (o->precision != RSGDF_FP64 && o->precision != RSGDF_MIXED) return fail(RSGDF_EINVAL, "unknown precision mode");
     if (o->screening != RSGDF_SCREEN_BOUND && o->screening != RSGDF_SCREEN_LEARNED)
         return fail(RSGDF_EINVAL, "unknown screening mode");
+    if (!(o->split_alpha >= 0.0) || !std::isfinite(o->split_alpha))
+        return fail(RSGDF_EINVAL, "split_alpha must be finite and >= 0");
+    if (o->kernel != RSGDF_KERNEL_ERF && o->kernel != RSGDF_KERNEL_PLAIN) return fail(RSGDF_EINVAL, "unknown kernel");
     return RSGDF_OK;
 }
 
@@ -639,6 +642,10 @@ struct J3cProblem {
     double *SP = nullptr, *Sf = nullptr;
     double g0fac = 0.0;
     bool g0 = false;
+    // compact/diffuse split (opts->split_alpha > 0): SR and G0 on the range-separated types only
+    double split_alpha = 0.0;
+    std::vector<char> ax_diffuse, ao_diffuse;          // per shell: every exponent <= split_alpha
+    int *dmask_ax = nullptr, *dmask_ao = nullptr;      // per function of the aux range / the AO basis
     // G space
     int *dg = nullptr;
     int NG = 0;
@@ -685,7 +692,12 @@ static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, uns
     const long long m = P.m;
     const double omega = P.omega;
     // SR folded sums X[lt][dt][P][mu][nu]
-    plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan);
+    if (P.split_alpha > 0.0)
+        plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan, [&](int Q, int mu, int nu) {
+            return !P.ax_diffuse[Q] && !(P.ao_diffuse[mu] && P.ao_diffuse[nu]);
+        });
+    else
+        plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan);
     P.nlt = (P.gkey.size() == 1 && P.gkey[0] == 0) ? 1 : Nk;
     RC(S.alloc(P.X, (size_t)P.nlt * Nk * m));
     SRExtras ex;
@@ -809,6 +821,27 @@ static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int np
         RC(S.alloc(P.SP, nP));
         RC(S.alloc(P.Sf, (size_t)Nk * nao * nao));
     }
+    P.split_alpha = opts->split_alpha;
+    if (P.split_alpha > 0.0) {
+        auto diffuse = [&](const HBasis &b, int sh) {
+            for (int i = 0; i < b.nprim[sh]; i++)
+                if (b.exps[b.poff[sh] + i] > P.split_alpha) return (char)0;
+            return (char)1;
+        };
+        P.ax_diffuse.resize(P.ax.nshell);
+        P.ao_diffuse.resize(P.ao.nshell);
+        for (int sh = 0; sh < P.ax.nshell; sh++) P.ax_diffuse[sh] = diffuse(P.ax, sh);
+        for (int sh = 0; sh < P.ao.nshell; sh++) P.ao_diffuse[sh] = diffuse(P.ao, sh);
+        if (P.g0) {
+            std::vector<int> mx(nP, 0), ma(nao, 0);
+            for (int sh = P.s0; sh < P.s1; sh++)
+                for (int c = 0; c < ncart(P.ax.l[sh]); c++) mx[P.ax.foff[sh] - P.pfunc0 + c] = P.ax_diffuse[sh];
+            for (int sh = 0; sh < P.ao.nshell; sh++)
+                for (int c = 0; c < ncart(P.ao.l[sh]); c++) ma[P.ao.foff[sh] + c] = P.ao_diffuse[sh];
+            RC(S.upload(P.dmask_ax, mx));
+            RC(S.upload(P.dmask_ao, ma));
+        }
+    }
     // G-space data
     std::vector<int> gl;
     gbox(P.gm, gl);
@@ -836,6 +869,7 @@ static int j3c_prepare(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, int np
             k12_frac(L, k12, Ga.f12);
             Ga.vol = L.vol;
             Ga.omega = omega;
+            Ga.full_coulomb = opts->kernel == RSGDF_KERNEL_PLAIN;
             P.garg.push_back(Ga);
         }
     }
@@ -904,8 +938,12 @@ static int j3c_exec_tables(J3cProblem &P, cudaStream_t st, int &nl)
         k_aux_charge<<<(P.s1 - P.s0 + 63) / 64, 64, 0, st>>>(P.dax, P.s0, P.s1, P.pfunc0, P.SP);
         CU(cudaGetLastError());
         RC(launch_ovlp_fold(P.dao, P.ao.nshell, P.nao, P.dent, P.dseg, P.ptab, P.Nk, P.Sf, st));
-        t_timer.end();
         nl += 2;
+        if (P.dmask_ax) {   // the G = 0 term belongs to the range-separated types only
+            RC(launch_split_g0_mask(P.SP, P.nP, P.dmask_ax, P.Sf, P.Nk, P.nao, P.dmask_ao, st));
+            nl++;
+        }
+        t_timer.end();
     }
     if (P.Bpl) CU(cudaMemsetAsync(P.Bpl, 0, sizeof(float) * P.nbpl, st));
     return RSGDF_OK;
@@ -1071,6 +1109,8 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     J3cProblem P;
     RC(j3c_check(P, cell, ao_in, aux_in, opts, npair, kpairs, s0, s1));
     if (!V) return fail(RSGDF_EINVAL, "V_out is NULL");
+    if (opts->kernel == RSGDF_KERNEL_PLAIN && mode != MODE_LR)
+        return fail(RSGDF_EINVAL, "the plain kernel is for rsgdf_j3c_lr only");
     RC(check_device());
     cudaStream_t st = (cudaStream_t)opts->stream;
     RC(ensure_boys(st));
@@ -1237,6 +1277,8 @@ int rsgdf_j3c_batch_create(int nprob, const rsgdf_problem *probs, const rsgdf_op
     if (flags & ~(RSGDF_BATCH_GRAPH | RSGDF_BATCH_AUTOTUNE)) return fail(RSGDF_EINVAL, "unknown batch flag");
     *out = nullptr;
     RC(check_opts(opts));
+    if (opts->split_alpha > 0.0 || opts->kernel != RSGDF_KERNEL_ERF)
+        return fail(RSGDF_ENOTIMPL, "the batch runs the plain range-separated path only");
     std::unique_ptr<rsgdf_batch> b(new rsgdf_batch());
     b->nprob = nprob;
     b->flags = flags;
@@ -2306,6 +2348,79 @@ int rsgdf_sr_items_split(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const
     n_items_out[3] = terms(p0, ao, ax);
     n_items_out[4] = terms(p1, hsa, hsx);
     n_items_out[5] = terms(p2, hsa, hsx);
+    return RSGDF_OK;
+}
+
+// parent function -> (sub function, weight) CSR map and kind per sub function
+static int upload_split_map(Scratch &S, const rsgdf_basis *b, const SplitBasis &sb, SphMapDev &m, int *&dkind,
+                            int &nsub)
+{
+    std::vector<int> pf0(b->nshell + 1, 0);
+    for (int s = 0; s < b->nshell; s++) pf0[s + 1] = pf0[s] + ncart(b->l[s]);
+    std::vector<std::vector<std::pair<int, double>>> rows(pf0[b->nshell]);
+    std::vector<int> kind;
+    int f = 0;
+    for (size_t j = 0; j < sb.l.size(); j++) {
+        for (int c = 0; c < ncart(sb.l[j]); c++) {
+            rows[pf0[sb.parent[j]] + c].push_back({f + c, sb.weight[j]});
+            kind.push_back(sb.kind[j]);
+        }
+        f += ncart(sb.l[j]);
+    }
+    nsub = f;
+    std::vector<int> off(1, 0), idx;
+    std::vector<double> coef;
+    for (auto &r : rows) {
+        for (auto &e : r) {
+            idx.push_back(e.first);
+            coef.push_back(e.second);
+        }
+        off.push_back((int)idx.size());
+    }
+    int *doff, *didx;
+    double *dcoef;
+    RC(S.upload(doff, off));
+    RC(S.upload(didx, idx));
+    RC(S.upload(dcoef, coef));
+    RC(S.upload(dkind, kind));
+    m.off = doff;
+    m.idx = didx;
+    m.coef = dcoef;
+    return RSGDF_OK;
+}
+
+int rsgdf_split_combine(const rsgdf_basis *ao_in, const rsgdf_basis *aux_in, double alpha_cut, int npair,
+                        const double *V_rs, const double *V_g, double *V_out, void *stream)
+{
+    t_err.clear();
+    HBasis ao, ax;
+    RC(load_basis(ao_in, ao, t_err));
+    RC(load_basis(aux_in, ax, t_err));
+    if (npair < 1) return fail(RSGDF_EINVAL, "need at least one k pair");
+    if (!V_rs || !V_g || !V_out) return fail(RSGDF_EINVAL, "V_rs, V_g and V_out are required");
+    SplitBasis sa, sx;
+    RC(split_basis(ao_in, alpha_cut, sa, t_err));
+    RC(split_basis(aux_in, alpha_cut, sx, t_err));
+    int nsa = 0, nsx = 0;
+    for (int l : sa.l) nsa += ncart(l);
+    for (int l : sx.l) nsx += ncart(l);
+    const size_t in_bytes = (size_t)16 * npair * nsx * nsa * nsa;
+    const size_t out_bytes = (size_t)16 * npair * ax.nfunc * ao.nfunc * ao.nfunc;
+    auto overlap = [](const void *a, size_t na, const void *b, size_t nb) {
+        const char *x = (const char *)a, *y = (const char *)b;
+        return x < y + nb && y < x + na;
+    };
+    if (overlap(V_out, out_bytes, V_rs, in_bytes) || overlap(V_out, out_bytes, V_g, in_bytes))
+        return fail(RSGDF_EINVAL, "V_out overlaps an input");
+    RC(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch S(st);
+    SphMapDev mx, ma;
+    int *kx, *ka, nx, na;
+    RC(upload_split_map(S, aux_in, sx, mx, kx, nx));
+    RC(upload_split_map(S, ao_in, sa, ma, ka, na));
+    RC(launch_split_combine(V_rs, V_g, V_out, npair, ax.nfunc, ao.nfunc, nx, na, mx, ma, kx, ka, st));
+    CU(cudaGetLastError());
     return RSGDF_OK;
 }
 

@@ -244,5 +244,10 @@ struct SphMapDev {
 };
 int launch_cart2sph(const double *in, double *out, long long nb, int n1, int n2, int n3, int c1, int c2, int c3,
                     SphMapDev m1, SphMapDev m2, SphMapDev m3, cudaStream_t st);
+// compact/diffuse split (k_split.cu)
+int launch_split_g0_mask(double *SP, int nP, const int *mask_ax, double *Sf, int Nk, int nao, const int *mask_ao,
+                         cudaStream_t st);
+int launch_split_combine(const double *Vrs, const double *Vg, double *out, long long nb, int n1, int n2, int c1,
+                         int c2, SphMapDev mx, SphMapDev ma, const int *kind_x, const int *kind_a, cudaStream_t st);
 
 }  // namespace rsgdf

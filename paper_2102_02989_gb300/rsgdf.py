@@ -23,6 +23,7 @@ RSGDF_FP64, RSGDF_MIXED = 0, 1
 RSGDF_SCREEN_BOUND, RSGDF_SCREEN_LEARNED = 0, 1
 RSGDF_BATCH_GRAPH, RSGDF_BATCH_AUTOTUNE = 1, 2
 RSGDF_FIT_CHOLESKY, RSGDF_FIT_EIGEN, RSGDF_FIT_AUTO = 0, 1, 2
+RSGDF_KERNEL_ERF, RSGDF_KERNEL_PLAIN = 0, 1
 RSGDF_DF_NMAX, RSGDF_DF_SWEEPS = 1024, 40
 
 # names exported by the library (every declaration of include/rsgdf.h)
@@ -33,7 +34,7 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
            "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk", "rsgdf_df_rho",
            "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c",
-           "rsgdf_split_basis", "rsgdf_sr_items_split")
+           "rsgdf_split_basis", "rsgdf_sr_items_split", "rsgdf_split_combine")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -56,7 +57,7 @@ class _Cell(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("omega", C.c_double), ("gmesh", C.c_int * 3), ("eps_screen", C.c_double),
                 ("eps_lr", C.c_double), ("precision", C.c_int), ("screening", C.c_int),
-                ("mlp", C.c_void_p), ("stream", C.c_void_p)]
+                ("mlp", C.c_void_p), ("stream", C.c_void_p), ("split_alpha", C.c_double), ("kernel", C.c_int)]
 
 
 class _Problem(C.Structure):
@@ -136,6 +137,7 @@ def load():
         lib.rsgdf_cart2sph_j2c.argtypes = [vp, i, vp, vp, vp]
         lib.rsgdf_split_basis.argtypes = [vp, C.c_double] + [vp] * 11
         lib.rsgdf_sr_items_split.argtypes = [vp, vp, vp, vp, C.c_double, vp]
+        lib.rsgdf_split_combine.argtypes = [vp, vp, C.c_double, i, vp, vp, vp, vp]
         for n in EXPORTS:
             if n != "rsgdf_last_error":
                 getattr(lib, n).restype = C.c_int
@@ -184,8 +186,9 @@ def _stream_ptr(stream):
 
 
 def _opts(omega=None, gmesh=None, eps_screen=1e-8, eps_lr=1e-8, precision=RSGDF_FP64,
-          screening=RSGDF_SCREEN_BOUND, mlp=None, stream=None):
+          screening=RSGDF_SCREEN_BOUND, mlp=None, stream=None, split_alpha=0.0, kernel=RSGDF_KERNEL_ERF):
     o = _Opts()
+    o.split_alpha, o.kernel = float(split_alpha), int(kernel)
     o.omega = float(omega) if omega else 0.0
     for k in range(3):
         o.gmesh[k] = int(gmesh[k]) if gmesh is not None else 0
@@ -439,6 +442,21 @@ def rsgdf_sr_items_split(a, kmesh, ao, aux, alpha_cut, **opt):
     o = _opts(**opt)
     _check(lib.rsgdf_sr_items_split(C.byref(_cell(a, kmesh)), ra.ref(), rx.ref(), C.byref(o), float(alpha_cut), n))
     return {"items": tuple(int(x) for x in n[:3]), "terms": tuple(int(x) for x in n[3:])}
+
+
+def rsgdf_split_combine(ao, aux, alpha_cut, V_rs, V_g, stream=None):
+    """V over the input bases from the range-separated (V_rs) and plain-kernel
+    (V_g) tensors over the split bases (complex128 cuda)."""
+    import torch
+    ra, rx = _BasisRef(ao), _BasisRef(aux)
+    out = torch.empty((V_rs.shape[0], rx.nfunc, ra.nfunc, ra.nfunc), dtype=torch.complex128, device=V_rs.device)
+    nsub = lambda b: int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in rsgdf_split_basis(b, alpha_cut)["l"]))
+    want = (nsub(aux), nsub(ao), nsub(ao))
+    assert tuple(V_rs.shape[1:]) == want and V_g.shape == V_rs.shape, "V_rs, V_g must be over the split bases"
+    _check(load().rsgdf_split_combine(ra.ref(), rx.ref(), float(alpha_cut), int(V_rs.shape[0]),
+                                      _cplx_cuda(V_rs, "V_rs"), _cplx_cuda(V_g, "V_g"), _cplx_cuda(out, "out"),
+                                      _stream_ptr(stream)))
+    return out
 
 
 def rsgdf_last_stats() -> dict:

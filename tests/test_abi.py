@@ -167,3 +167,26 @@ def test_cart2sph_argument_errors_without_device(rs, bad):
         out = (1 << 20) + 32
     rc = lib.rsgdf_cart2sph_j3c(ra.ref(), rx.ref(), s0, s1, npair, C.c_void_p(1 << 20), C.c_void_p(out), None)
     assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+
+
+@pytest.mark.parametrize("bad", ["alpha", "plain_j3c", "plain_sr", "kernel"])
+def test_split_options_rejected_without_device(rs, bad):
+    import ctypes as C
+    lib = rs.load()
+    p = inputs.tiny()
+    ra, rx = rs._BasisRef(p.ao), rs._BasisRef(p.aux)
+    o = rs._opts(omega=0.9, eps_screen=1e-10, eps_lr=1e-10)
+    name = "rsgdf_j3c"
+    if bad == "alpha":
+        o.split_alpha = -1.0
+    if bad == "plain_j3c":
+        o.kernel = rs.RSGDF_KERNEL_PLAIN
+    if bad == "plain_sr":
+        o.kernel, name = rs.RSGDF_KERNEL_PLAIN, "rsgdf_j3c_sr"
+    if bad == "kernel":
+        o.kernel = 7
+    c = rs._cell(p.a, (1, 1, 1))
+    kpa = np.zeros((1, 2), np.int32)
+    rc = getattr(lib, name)(C.byref(c), ra.ref(), rx.ref(), C.byref(o), 1, kpa.ctypes.data_as(C.c_void_p), 0,
+                            len(rx.l), C.c_void_p(16))
+    assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
