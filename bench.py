@@ -377,6 +377,10 @@ def main():
             line["auto_omega"] = auto_omega_bench(rsgdf, p, paths, make, timed, np)
         line["df_consumers"] = df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64,
                                         cpu_baseline=world == 1 and not args.no_cpu_baseline)
+        try:
+            line["split_route"] = split_bench(rsgdf, inputs, torch)
+        except Exception as e:   # recorded, so that a failure here does not cost the headline line
+            line["split_route"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shells = (0, 16)
         n, dt, th = oracle_sample(p, omega, gmesh, shells)
@@ -494,6 +498,46 @@ def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64, cpu_base
     out["note"] = ("FP64 throughout; fit and J/K are complex GEMMs on the FP64 pipe (flops 8 naux^2 nao^2 and "
                    "16 naux nao^3 per k pair); metric = Cholesky + triangular inverse, Jacobi where it fails")
     return out
+
+
+def split_bench(rsgdf, inputs, torch):
+    """j3c (every k pair and aux shell, FP64) of the headline cell at 2x2x2 on
+    the 11^3 box (omega 0.691, the box the tuner picks for the mixed path):
+    the plain range-separated route against the compact/diffuse split route
+    (alpha_cut = omega^2/2), CUDA events around the whole call, median of 3
+    after one warm-up; the planner's SR work of both."""
+    from paper_2102_02989_gb300 import cdsplit
+    p = inputs.config2((2, 2, 2))
+    gm = (11, 11, 11)
+    w, _ = rsgdf.rsgdf_params(p.a, p.kmesh, gmesh=gm, eps_lr=p.eps_lr)
+    kp = inputs.kpairs_all(p.nk)
+    opt = dict(omega=w, gmesh=gm, eps_screen=p.eps_sr, eps_lr=p.eps_lr)
+    ac = 0.5 * w * w
+    out = {}
+
+    def ev(f, reps=3):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {"workload": "FCC a=6.74 2-atom cell, 2x2x2, all 64 k pairs, j3c only, FP64, eps 1e-8",
+           "gmesh": list(gm), "omega": w, "alpha_cut": ac}
+    res["plain_ms"] = ev(lambda: out.update(plain=rsgdf.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, **opt)))
+    res["split_ms"] = ev(lambda: out.update(split=cdsplit.j3c_split(p.a, p.kmesh, p.ao, p.aux, kp, alpha_cut=ac,
+                                                                      **opt)))
+    res["speedup"] = res["plain_ms"] / res["split_ms"]
+    res["max_abs_split_vs_plain"] = (out["split"] - out["plain"]).abs().max().item()
+    res["sr_candidate_terms_plain_split_rs"] = list(
+        rsgdf.rsgdf_sr_items_split(p.a, p.kmesh, p.ao, p.aux, ac, **opt)["terms"])
+    return res
 
 
 def auto_omega_bench(rsgdf, p, paths, make, timed, np):
