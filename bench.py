@@ -501,11 +501,11 @@ def df_bench(rsgdf, hfproxy, inputs, paths, make, np, torch, peak_fp64, cpu_base
 
 
 def split_bench(rsgdf, inputs, torch):
-    """j3c (every k pair and aux shell, FP64) of the headline cell at 2x2x2 on
-    the 11^3 box (omega 0.691, the box the tuner picks for the mixed path):
-    the plain range-separated route against the compact/diffuse split route
-    (alpha_cut = omega^2/2), CUDA events around the whole call, median of 3
-    after one warm-up; the planner's SR work of both."""
+    """j3c (every k pair and aux shell) of the headline cell at 2x2x2 on the
+    11^3 box (omega 0.691, the box the tuner picks for the mixed path): the
+    plain range-separated route against the compact/diffuse split route
+    (alpha_cut = omega^2/2), FP64 and mixed, CUDA events around the whole
+    call, median of 3 after one warm-up; the planner's SR work of both."""
     from paper_2102_02989_gb300 import cdsplit
     p = inputs.config2((2, 2, 2))
     gm = (11, 11, 11)
@@ -528,15 +528,22 @@ def split_bench(rsgdf, inputs, torch):
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
-    res = {"workload": "FCC a=6.74 2-atom cell, 2x2x2, all 64 k pairs, j3c only, FP64, eps 1e-8",
-           "gmesh": list(gm), "omega": w, "alpha_cut": ac}
-    res["plain_ms"] = ev(lambda: out.update(plain=rsgdf.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, **opt)))
-    res["split_ms"] = ev(lambda: out.update(split=cdsplit.j3c_split(p.a, p.kmesh, p.ao, p.aux, kp, alpha_cut=ac,
-                                                                      **opt)))
-    res["speedup"] = res["plain_ms"] / res["split_ms"]
-    res["max_abs_split_vs_plain"] = (out["split"] - out["plain"]).abs().max().item()
-    res["sr_candidate_terms_plain_split_rs"] = list(
-        rsgdf.rsgdf_sr_items_split(p.a, p.kmesh, p.ao, p.aux, ac, **opt)["terms"])
+    res = {"workload": "FCC a=6.74 2-atom cell, 2x2x2, all 64 k pairs, j3c only, eps 1e-8",
+           "gmesh": list(gm), "omega": w, "alpha_cut": ac,
+           "sr_candidate_terms_plain_split_rs": list(
+               rsgdf.rsgdf_sr_items_split(p.a, p.kmesh, p.ao, p.aux, ac, **opt)["terms"])}
+    for name, prec in (("fp64", rsgdf.RSGDF_FP64), ("mixed", rsgdf.RSGDF_MIXED)):
+        try:
+            o = dict(opt, precision=prec)
+            r = {"plain_ms": ev(lambda: out.update(plain=rsgdf.rsgdf_j3c(p.a, p.kmesh, p.ao, p.aux, kp, **o))),
+                 "split_ms": ev(lambda: out.update(split=cdsplit.j3c_split(p.a, p.kmesh, p.ao, p.aux, kp,
+                                                                             alpha_cut=ac, **o)))}
+            r["speedup"] = r["plain_ms"] / r["split_ms"]
+            r["max_abs_split_vs_plain"] = (out["split"] - out["plain"]).abs().max().item()
+            res[name] = r
+        except Exception as e:   # recorded per precision
+            res[name] = {"error": repr(e)[:300]}
+        out.clear()
     return res
 
 
