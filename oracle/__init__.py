@@ -94,6 +94,8 @@ def lib():
             _lib.or_count_nf_cells.restype = C.c_int
             _lib.or_num_threads.restype = C.c_int
             _lib.or_set_num_threads.argtypes = [C.c_int]
+            _lib.or_flops_end.argtypes = [C.c_void_p]
+            _lib.or_flops_ncat.restype = C.c_int
         return _lib
 
 
@@ -274,3 +276,48 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     lib().or_set_num_threads(int(n))
+
+
+# Categories of the instrumented operation counter (rsgdf_oracle.c, in its order).
+FLOP_CATEGORIES = ("sep_T", "boys_calls", "boys_orders", "combine", "seed", "hermite", "per_combination")
+# Counting convention for one Boys evaluation of orders 0..m: the tabulated
+# Taylor scheme -- F_m(T) and e^{-T} each from a degree-6 polynomial about the
+# nearest grid point (6 fused multiply-adds, 12 flops), then m downward steps
+# F_n = (2T F_{n+1} + e^{-T})/(2n+1) (one FMA and one multiply, 3 flops).
+BOYS_BASE_FLOPS = 24
+BOYS_STEP_FLOPS = 3
+
+
+def sr_term_op_counts(lc, la, lb, omega=0.4, T=2.0):
+    """Operation counts of one SR (erfc-kernel) primitive integral of class
+    (lc | la lb), tallied by the instrumented oracle while it evaluates the
+    integral (Eq. VPmunu_SR; the auxiliary function G_n and the Hermite
+    integrals R_tuv of the McMurchie-Davidson scheme).  Returns a dict over
+    FLOP_CATEGORIES.  The centres are placed so that the separation gives the
+    requested T at unit exponents; the counts do not depend on it."""
+    lib()
+    g, a, b = 1.0, 1.0, 1.0
+    p = a + b
+    alpha = p * g / (p + g)
+    r = (float(T) / alpha) ** 0.5
+    A = np.zeros(3)
+    B = np.zeros(3)
+    Cc = np.array([r, 0.0, 0.0])
+    out = np.zeros(len(FLOP_CATEGORIES), dtype=np.int64)
+    assert int(_lib.or_flops_ncat()) == len(FLOP_CATEGORIES)
+    _lib.or_flops_begin()
+    try:
+        prim3c(KERNEL_ERFC, float(omega), lc, g, Cc, la, a, A, lb, b, B)
+    finally:
+        _lib.or_flops_end(_p(out))
+    return dict(zip(FLOP_CATEGORIES, (int(x) for x in out)))
+
+
+def sr_term_flops(lc, la, lb):
+    """FP64 flops of the part of one SR primitive term that depends on its
+    lattice translation: separation and T, two Boys evaluations (counted by
+    the convention above), the erfc combination, the Hermite seeds and
+    recursion.  Per-combination constants are excluded."""
+    c = sr_term_op_counts(lc, la, lb)
+    boys = BOYS_BASE_FLOPS * c["boys_calls"] + BOYS_STEP_FLOPS * c["boys_orders"]
+    return c["sep_T"] + boys + c["combine"] + c["seed"] + c["hermite"]

@@ -48,6 +48,46 @@
 
 static const double OR_PI = 3.14159265358979323846264338327950288;
 
+/* ------------------------------------------------------------------ */
+/* Instrumented operation counter                                      */
+/* ------------------------------------------------------------------ */
+
+/* When switched on for a thread (or_flops_begin), the FP64 operations of one
+ * SR primitive integral are tallied by category as the code below performs
+ * them.  The categories separate what depends on the lattice translation of
+ * a term (the separation and T, the erfc auxiliary function G_n, the Hermite
+ * seeds and recursion) from what depends only on the primitive combination
+ * (s, sqrt s, the (-2 alpha)^n factors).  Boys evaluations are counted as
+ * calls with their highest order: the series used here is written for
+ * clarity, not economy, so its own operation count is not the method's. */
+enum {
+    OR_FL_SEP_T,      /* P - C - l and T = alpha |P - C - l|^2 */
+    OR_FL_BOYS_CALL,  /* Boys evaluations (calls) */
+    OR_FL_BOYS_ORD,   /* sum over calls of the highest order requested */
+    OR_FL_COMBINE,    /* s T and G_n = F_n(T) - s^{n+1/2} F_n(sT), n = 0..L */
+    OR_FL_SEED,       /* R^n_000 = (-2 alpha)^n G_n */
+    OR_FL_HERMITE,    /* R^n_{tuv} recursion */
+    OR_FL_COMBO,      /* per primitive combination: s, sqrt s, (-2 alpha)^n */
+    OR_FL_N
+};
+static _Thread_local long long or_fl[OR_FL_N];
+static _Thread_local int or_fl_on;
+#define OR_FL(k, n) do { if (or_fl_on) or_fl[k] += (n); } while (0)
+
+void or_flops_begin(void)
+{
+    memset(or_fl, 0, sizeof(or_fl));
+    or_fl_on = 1;
+}
+
+void or_flops_end(long long *out /* [OR_FL_N] */)
+{
+    or_fl_on = 0;
+    for (int k = 0; k < OR_FL_N; k++) out[k] = or_fl[k];
+}
+
+int or_flops_ncat(void) { return OR_FL_N; }
+
 typedef struct {
     int nshell;
     const int *l;         /* [nshell] angular momentum */
@@ -70,6 +110,8 @@ typedef struct {
  * for m < T. */
 void or_boys(int mmax, double T, double *F)
 {
+    OR_FL(OR_FL_BOYS_CALL, 1);
+    OR_FL(OR_FL_BOYS_ORD, mmax);
     if (T < 30.0) {
         double eT = exp(-T);
         for (int m = 0; m <= mmax; m++) {
@@ -101,13 +143,16 @@ static void kernel_G(int kernel, double omega, int L, double alpha, double T, do
         return;
     }
     double s = omega * omega / (omega * omega + alpha);
+    OR_FL(OR_FL_COMBO, 4);
     or_boys(L, s * T, Fs);
+    OR_FL(OR_FL_COMBINE, 1);
     double sp = sqrt(s);
+    OR_FL(OR_FL_COMBO, 1);
     if (kernel == 1) {
         for (int n = 0; n <= L; n++) { G[n] = sp * Fs[n]; sp *= s; }
     } else {
         or_boys(L, T, F);
-        for (int n = 0; n <= L; n++) { G[n] = F[n] - sp * Fs[n]; sp *= s; }
+        for (int n = 0; n <= L; n++) { G[n] = F[n] - sp * Fs[n]; sp *= s; OR_FL(OR_FL_COMBINE, 3); }
     }
 }
 
@@ -218,7 +263,12 @@ static void herm_R(int L, double alpha, double X, double Y, double Z, const doub
     double *W = (double *)malloc(sizeof(double) * D * D * D * D);
 #define RI(n, t, u, v) W[(((n) * D + (t)) * D + (u)) * D + (v)]
     double f = 1.0;
-    for (int n = 0; n <= L; n++) { RI(n, 0, 0, 0) = f * G[n]; f *= -2.0 * alpha; }
+    for (int n = 0; n <= L; n++) {
+        RI(n, 0, 0, 0) = f * G[n];
+        f *= -2.0 * alpha;
+        OR_FL(OR_FL_SEED, 1);
+        OR_FL(OR_FL_COMBO, 2);
+    }
     for (int s = 1; s <= L; s++)
         for (int t = 0; t <= s; t++)
             for (int u = 0; u <= s - t; u++) {
@@ -227,13 +277,16 @@ static void herm_R(int L, double alpha, double X, double Y, double Z, const doub
                     double r;
                     if (t > 0) {
                         r = X * RI(n + 1, t - 1, u, v);
-                        if (t > 1) r += (t - 1) * RI(n + 1, t - 2, u, v);
+                        OR_FL(OR_FL_HERMITE, 1);
+                        if (t > 1) { r += (t - 1) * RI(n + 1, t - 2, u, v); OR_FL(OR_FL_HERMITE, 2); }
                     } else if (u > 0) {
                         r = Y * RI(n + 1, t, u - 1, v);
-                        if (u > 1) r += (u - 1) * RI(n + 1, t, u - 2, v);
+                        OR_FL(OR_FL_HERMITE, 1);
+                        if (u > 1) { r += (u - 1) * RI(n + 1, t, u - 2, v); OR_FL(OR_FL_HERMITE, 2); }
                     } else {
                         r = Z * RI(n + 1, t, u, v - 1);
-                        if (v > 1) r += (v - 1) * RI(n + 1, t, u, v - 2);
+                        OR_FL(OR_FL_HERMITE, 1);
+                        if (v > 1) { r += (v - 1) * RI(n + 1, t, u, v - 2); OR_FL(OR_FL_HERMITE, 2); }
                     }
                     RI(n, t, u, v) = r;
                 }
@@ -266,6 +319,7 @@ void or_prim3c(int kernel, double omega, int lc, double g, const double *C,
     double alpha = p * g / (p + g);
     double X = Pc[0] - C[0], Y = Pc[1] - C[1], Z = Pc[2] - C[2];
     double T = alpha * (X * X + Y * Y + Z * Z);
+    OR_FL(OR_FL_SEP_T, 9);
     double G[OR_LTOT + 2];
     kernel_G(kernel, omega, L, alpha, T, G);
     double *R = (double *)malloc(sizeof(double) * D * D * D);

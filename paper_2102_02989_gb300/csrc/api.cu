@@ -1830,6 +1830,7 @@ int rsgdf_last_stats(rsgdf_stats *out)
         if (cudaStreamSynchronize(t_stats_stream) != cudaSuccess) return fail(RSGDF_EDEVICE, "stream sync failed");
         t_stats.sr_terms = 0;
         t_stats.sr_flops = 0;
+        t_stats.sr_prim_terms = 0;
         for (int L = 0; L <= LTOT_MAX; L++) {
             t_stats.sr_terms += (long long)t_count_host[L];
             // the Hermite work is done per primitive combination of a term
@@ -1840,7 +1841,10 @@ int rsgdf_last_stats(rsgdf_stats *out)
         t_stats.sr_items_pruned = (long long)t_count_host[2 * LTOT_MAX + 4];
         double ms[PH_N];
         t_timer.totals(ms, t_stats.sr_ms_by_L);
-        for (int L = 0; L <= LTOT_MAX; L++) t_stats.sr_terms_by_L[L] = (long long)t_count_host[L];
+        for (int L = 0; L <= LTOT_MAX; L++) {
+            t_stats.sr_terms_by_L[L] = (long long)t_count_host[L];
+            t_stats.sr_prim_terms_by_L[L] = (long long)t_count_host[LTOT_MAX + 2 + L];
+        }
         t_stats.sr_ms = ms[PH_SR];
         t_stats.aft_ms = ms[PH_AFT];
         t_stats.lr_gemm_ms = ms[PH_GEMM];
