@@ -167,31 +167,31 @@ def df_oracle_sample(J, V, D, kp, kmesh, ao_l, aux_l):
 # every angular-momentum class of the workload, half of its aux functions) x
 # every k pair, SR + G0 + LR.  The one-core figure uses one shell per class.
 ORACLE_SHELLS = (0, 16)
-ORACLE_SHELLS_1CORE = "one aux shell per class: the first s, p, d and f shell of the first atom"
+ORACLE_SHELL_1CORE = 10   # the first atom's p shell of exponent 0.8, the middle of its p shells
 
 
 def oracle_1core_sample(p, omega, gmesh):
-    """The oracle on one host core: one aux shell of each angular momentum of
-    the first atom (its first s, p, d, f shells), every k pair."""
+    """The oracle on one host core: one aux shell (ORACLE_SHELL_1CORE, a
+    p shell from the middle of the exponent range; one shell already takes
+    about 20 s on one core, most of it the reciprocal-space part over 64
+    k pairs), every k pair."""
     import oracle
     oracle.build()
-    l = [int(x) for x in p.aux.l[ORACLE_SHELLS[0]:ORACLE_SHELLS[1]]]
-    picks = [ORACLE_SHELLS[0] + l.index(lv) for lv in (0, 1, 2, 3)]
+    s = ORACLE_SHELL_1CORE
     kp = [(i, j) for i in range(p.nk) for j in range(p.nk)]
     nth = oracle.num_threads()
     oracle.set_num_threads(1)
     try:
-        terms, dt = 0, 0.0
-        for s in picks:
-            t0 = time.perf_counter()
-            _, cnt = oracle.j3c(p.a, p.kmesh, p.ao, p.aux, omega, kp, eps_sr=p.eps_sr, eps_lr=p.eps_lr,
-                                gmesh=gmesh, shells=(s, s + 1), return_counts=True)
-            dt += time.perf_counter() - t0
-            terms += cnt["terms"]
+        t0 = time.perf_counter()
+        _, cnt = oracle.j3c(p.a, p.kmesh, p.ao, p.aux, omega, kp, eps_sr=p.eps_sr, eps_lr=p.eps_lr,
+                            gmesh=gmesh, shells=(s, s + 1), return_counts=True)
+        dt = time.perf_counter() - t0
     finally:
         oracle.set_num_threads(nth)
-    return {"value": terms / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt, "terms": int(terms),
-            "sample": ORACLE_SHELLS_1CORE + " (aux shells %s) x all %d k pairs, SR+G0+LR" % (picks, p.nk * p.nk)}
+    return {"value": cnt["terms"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
+            "terms": int(cnt["terms"]),
+            "sample": "aux shell %d (l=%d, exponent %g) x all %d k pairs, SR+G0+LR"
+                      % (s, int(p.aux.l[s]), float(p.aux.exps[p.aux.prim_off[s]]), p.nk * p.nk)}
 
 
 def run_reference(args, rank, world):

@@ -317,6 +317,25 @@ int rsgdf_last_stats(rsgdf_stats *out);
  * RSGDF_OK otherwise.  Clears the flag. */
 int rsgdf_sync_status(void *stream);
 
+/* Device scratch budget (no counterpart in the paper): the largest number of
+ * bytes of stream-ordered scratch one call may hold at a time; 0 (the
+ * default) means no limit.  A call whose scratch would exceed it returns
+ * RSGDF_ENOMEM, exactly as when the device allocator fails; work it had
+ * already enqueued still runs, and its outputs are then unspecified.  The
+ * batch handle's own buffers and the caller's outputs do not count.
+ * Process-wide; returns RSGDF_EINVAL for a negative value. */
+int rsgdf_set_scratch_limit(long long bytes);
+
+/* Self-test of the bounded device wait and of its error report (no
+ * counterpart in the paper): enqueues one CTA on `stream` that waits, with
+ * the same bounded poll the tensor-core contraction uses (at most `limit`
+ * polls, >= 1), on a barrier that expects one arrival.  arrive != 0: the CTA
+ * arrives first and the wait completes, so rsgdf_sync_status then returns
+ * RSGDF_OK; arrive == 0: nothing arrives, the wait gives up, the kernel
+ * returns and the next rsgdf_sync_status returns RSGDF_ETIMEOUT.  The device
+ * stays usable either way. */
+int rsgdf_selftest_wait(int arrive, long long limit, void *stream);
+
 /* Range-separation parameter and G box implied by opts (host only). */
 int rsgdf_params(const rsgdf_cell *cell, const rsgdf_opts *opts, double *omega_out, int *gmesh_out);
 

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <atomic>
 #include <mutex>
 #include <set>
 #include <string>
@@ -98,9 +99,14 @@ static int fail(int code, const std::string &msg)
     } while (0)
 
 // Stream-ordered device scratch released on scope exit.
+// Largest device scratch one call may hold (bytes; 0 = no limit), set by
+// rsgdf_set_scratch_limit.
+static std::atomic<long long> g_scratch_limit{0};
+
 struct Scratch {
     cudaStream_t st;
     std::vector<void *> ptrs;
+    size_t held = 0;
     explicit Scratch(cudaStream_t s) : st(s) {}
     ~Scratch()
     {
@@ -111,12 +117,17 @@ struct Scratch {
     {
         p = nullptr;
         if (n == 0) n = 1;
+        const long long lim = g_scratch_limit.load();
+        if (lim > 0 && held + n * sizeof(T) > (size_t)lim)
+            return fail(RSGDF_ENOMEM, "device scratch of " + std::to_string(held + n * sizeof(T)) +
+                                          " bytes would exceed the limit of " + std::to_string(lim) + " bytes");
         void *q = nullptr;
         if (cudaMallocAsync(&q, n * sizeof(T), st) != cudaSuccess) {
             cudaGetLastError();
             return fail(RSGDF_ENOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
         }
         ptrs.push_back(q);
+        held += n * sizeof(T);
         p = (T *)q;
         return RSGDF_OK;
     }
@@ -1144,6 +1155,52 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
 }
 
 // ---------------------------------------------------------------------------
+// k-phase contraction pieces shared by rsgdf_kphase and rsgdf_kphase_noalloc:
+// argument checks, the grouping of the k pairs by k12, and the launches.
+// ---------------------------------------------------------------------------
+static int kphase_check(const rsgdf_cell *cell, const double *X, long long m, int npair, const int *kpairs,
+                        const double *V_out, Lattice &L)
+{
+    RC(make_lattice(cell, L, t_err));
+    if (!X || !V_out || m < 1) return fail(RSGDF_EINVAL, "X, V_out and m >= 1 are required");
+    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
+    for (int i = 0; i < 2 * npair; i++)
+        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    return RSGDF_OK;
+}
+
+struct KphaseGroups {
+    std::vector<int> plist, pk2, goff, gkey;   // pairs grouped by k12; group gi = plist[goff[gi], goff[gi+1])
+};
+
+static void kphase_groups(const Lattice &L, int npair, const int *kpairs, KphaseGroups &g)
+{
+    std::map<int, std::vector<int>> groups;
+    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
+    for (auto &kv : groups) {
+        g.goff.push_back((int)g.plist.size());
+        g.gkey.push_back(kv.first);
+        for (int p : kv.second) {
+            g.plist.push_back(p);
+            g.pk2.push_back(kpairs[2 * p + 1]);
+        }
+    }
+    g.goff.push_back((int)g.plist.size());
+}
+
+static int kphase_launch(const double *X, long long m, int Nk, const KphaseGroups &g, const double *dph,
+                         const int *dplist, const int *dpk2, double *T, double *V_out, cudaStream_t st)
+{
+    for (size_t gi = 0; gi < g.gkey.size(); gi++) {
+        RC(launch_phase1(X, m, Nk, Nk, g.gkey[gi], dph, T, 0, st));
+        RC(launch_phase2(T, m, Nk, dplist + g.goff[gi], dpk2 + g.goff[gi], g.goff[gi + 1] - g.goff[gi], dph, V_out,
+                         0, st));
+    }
+    CU(cudaGetLastError());
+    return RSGDF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free k-phase contraction.  Its scratch is one file-scope device
 // array; the host-side name of that array is only a stand-in, so the device
 // address is looked up once per device with cudaGetSymbolAddress.
@@ -1175,11 +1232,7 @@ static int kphase_noalloc_impl(const rsgdf_cell *cell, const double *X, long lon
 {
     t_err.clear();
     Lattice L;
-    RC(make_lattice(cell, L, t_err));
-    if (!X || !V_out || m < 1) return fail(RSGDF_EINVAL, "X, V_out and m >= 1 are required");
-    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
-    for (int i = 0; i < 2 * npair; i++)
-        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    RC(kphase_check(cell, X, m, npair, kpairs, V_out, L));
     const int Nk = L.Nk;
     const size_t b_ph = align256(sizeof(double) * 2 * (size_t)Nk * Nk);
     const size_t b_pl = align256(sizeof(int) * (size_t)npair);
@@ -1199,28 +1252,13 @@ static int kphase_noalloc_impl(const rsgdf_cell *cell, const double *X, long lon
     double *T = (double *)(b + b_ph + 2 * b_pl);
     std::vector<double> ph;
     phase_table(L, ph);
-    std::map<int, std::vector<int>> groups;
-    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
-    std::vector<int> plist, pk2, goff, gkey;
-    for (auto &kv : groups) {
-        goff.push_back((int)plist.size());
-        gkey.push_back(kv.first);
-        for (int p : kv.second) {
-            plist.push_back(p);
-            pk2.push_back(kpairs[2 * p + 1]);
-        }
-    }
-    goff.push_back((int)plist.size());
+    KphaseGroups g;
+    kphase_groups(L, npair, kpairs, g);
     // pageable sources: each copy has consumed its host buffer when it returns
     CU(cudaMemcpyAsync(dph, ph.data(), sizeof(double) * ph.size(), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(dplist, plist.data(), sizeof(int) * plist.size(), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(dpk2, pk2.data(), sizeof(int) * pk2.size(), cudaMemcpyHostToDevice, st));
-    for (size_t gi = 0; gi < gkey.size(); gi++) {
-        RC(launch_phase1(X, m, Nk, Nk, gkey[gi], dph, T, 0, st));
-        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V_out, 0, st));
-    }
-    CU(cudaGetLastError());
-    return RSGDF_OK;
+    CU(cudaMemcpyAsync(dplist, g.plist.data(), sizeof(int) * g.plist.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dpk2, g.pk2.data(), sizeof(int) * g.pk2.size(), cudaMemcpyHostToDevice, st));
+    return kphase_launch(X, m, Nk, g, dph, dplist, dpk2, T, V_out, st);
 }
 
 }  // namespace rsgdf
@@ -1572,11 +1610,7 @@ int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair
 {
     t_err.clear();
     Lattice L;
-    RC(make_lattice(cell, L, t_err));
-    if (!X || !V_out || m < 1) return fail(RSGDF_EINVAL, "X, V_out and m >= 1 are required");
-    if (npair < 1 || !kpairs) return fail(RSGDF_EINVAL, "need at least one k pair");
-    for (int i = 0; i < 2 * npair; i++)
-        if (kpairs[i] < 0 || kpairs[i] >= L.Nk) return fail(RSGDF_EINVAL, "k index outside the mesh");
+    RC(kphase_check(cell, X, m, npair, kpairs, V_out, L));
     RC(check_device());
     cudaStream_t st = (cudaStream_t)stream;
     Scratch S(st);
@@ -1585,29 +1619,14 @@ int rsgdf_kphase(const rsgdf_cell *cell, const double *X, long long m, int npair
     phase_table(L, ph);
     double *dph;
     RC(S.upload(dph, ph));
-    std::map<int, std::vector<int>> groups;
-    for (int p = 0; p < npair; p++) groups[k12_of(L, kpairs[2 * p], kpairs[2 * p + 1])].push_back(p);
-    std::vector<int> plist, pk2, goff, gkey;
-    for (auto &kv : groups) {
-        goff.push_back((int)plist.size());
-        gkey.push_back(kv.first);
-        for (int p : kv.second) {
-            plist.push_back(p);
-            pk2.push_back(kpairs[2 * p + 1]);
-        }
-    }
-    goff.push_back((int)plist.size());
+    KphaseGroups g;
+    kphase_groups(L, npair, kpairs, g);
     int *dplist, *dpk2;
-    RC(S.upload(dplist, plist));
-    RC(S.upload(dpk2, pk2));
+    RC(S.upload(dplist, g.plist));
+    RC(S.upload(dpk2, g.pk2));
     double *T;
     RC(S.alloc(T, (size_t)2 * Nk * m));
-    for (size_t gi = 0; gi < gkey.size(); gi++) {
-        RC(launch_phase1(X, m, Nk, Nk, gkey[gi], dph, T, 0, st));
-        RC(launch_phase2(T, m, Nk, dplist + goff[gi], dpk2 + goff[gi], goff[gi + 1] - goff[gi], dph, V_out, 0, st));
-    }
-    CU(cudaGetLastError());
-    return RSGDF_OK;
+    return kphase_launch(X, m, Nk, g, dph, dplist, dpk2, T, V_out, st);
 }
 
 int rsgdf_kphase_noalloc(const rsgdf_cell *cell, const double *X, long long m, int npair, const int *kpairs,
@@ -1852,6 +1871,22 @@ int rsgdf_last_stats(rsgdf_stats *out)
         t_stats.other_ms = ms[PH_OTHER];
     }
     *out = t_stats;
+    return RSGDF_OK;
+}
+
+int rsgdf_set_scratch_limit(long long bytes)
+{
+    if (bytes < 0) return fail(RSGDF_EINVAL, "the scratch limit must be >= 0 (0: no limit)");
+    g_scratch_limit.store(bytes);
+    return RSGDF_OK;
+}
+
+int rsgdf_selftest_wait(int arrive, long long limit, void *stream)
+{
+    t_err.clear();
+    if (limit < 1) return fail(RSGDF_EINVAL, "limit must be >= 1");
+    RC(check_device());
+    RC(launch_wait_selftest(arrive, limit, (cudaStream_t)stream));
     return RSGDF_OK;
 }
 

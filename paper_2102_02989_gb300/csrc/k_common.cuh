@@ -197,6 +197,7 @@ int launch_zgemm_tc2(int M, int N, int K, int batch, const float *Ap, const floa
 long long tc_b_floats(int N, int K, int batch);
 long long tc_a_floats(int M, int K);
 int tc_status_take(int *flag);
+int launch_wait_selftest(int arrive, long long limit, cudaStream_t st);
 // ph: double2 table for the FP64 path, float2 table when fp32 != 0
 constexpr int DFT_NMAX_HOST = 16;   // longest mesh axis of the DFT path
 int launch_dft_mesh(double *T, const int nk[3], long long slab, long long nrep, const double *tw, int conj,

@@ -284,11 +284,11 @@ int launch_split_a(int M, int K, const double *A, float *Ap, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, int parity)
+__device__ __forceinline__ bool mbar_wait_n(uint32_t mb, int parity, long long limit)
 {
     uint32_t done = 0;
     long long it = 0;
-    while (!done && it < TC_SPIN) {
+    while (!done && it < limit) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done)
@@ -296,6 +296,32 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, int parity)
         it++;
     }
     return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, int parity) { return mbar_wait_n(mb, parity, TC_SPIN); }
+
+// Self-test of the bounded wait and of its error report: one CTA waits on an
+// mbarrier that expects one arrival.  With arrive != 0 thread 0 arrives
+// first and the wait completes; with arrive == 0 nothing ever arrives, every
+// thread gives up after `limit` polls and the kernel records the timeout in
+// g_tc_status exactly as the tensor-core contraction does, then returns.
+__global__ void k_wait_selftest(int arrive, long long limit)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1));
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb));
+    const bool ok = mbar_wait_n(mb, 0, limit);
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
+    if (!all_ok && threadIdx.x == 0) atomicExch(&g_tc_status, 1);
+}
+
+int launch_wait_selftest(int arrive, long long limit, cudaStream_t st)
+{
+    if (limit < 1) return RSGDF_EINVAL;
+    k_wait_selftest<<<1, 64, 0, st>>>(arrive, limit);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb)

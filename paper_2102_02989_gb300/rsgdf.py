@@ -34,7 +34,8 @@ EXPORTS = ("rsgdf_j2c", "rsgdf_j3c_sr", "rsgdf_j3c_lr", "rsgdf_j3c", "rsgdf_kpha
            "rsgdf_sr_items", "rsgdf_j3c_batch_create", "rsgdf_j3c_batch_run", "rsgdf_j3c_batch_destroy",
            "rsgdf_j3c_batch_tiles", "rsgdf_j3c_batch", "rsgdf_df_metric", "rsgdf_df_fit", "rsgdf_df_jk", "rsgdf_df_rho",
            "rsgdf_sph_coefficients", "rsgdf_sph_nfunc", "rsgdf_cart2sph_j3c", "rsgdf_cart2sph_j2c",
-           "rsgdf_split_basis", "rsgdf_sr_items_split", "rsgdf_split_combine")
+           "rsgdf_split_basis", "rsgdf_sr_items_split", "rsgdf_split_combine", "rsgdf_set_scratch_limit",
+           "rsgdf_selftest_wait")
 RSGDF_MLP_NFEAT = 10
 
 
@@ -112,6 +113,8 @@ def load():
         lib.rsgdf_last_error.restype = C.c_char_p
         lib.rsgdf_probe_fp64.argtypes = [vp, vp]
         lib.rsgdf_sync_status.argtypes = [vp]
+        lib.rsgdf_set_scratch_limit.argtypes = [C.c_longlong]
+        lib.rsgdf_selftest_wait.argtypes = [i, C.c_longlong, vp]
         lib.rsgdf_mlp_nparams.argtypes = [i]
         lib.rsgdf_mlp_create.argtypes = [i, vp, vp, vp, vp]
         lib.rsgdf_mlp_destroy.argtypes = [vp]
@@ -468,6 +471,16 @@ def rsgdf_last_stats() -> dict:
 def rsgdf_sync_status(stream=None) -> None:
     """Synchronise the stream; raise RsgdfError(RSGDF_ETIMEOUT) if a bounded device wait gave up."""
     _check(load().rsgdf_sync_status(_stream_ptr(stream)))
+
+
+def rsgdf_set_scratch_limit(nbytes: int) -> None:
+    """Largest device scratch (bytes) one call may hold; 0 = no limit."""
+    _check(load().rsgdf_set_scratch_limit(int(nbytes)))
+
+
+def rsgdf_selftest_wait(arrive: bool, limit: int, stream=None) -> None:
+    """Enqueue the bounded-wait self-test; read its outcome with rsgdf_sync_status."""
+    _check(load().rsgdf_selftest_wait(1 if arrive else 0, int(limit), _stream_ptr(stream)))
 
 
 def rsgdf_last_error() -> str:

@@ -190,3 +190,11 @@ def test_split_options_rejected_without_device(rs, bad):
     rc = getattr(lib, name)(C.byref(c), ra.ref(), rx.ref(), C.byref(o), 1, kpa.ctypes.data_as(C.c_void_p), 0,
                             len(rx.l), C.c_void_p(16))
     assert rc == rs.RSGDF_EINVAL, (bad, rc, rs.rsgdf_last_error())
+
+
+def test_error_control_arguments_without_device(rs):
+    lib = rs.load()
+    assert lib.rsgdf_set_scratch_limit(-1) == rs.RSGDF_EINVAL
+    assert lib.rsgdf_set_scratch_limit(0) == rs.RSGDF_OK
+    assert lib.rsgdf_selftest_wait(0, 0, None) == rs.RSGDF_EINVAL
+    assert "limit" in rs.rsgdf_last_error()
