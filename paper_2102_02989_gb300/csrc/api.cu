@@ -331,6 +331,18 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     RC(S.upload(dpoff, plan.pair_doff));
     RC(S.upload(R.ddl, plan.dlist));
     RC(S.upload(dsph, plan.sph));
+    // Cartesian vectors of the lattice list, FP64 and FP32
+    std::vector<double> sphv(plan.sph.size());
+    std::vector<float> sphvf(plan.sph.size());
+    for (size_t i = 0; i + 2 < plan.sph.size(); i += 3)
+        for (int x = 0; x < 3; x++) {
+            sphv[i + x] = plan.sph[i] * L.a[0][x] + plan.sph[i + 1] * L.a[1][x] + plan.sph[i + 2] * L.a[2][x];
+            sphvf[i + x] = (float)sphv[i + x];
+        }
+    double *dsphv;
+    float *dsphvf;
+    RC(S.upload(dsphv, sphv));
+    RC(S.upload(dsphvf, sphvf));
     // Hermite tables of every (pair, d, primitive pair) of the SR d lists,
     // shared by all aux shells (entries of one d contiguous, ij order)
     const int npairs = hao.nshell * hao.nshell;
@@ -379,6 +391,8 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.pair_doff = dpoff;
     A.dlist = R.ddl;
     A.sph = dsph;
+    A.sphv = dsphv;
+    A.sphvf = dsphvf;
     fill_lattice(L, A.a, A.bq, A.nk);
     A.Nk = L.Nk;
     A.omega = omega;
@@ -411,10 +425,11 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     for (int c = 0; c <= LTOT_MAX; c++) {
         int b = plan.class_tri_begin[c], e = plan.class_tri_begin[c + 1];
         if (b >= e) continue;
-        int ncmax = 0, wmax = 0, lmax_list = 0;
+        int ncmax = 0, wmax = 0, lmax_list = 0, cmax = 1;
         for (int i = b; i < e; i++) {
             const SRTriple &t = plan.tri[i];
             const int lP = hax.l[t.P], lm = hao.l[t.mu], ln = hao.l[t.nu];
+            cmax = std::max(cmax, hax.nprim[t.P] * hao.nprim[t.mu] * hao.nprim[t.nu]);
             ncmax = std::max(ncmax, ncart(lP) * ncart(lm) * ncart(ln));
             if (lP > 0) wmax = std::max(wmax, ncart(lP) * ntuv(lm + ln));
             // coefficient-list length: sum over (a, b) of (ax+bx+1)(ay+by+1)(az+bz+1)
@@ -439,6 +454,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
         Ac.ncomp_max = ncmax;
         Ac.w_max = wmax;
         Ac.list_max = lmax_list;
+        Ac.combo_max = cmax;
         R.cls.push_back(Ac);
         R.cls_L.push_back(c);
     }
@@ -476,7 +492,7 @@ struct SRClassLaunch {
     std::vector<long long> cum;
     SRArgs *ddesc = nullptr;
     long long *dcum = nullptr;
-    int ncmax = 0, wmax = 0, lmax = 0;
+    int ncmax = 0, wmax = 0, lmax = 0, cmax = 1;
     int nkmax = 1;   // largest k mesh among the descriptors (bin chunks beyond it are useless)
     int bc = 1;
     size_t warp_bytes = 0;
@@ -489,16 +505,17 @@ static int g_num_sms = 0;
 static int sr_set_bc(SRClassLaunch &c, int bc, cudaStream_t st)
 {
     c.bc = bc;
-    c.warp_bytes = sr_warp_bytes(c.L, bc, c.ncmax, c.wmax, c.lmax);
+    c.warp_bytes = sr_warp_bytes(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax);
     for (SRArgs &a : c.desc) {
         a.bc = bc;
         a.warp_bytes = (int)c.warp_bytes;
         a.ncomp_max = c.ncmax;
         a.w_max = c.wmax;
         a.list_max = c.lmax;
+        a.combo_max = c.cmax;
     }
     CU(cudaMemcpyAsync(c.ddesc, c.desc.data(), sizeof(SRArgs) * c.desc.size(), cudaMemcpyHostToDevice, st));
-    const int occ = sr_occupancy(c.L, sr_launch_smem(c.L, bc, c.ncmax, c.wmax, c.lmax));
+    const int occ = sr_occupancy(c.L, sr_launch_smem(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax));
     if (occ < 1) return fail(RSGDF_EDEVICE, "SR kernel does not fit on an SM");
     if (!g_num_sms) {
         int dev = 0;
@@ -529,6 +546,7 @@ static int sr_merge(const std::vector<const SRSetup *> &rs, Scratch &S, cudaStre
                 c.nkmax = std::max(c.nkmax, a.Nk);
                 c.wmax = std::max(c.wmax, a.w_max);
                 c.lmax = std::max(c.lmax, a.list_max);
+                c.cmax = std::max(c.cmax, a.combo_max);
             }
         }
         if (c.desc.empty()) continue;
@@ -545,8 +563,8 @@ static int sr_run(std::vector<SRClassLaunch> &cl, unsigned long long *dqueue, cu
 {
     for (SRClassLaunch &c : cl) {
         t_timer.begin(PH_SR, c.L);
-        RC(launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes, dqueue + c.L, c.grid,
-                           c.grab, st));
+        RC(launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes, dqueue + c.L,
+                           c.grid, c.grab, st));
         t_timer.end();
         nl++;
     }

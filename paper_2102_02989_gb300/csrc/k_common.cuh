@@ -40,6 +40,8 @@ struct SRArgs {
     long long item_begin, item_end;
     const double *win;
     const int *pair_doff, *dlist, *sph;
+    const double *sphv;               // Cartesian vectors of the lattice list (FP64), [nsph][3]
+    const float *sphvf;               // the same in FP32 (pre-filter)
     double a[9];    // lattice vectors (rows)
     float af[9];    // the same in FP32 (pre-filter of the translations)
     double bq[9];   // b_i / 2 pi: fractional coordinates
@@ -52,6 +54,7 @@ struct SRArgs {
     int bc;
     int warp_bytes;
     int ncomp_max, w_max, list_max;
+    int combo_max;                    // primitive combinations of the largest triple of the launch (<= 64)
     unsigned long long *term_count;   // [LTOT_MAX+2] or NULL
     const double *ec_tab;             // [aux primitive][(LMAX+1)^2] single-centre Hermite coefficients
     const double *ptab;               // pair entries of the SR d list
@@ -86,11 +89,11 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
 // rows (BvK cell x primitive combination) of Hermite sums a warp holds for a bin chunk bc:
 // room for up to 4 combinations at once when the chunk is small
 __host__ __device__ constexpr int sr_rb_rows(int bc) { return 4 * bc < 32 ? 4 * bc : (bc > 32 ? bc : 32); }
-size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max);
-size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max);
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max);
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max);
 int sr_occupancy(int L, size_t smem);
-int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot, size_t warp_bytes,
-                    unsigned long long *queue, int grid, int grab, cudaStream_t st);
+int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot,
+                    size_t warp_bytes, unsigned long long *queue, int grid, int grab, cudaStream_t st);
 __global__ void k_aux_charge(DevShells ax, int s0, int s1, int pfunc0, double *S);
 __host__ __device__ void single_E(int lc, double g, double *E);
 __global__ void k_g0_correct(double *V, const int *kpairs, int npair, int nP, int nao, const double *SP,

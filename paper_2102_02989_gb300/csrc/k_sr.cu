@@ -27,7 +27,7 @@
 
 namespace rsgdf {
 
-__device__ double g_boys_table[BOYS_NT * BOYS_ROW];
+__device__ double g_boys_table[(LTOT_MAX + 1) * BOYS_NT * BOYS_W];
 static bool g_boys_ready[64] = {false};
 
 int upload_boys_table(const double *tab, cudaStream_t st)
@@ -35,7 +35,7 @@ int upload_boys_table(const double *tab, cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RSGDF_EDEVICE;
     if (dev < 64 && g_boys_ready[dev]) return RSGDF_OK;
-    if (cudaMemcpyToSymbolAsync(g_boys_table, tab, sizeof(double) * BOYS_NT * BOYS_ROW, 0,
+    if (cudaMemcpyToSymbolAsync(g_boys_table, tab, sizeof(double) * (LTOT_MAX + 1) * BOYS_NT * BOYS_W, 0,
                                 cudaMemcpyHostToDevice, st) != cudaSuccess)
         return RSGDF_EDEVICE;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSGDF_EDEVICE;
@@ -43,49 +43,61 @@ int upload_boys_table(const double *tab, cudaStream_t st)
     return RSGDF_OK;
 }
 
-// F_m(T), m = 0..L: Taylor series of F_L about the nearest tabulated point,
-// then downward recursion F_m = (2T F_{m+1} + e^{-T})/(2m+1) with e^{-T} =
-// e^{-T_i} e^{T_i - T} (tabulated value times a short Taylor series); for T
-// beyond the table F_0 = sqrt(pi/T)/2 and the upward recursion.
+// T >= 0 truncated to a float from the top word of its FP64 encoding (20 of
+// its mantissa bits, relative error below 1e-6): integer arithmetic only, so
+// the table index costs nothing on the narrow FP64 pipe.  T below 2^-126
+// gives 0.
+__device__ __forceinline__ float top_float(double T)
+{
+    const int hi = __double2hiint(T);
+    return __int_as_float(max(hi - (896 << 20), 0) << 3);
+}
+
+// F_m(T), m = 0..L.  Below BOYS_TMAX: Taylor series about the nearest
+// tabulated point T_i (D = T_i - T, |D| <= h/2 up to the float rounding of
+// the index); classes L <= 1 sum one series per order, classes L >= 2 sum
+// the series of F_L and of e^{-T} = e^{-T_i} e^{D} and recur downward,
+// F_m = (2T F_{m+1} + e^{-T})/(2m+1).  Above it: F_0 = sqrt(pi/T)/2 and the
+// upward recursion without e^{-T} (below 1e-43 there).  The branch and the
+// index use integer and FP32 arithmetic; the FP64 work is one subtraction,
+// the Horner steps and the recursion.
 template <int L>
 __device__ __forceinline__ void boys_f64(double T, double *F)
 {
-    if (T < BOYS_TMAX) {
-        const int i = __double2int_rn(T * (1.0 / BOYS_H));
-        const double D = i * BOYS_H - T;
-        // row[m*BOYS_TAYLOR + k] = F_{m+k}(T_i)/k!, row[BOYS_NM*BOYS_TAYLOR + k] = e^{-T_i}/k!
-        const double *row = g_boys_table + i * BOYS_ROW;
-        if (L <= 2) {
+    const float Tf = top_float(T);
+    if (Tf < (float)BOYS_TMAX) {
+        const int i = min(__float2int_rn(Tf * (float)(1.0 / BOYS_H)), BOYS_NT - 1);
+        const double *row = g_boys_table + ((size_t)L * BOYS_NT + i) * BOYS_W;
+        const double D = row[0] - T;
+        if (L <= 1) {
 #pragma unroll
             for (int m = 0; m <= L; m++) {
-                const double *c = row + m * BOYS_TAYLOR;
+                const double *c = row + 1 + m * BOYS_TAYLOR;
                 double f = c[BOYS_TAYLOR - 1];
 #pragma unroll
                 for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
                 F[m] = f;
             }
         } else {
-            const double *c = row + L * BOYS_TAYLOR;
+            const double *c = row + 1;
             double f = c[BOYS_TAYLOR - 1];
 #pragma unroll
             for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
             F[L] = f;
-            const double *ce = row + BOYS_NM * BOYS_TAYLOR;
+            const double *ce = row + 1 + BOYS_TAYLOR;
             double e = ce[BOYS_TAYLOR - 1];
 #pragma unroll
             for (int k = BOYS_TAYLOR - 2; k >= 0; k--) e = fma(e, D, ce[k]);
-            const double T2 = 2.0 * T;
+            const double T2 = T + T;
 #pragma unroll
             for (int m = L - 1; m >= 0; m--) F[m] = fma(T2, F[m + 1], e) * (1.0 / (2 * m + 1));
         }
     } else {
-        // e^{-T} is below 1e-43 of F_m for T >= 100 and m <= 9
-        const double e = (T < 100.0) ? exp(-T) : 0.0;
         const double rs = rsqrt(T);
         const double it = rs * rs;
         F[0] = 0.5 * sqrt(KPI) * rs;
 #pragma unroll
-        for (int m = 0; m < L; m++) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * it);
+        for (int m = 0; m < L; m++) F[m + 1] = F[m] * ((m + 0.5) * it);
     }
 }
 
@@ -100,12 +112,12 @@ __host__ __device__ constexpr int ridx(int t, int u, int v)
 // level n+1.  sw[n] = s^{n+1/2}, fw[n] = (-2 alpha)^n (per primitive
 // combination), s = omega^2/(omega^2 + alpha).
 template <int L>
-__device__ __forceinline__ void hermite_R(double T, double s, const double *sw, const double *fw, double X, double Y,
+__device__ __forceinline__ void hermite_R(double T, double sT, const double *sw, const double *fw, double X, double Y,
                                           double Z, double *r)
 {
     double F[L + 1], Fs[L + 1];
     boys_f64<L>(T, F);
-    boys_f64<L>(s * T, Fs);
+    boys_f64<L>(sT, Fs);
     r[0] = fw[L] * fma(-sw[L], Fs[L], F[L]);
 #pragma unroll
     for (int n = L - 1; n >= 0; n--) {
@@ -150,23 +162,47 @@ constexpr int SR_WARPS = 2;
 constexpr int SR_NT = 256;   // translations buffered per segment (flush above SR_NT - 64)
 constexpr int SR_MAXCOMBO = 64;
 constexpr int SR_GMAX = 4;   // primitive combinations summed at once in the term loop
-constexpr double SR_SKIP_ST = 70.0;   // erfc terms with s T beyond this vanish   // primitive combinations per triple (aux x AO x AO)
+constexpr int SR_SKIP_ST_HI = 0x40518000;   // top word of 70.0: erfc terms with s T >= 70 vanish
 
-// per-warp shared memory: term positions (3 doubles) and BvK cells, twice
-// (collected and sorted), bin counters, Hermite coefficients of the current
-// primitive combination, Hermite sums per cell and contracted blocks.
-size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max)
+// Per-warp shared memory of the SR kernel, one layout for the host (sizes)
+// and the device (carving); offsets in bytes from the warp's base:
+// translations sorted by BvK cell (positions and cells), the collected
+// translations (index into the lattice list and cell), bin counters,
+// coefficient-list offsets, the FP32 survivor queue, the Hermite
+// coefficients of the current primitive combination, Hermite sums per cell,
+// contracted blocks, coefficient lists, and the per-combination constants.
+struct SRSmem {
+    unsigned sx, sb, tq, tb, cnt, fill, loff, qd, eab, ec, rb, o, wb, lc, li, kc, total;
+};
+__host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
 {
-    size_t b = 2 * SR_NT * (3 * sizeof(double) + sizeof(int)) + 2 * (NBIN_MAX + 4) * sizeof(int);
-    b += (NC_MAX * NC_MAX + 4) * sizeof(int);                      // list offsets per (a, b)
-    b += 64 * sizeof(int);                                        // FP32 survivor queue
-    b = (b + 15) & ~(size_t)15;
-    b += (3 * EAB_SZ + EC_SZ) * sizeof(double);
-    b += ((size_t)sr_rb_rows(bc) * ntuv(L) + (size_t)bc * (ncomp_max + w_max)) * sizeof(double);
-    b += (size_t)list_max * (sizeof(double) + sizeof(short));
-    b = (b + 15) & ~(size_t)15;
-    b += (size_t)SR_MAXCOMBO * 8 * sizeof(double);                    // per-combination constants
-    return (b + 15) & ~(size_t)15;
+    SRSmem s;
+    unsigned b = 0;
+    s.sx = b; b += 3u * SR_NT * 8u;
+    s.sb = b; b += SR_NT * 4u;
+    s.tq = b; b += SR_NT * 4u;
+    s.tb = b; b += SR_NT * 4u;
+    s.cnt = b; b += (NBIN_MAX + 4) * 4u;
+    s.fill = b; b += (NBIN_MAX + 4) * 4u;
+    s.loff = b; b += (NC_MAX * NC_MAX + 4) * 4u;
+    s.qd = b; b += 64u * 4u;
+    b = (b + 15u) & ~15u;
+    s.eab = b; b += 3u * EAB_SZ * 8u;
+    s.ec = b; b += EC_SZ * 8u;
+    s.rb = b; b += (unsigned)(sr_rb_rows(bc) * ntuv(L)) * 8u;
+    s.o = b; b += (unsigned)(bc * ncomp_max) * 8u;
+    s.wb = b; b += (unsigned)(bc * w_max) * 8u;
+    s.lc = b; b += (unsigned)list_max * 8u;
+    s.li = b; b += (unsigned)list_max * 2u;
+    b = (b + 15u) & ~15u;
+    s.kc = b; b += (unsigned)combo_max * 8u * 8u;
+    s.total = (b + 15u) & ~15u;
+    return s;
+}
+
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
+{
+    return sr_smem(L, bc, ncomp_max, w_max, list_max, combo_max).total;
 }
 
 // (t, u, v) of a packed index p = ridx(t, u, v)
@@ -190,25 +226,23 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
 {
     if (A.item_skip && A.item_skip[item]) return;   // pruned by the learned screen (warp-uniform)
     constexpr int NR = ntuv(L);
-    double *Tx = (double *)base;            // collected translations (Cartesian)
-    double *Ty = Tx + SR_NT, *Tz = Ty + SR_NT;
-    double *Sx = Tz + SR_NT, *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
-    int *Tb = (int *)(Sz + SR_NT);
-    int *Sb = Tb + SR_NT;
-    int *cnt = Sb + SR_NT;
-    int *fill = cnt + NBIN_MAX + 4;
-    int *loff = fill + NBIN_MAX + 4;
-    int *Qd = loff + NC_MAX * NC_MAX + 4;
-    double *Eab = (double *)(base + ((2 * SR_NT * (3 * sizeof(double) + sizeof(int)) + 2 * (NBIN_MAX + 4) * sizeof(int) +
-                                      (NC_MAX * NC_MAX + 4) * sizeof(int) + 64 * sizeof(int) + 15) &
-                                     ~(size_t)15));
-    double *Ec = Eab + 3 * EAB_SZ;
-    double *Rb = Ec + EC_SZ;
-    double *O = Rb + sr_rb_rows(A.bc) * NR;
-    double *Wb = O + A.bc * A.ncomp_max;
-    double *Lc = Wb + A.bc * A.w_max;
-    short *Li = (short *)(Lc + A.list_max);
-    double *Kc = (double *)(((uintptr_t)(Li + A.list_max) + 15) & ~(uintptr_t)15);   // [combo][8]
+    const SRSmem sm = sr_smem(L, A.bc, A.ncomp_max, A.w_max, A.list_max, A.combo_max);
+    double *Sx = (double *)(base + sm.sx), *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
+    int *Sb = (int *)(base + sm.sb);
+    int *Tq = (int *)(base + sm.tq);   // collected: index into the lattice list
+    int *Tb = (int *)(base + sm.tb);   // collected: BvK cell
+    int *cnt = (int *)(base + sm.cnt);
+    int *fill = (int *)(base + sm.fill);
+    int *loff = (int *)(base + sm.loff);
+    int *Qd = (int *)(base + sm.qd);
+    double *Eab = (double *)(base + sm.eab);
+    double *Ec = (double *)(base + sm.ec);
+    double *Rb = (double *)(base + sm.rb);
+    double *O = (double *)(base + sm.o);
+    double *Wb = (double *)(base + sm.wb);
+    double *Lc = (double *)(base + sm.lc);
+    short *Li = (short *)(base + sm.li);
+    double *Kc = (double *)(base + sm.kc);   // [combo][8]
 
     // the triple of this item: last triple with item_off <= item
     int lo = A.tri_begin, hi = A.tri_end - 1;
@@ -249,7 +283,13 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const int l00 = __double2int_rn(xr0 * A.bq[0] + xr1 * A.bq[1] + xr2 * A.bq[2]);
     const int l01 = __double2int_rn(xr0 * A.bq[3] + xr1 * A.bq[4] + xr2 * A.bq[5]);
     const int l02 = __double2int_rn(xr0 * A.bq[6] + xr1 * A.bq[7] + xr2 * A.bq[8]);
-    const float fx = (float)xr0, fy = (float)xr1, fz = (float)xr2;
+    // candidate translations l = L0 + (an entry of the length-sorted lattice
+    // list): h = (pair centre - C) - L0 once per item, then h - l' per entry
+    const double L0x = l00 * A.a[0] + l01 * A.a[3] + l02 * A.a[6];
+    const double L0y = l00 * A.a[1] + l01 * A.a[4] + l02 * A.a[7];
+    const double L0z = l00 * A.a[2] + l01 * A.a[5] + l02 * A.a[8];
+    const double hx = xr0 - L0x, hy = xr1 - L0y, hz = xr2 - L0z;
+    const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
     const float fcut = (float)tr.Rc_cut + 1e-3f;
     const int dt = bvk_bin(d0, d1, d2, A.nk);
     const double *win = A.win + tr.win_off;
@@ -289,11 +329,8 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         const int idx = b0 + lane;
         bool pass = false;
         if (idx < tr.nsph) {
-            const int li0 = l00 + A.sph[3 * idx], li1 = l01 + A.sph[3 * idx + 1], li2 = l02 + A.sph[3 * idx + 2];
             // FP32 pre-filter with a margin far above its rounding error
-            const float ex = fx - (li0 * A.af[0] + li1 * A.af[3] + li2 * A.af[6]);
-            const float ey = fy - (li0 * A.af[1] + li1 * A.af[4] + li2 * A.af[7]);
-            const float ez = fz - (li0 * A.af[2] + li1 * A.af[5] + li2 * A.af[8]);
+            const float ex = fx - A.sphvf[3 * idx], ey = fy - A.sphvf[3 * idx + 1], ez = fz - A.sphvf[3 * idx + 2];
             pass = (ex * ex + ey * ey + ez * ez <= fcut * fcut);
         }
         const unsigned pm = __ballot_sync(0xffffffffu, pass);
@@ -306,34 +343,27 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         for (int q0 = 0; q0 < nq; q0 += 32) {
         const int qi = q0 + lane;
         bool acc = false;
-        int li0 = 0, li1 = 0, li2 = 0;
-        double lx = 0.0, ly = 0.0, lz = 0.0;
+        int ci = 0;
         if (qi < nq) {
-            const int ci = Qd[qi];
-            li0 = l00 + A.sph[3 * ci];
-            li1 = l01 + A.sph[3 * ci + 1];
-            li2 = l02 + A.sph[3 * ci + 2];
-            {
-                lx = li0 * A.a[0] + li1 * A.a[3] + li2 * A.a[6];
-                ly = li0 * A.a[1] + li1 * A.a[4] + li2 * A.a[7];
-                lz = li0 * A.a[2] + li1 * A.a[5] + li2 * A.a[8];
-                const double r0 = xr0 - lx, r1 = xr1 - ly, r2 = xr2 - lz;
-                const double rc = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-                if (rc <= tr.Rc_cut) {
-                    int w = (int)floor(rc * (1.0 / SCREEN_DR));
-                    if (w >= tr.nwin) w = tr.nwin - 1;
-                    acc = (R12 <= win[w]);
-                }
+            ci = Qd[qi];
+            const double r0 = hx - A.sphv[3 * ci], r1 = hy - A.sphv[3 * ci + 1], r2 = hz - A.sphv[3 * ci + 2];
+            const double rc2 = r0 * r0 + r1 * r1 + r2 * r2;
+            if (rc2 <= Rc2) {
+                // window floor(Rc / DR) from a float square root; in FP64 only
+                // where the float value lies within 1e-4 of a window boundary
+                const float q = sqrtf(top_float(rc2)) * (float)(1.0 / SCREEN_DR);
+                int w = (int)q;
+                const float fr = q - (float)w;
+                if (fr < 1e-4f || fr > 1.0f - 1e-4f) w = (int)floor(sqrt(rc2) * (1.0 / SCREEN_DR));
+                if (w >= tr.nwin) w = tr.nwin - 1;
+                acc = (R12 <= win[w]);
             }
         }
-        (void)Rc2;
         const unsigned m = __ballot_sync(0xffffffffu, acc);
         if (acc) {
             const int pos = nT + __popc(m & ((1u << lane) - 1u));
-            Tx[pos] = lx;
-            Ty[pos] = ly;
-            Tz[pos] = lz;
-            Tb[pos] = bvk_bin(li0, li1, li2, A.nk);
+            Tq[pos] = ci;
+            Tb[pos] = bvk_bin(l00 + A.sph[3 * ci], l01 + A.sph[3 * ci + 1], l02 + A.sph[3 * ci + 2], A.nk);
         }
         nT += __popc(m);
         }
@@ -359,9 +389,10 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                 if (t < nT) {
                     const int rank = __popc(peers & act & ((1u << lane) - 1u));
                     const int dst = cnt[bin] + fill[bin] + rank;
-                    Sx[dst] = Tx[t];
-                    Sy[dst] = Ty[t];
-                    Sz[dst] = Tz[t];
+                    const int ci = Tq[t];
+                    Sx[dst] = L0x + A.sphv[3 * ci];
+                    Sy[dst] = L0y + A.sphv[3 * ci + 1];
+                    Sz[dst] = L0z + A.sphv[3 * ci + 2];
                     Sb[dst] = bin;
                 }
                 __syncwarp();
@@ -432,10 +463,12 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             const double X = Px - Sx[tt], Y = Py - Sy[tt], Z = Pz - Sz[tt];
                             const double T = alpha * (X * X + Y * Y + Z * Z);
                             // F_n(T) and s^{n+1/2} F_n(sT) share their power-law part; for sT >= 70
-                            // they differ by O(e^{-sT}) < 1e-30: the erfc term vanishes
-                            if (s * T >= SR_SKIP_ST) continue;
+                            // they differ by O(e^{-sT}) < 1e-30: the erfc term vanishes (the test
+                            // compares the top words of the FP64 encodings as integers)
+                            const double sT = s * T;
+                            if (__double2hiint(sT) >= SR_SKIP_ST_HI) continue;
                             double r[NR];
-                            hermite_R<L>(T, s, sw, fw, X, Y, Z, r);
+                            hermite_R<L>(T, sT, sw, fw, X, Y, Z, r);
 #pragma unroll
                             for (int q = 0; q < NR; q++) accR[q] += r[q];
                         }
@@ -549,7 +582,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
 // Descriptors of one launch share bc, ncomp_max, w_max and list_max, so all
 // warps carve shared memory alike.
 template <int L>
-__global__ void __launch_bounds__(SR_WARPS * 32) k_sr3c(const SRArgs *__restrict__ desc, const long long *__restrict__ cum,
+__global__ void __launch_bounds__(SR_WARPS * 32, 1) k_sr3c(const SRArgs *__restrict__ desc, const long long *__restrict__ cum,
                                                         int ndesc, int warp_bytes, unsigned long long *queue, int grab)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -589,35 +622,37 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max)
     return bc > nk_max ? (nk_max < 1 ? 1 : nk_max) : bc;
 }
 
-size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max)
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
 {
-    return sr_warp_bytes(L, bc, ncomp_max, w_max, list_max) * SR_WARPS;
+    return sr_warp_bytes(L, bc, ncomp_max, w_max, list_max, combo_max) * SR_WARPS;
 }
 
 // Resident CTAs per SM of the class-L kernel with the given dynamic shared memory.
 int sr_occupancy(int L, size_t smem)
 {
-    if (cudaFuncSetAttribute(sr_kernels[L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    SRKern kern = sr_kernels[L];
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sr_kernels[L], SR_WARPS * 32, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SR_WARPS * 32, smem) != cudaSuccess) return 0;
     return nb;
 }
 
 // Launch of the class-L kernel over descriptors already on the device.  The
 // queue counter is reset on the stream first.  grid = CTAs (persistent).
-int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot, size_t warp_bytes,
-                    unsigned long long *queue, int grid, int grab, cudaStream_t st)
+int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot,
+                    size_t warp_bytes, unsigned long long *queue, int grid, int grab, cudaStream_t st)
 {
     if (ntot <= 0) return RSGDF_OK;
     if (L < 0 || L > LTOT_MAX || grid < 1 || grab < 1) return RSGDF_EINVAL;
     const size_t smem = warp_bytes * SR_WARPS;
-    if (cudaFuncSetAttribute(sr_kernels[L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    SRKern kern = sr_kernels[L];
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSGDF_EDEVICE;
     if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return RSGDF_EDEVICE;
     const long long need = (ntot + (long long)SR_WARPS * grab - 1) / ((long long)SR_WARPS * grab);
     const int g = (int)std::min<long long>(grid, need);
-    sr_kernels[L]<<<g, SR_WARPS * 32, smem, st>>>(ddesc, dcum, ndesc, (int)warp_bytes, queue, grab);
+    kern<<<g, SR_WARPS * 32, smem, st>>>(ddesc, dcum, ndesc, (int)warp_bytes, queue, grab);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

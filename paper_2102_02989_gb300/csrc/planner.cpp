@@ -705,31 +705,40 @@ void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int>
     pair_doff[ns * ns] = (int)(dlist.size() / 3);
 }
 
-// F_m(T) = e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) in long double,
-// stored as Taylor blocks: row i holds F_{m+k}(T_i)/k! for m < BOYS_NM and
-// k < BOYS_TAYLOR (d^k F_m/dT^k = (-1)^k F_{m+k}), then e^{-T_i}/k!.
+// F_m(T) = e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) in long double
+// (every term positive), stored per class L as Taylor blocks about T_i
+// (d^k F_m/dT^k = (-1)^k F_{m+k}): row i of class L holds T_i, then
+// F_{m+k}(T_i)/k! for m = 0..L (L <= 1) or for m = L followed by
+// e^{-T_i}/k! (L >= 2).
 void boys_table(std::vector<double> &tab)
 {
-    tab.assign((size_t)BOYS_NT * BOYS_ROW, 0.0);
+    tab.assign((size_t)(LTOT_MAX + 1) * BOYS_NT * BOYS_W, 0.0);
     std::vector<long double> F(BOYS_NF);
     for (int i = 0; i < BOYS_NT; i++) {
-        long double T = (long double)i * BOYS_H;
-        long double eT = expl(-T);
+        const long double T = (long double)i * BOYS_H;
+        const long double eT = expl(-T);
         for (int m = 0; m < BOYS_NF; m++) {
             long double term = 1.0L / (2 * m + 1), sum = term;
-            for (int k = 1; k < 4000; k++) {
+            for (int k = 1; k < 8000; k++) {
                 term *= 2.0L * T / (2 * m + 2 * k + 1);
                 sum += term;
                 if (term < 1e-22L * sum) break;
             }
             F[m] = eT * sum;
         }
-        double *row = &tab[(size_t)i * BOYS_ROW];
-        long double fact = 1.0L;
-        for (int k = 0; k < BOYS_TAYLOR; k++) {
-            if (k > 0) fact *= k;
-            for (int m = 0; m < BOYS_NM; m++) row[m * BOYS_TAYLOR + k] = (double)(F[m + k] / fact);
-            row[BOYS_NM * BOYS_TAYLOR + k] = (double)(eT / fact);
+        for (int L = 0; L <= LTOT_MAX; L++) {
+            double *row = &tab[((size_t)L * BOYS_NT + i) * BOYS_W];
+            row[0] = (double)T;
+            long double fact = 1.0L;
+            for (int k = 0; k < BOYS_TAYLOR; k++) {
+                if (k > 0) fact *= k;
+                if (L <= 1) {
+                    for (int m = 0; m <= L; m++) row[1 + m * BOYS_TAYLOR + k] = (double)(F[m + k] / fact);
+                } else {
+                    row[1 + k] = (double)(F[L + k] / fact);
+                    row[1 + BOYS_TAYLOR + k] = (double)(eT / fact);
+                }
+            }
         }
     }
 }

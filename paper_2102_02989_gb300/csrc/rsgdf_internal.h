@@ -21,14 +21,16 @@ constexpr int NBIN_MAX = 128;                    // largest k-mesh (BvK cells) s
 constexpr double SCREEN_DR = 1.0;                // window width of the R12 cutoffs (Bohr)
 constexpr double SCREEN_EPS_PRIME = 1e-4;        // truncation of S_h (Supplementary Material)
 
-// Boys table: F_m(T_i), T_i = i * BOYS_H, i = 0..BOYS_NT-1, m = 0..BOYS_NM-1
+// Boys table, one block per class L = 0..LTOT_MAX: rows i = 0..BOYS_NT-1 at
+// T_i = i * BOYS_H.  Row layout: [0] T_i; classes L <= 1: Taylor blocks
+// F_{m+k}(T_i)/k!, k < BOYS_TAYLOR, for m = 0..L; classes L >= 2: the block
+// of m = L, then e^{-T_i}/k! (the device recurs downward from F_L).
 constexpr double BOYS_H = 0.1;
-constexpr int BOYS_NT = 401;
-constexpr double BOYS_TMAX = 40.0;
+constexpr int BOYS_NT = 1001;                   // T_i up to 100
+constexpr double BOYS_TMAX = 99.9;              // table below, power law above (e^{-T} < 1e-43)
 constexpr int BOYS_TAYLOR = 8;
-constexpr int BOYS_NM = LTOT_MAX + 1;           // orders with a Taylor block
-constexpr int BOYS_NF = LTOT_MAX + BOYS_TAYLOR + 1;   // orders tabulated
-constexpr int BOYS_ROW = (BOYS_NM + 1) * BOYS_TAYLOR;   // F_{m+k}(T_i)/k! for m < NM, then e^{-T_i}/k!
+constexpr int BOYS_NF = LTOT_MAX + BOYS_TAYLOR + 1;   // orders the generator evaluates
+constexpr int BOYS_W = 18;                      // doubles per row (1 + 2 blocks, padded to 16 bytes)
 constexpr int ENT_HDR = 8;                      // header doubles of a pair entry
 
 __host__ __device__ constexpr inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
@@ -105,7 +107,7 @@ int split_basis(const rsgdf_basis *b, double acut, SplitBasis &out, std::string 
 // j2c SR plan: "AO" basis = aux + unit partner, pairs (Q, unit)
 void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double omega, double eps,
                SRPlan &plan);
-void boys_table(std::vector<double> &tab);  // [BOYS_NT][BOYS_ROW]
+void boys_table(std::vector<double> &tab);  // [LTOT_MAX+1][BOYS_NT][BOYS_W]
 void single_E_host(int lc, double g, double *E);   // [(LMAX+1)^2]
 // AFT pair screening: list of d per AO shell pair with some primitive pair above eps
 void plan_pairs(const Lattice &L, const HBasis &ao, double eps, std::vector<int> &pair_doff,
