@@ -435,7 +435,13 @@ def main():
         "clocks": clk,
         "vs_plain_fp64": {"fp64_ms_per_step": ref_ms, "fp64_value": work / (ref_ms * 1e-3),
                           "speedup": ref_ms / (tmax / args.steps)},
-        "sr_terms_per_step": {"bound_screened": int(work), "computed": int(own_terms)},
+        "sr_terms_per_step": {"bound_screened": int(work), "computed": int(own_terms),
+                              "prim_terms_evaluated": int(sum(sum(s2.get("sr_prim_terms_by_L", [])) +
+                                                              sum(s3.get("sr_prim_terms_by_L", []))
+                                                              for s2, s3 in stats) / len(stats)),
+                              "prim_terms_dropped_by_combination_bound": int(
+                                  sum(s2.get("sr_prim_terms_skipped", 0) + s3.get("sr_prim_terms_skipped", 0)
+                                      for s2, s3 in stats) / len(stats))},
     }
     guarded(line, "roofline", lambda: roofline(stats, args, peak_fp64))
     line["phases_ms_per_step"] = line["roofline"].pop("phases_ms", None)
@@ -499,7 +505,7 @@ def _stats0(s):
     return {"sr_terms": 0, "sr_integrals": 0, "sr_flops": 0, "aft_units": 0, "lr_flops": 0, "n_launch": 0,
             "sr_ms": 0.0, "aft_ms": 0.0, "lr_gemm_ms": 0.0, "phase_ms": 0.0, "other_ms": 0.0,
             "sr_terms_by_L": [0] * 10, "sr_prim_terms": 0, "sr_items": 0, "sr_items_pruned": 0,
-            "sr_ms_by_L": [0.0] * 10, "sr_prim_terms_by_L": [0] * 10}
+            "sr_ms_by_L": [0.0] * 10, "sr_prim_terms_by_L": [0] * 10, "sr_prim_terms_skipped": 0}
 
 
 PHASE_NAMES = {"sr_ms": "k_sr3c (SR lattice-sum kernels, all class launches of one step)",

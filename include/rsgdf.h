@@ -307,6 +307,7 @@ typedef struct {
     long long sr_items_pruned;     /* of which skipped by the learned screen */
     double sr_ms_by_L[10];         /* device time of the SR kernel of each L class */
     long long sr_prim_terms_by_L[10];   /* SR terms times their primitive combinations, per L */
+    long long sr_prim_terms_skipped;    /* primitive terms dropped by the per-combination bound (not evaluated) */
 } rsgdf_stats;
 
 int rsgdf_last_stats(rsgdf_stats *out);

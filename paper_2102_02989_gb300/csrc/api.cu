@@ -279,6 +279,7 @@ struct SRExtras {
     float *feat_out = nullptr;        // features of every item (device [n][SR_NFEAT])
     float *mag_out = nullptr;         // magnitude mode (device [n])
     bool skip_sr = false;             // features only
+    float log_prim_cut = -1e31f;      // per-combination bound cut (natural log); -1e31: none
 };
 
 struct SRSetup {
@@ -391,6 +392,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.pair_doff = dpoff;
     A.dlist = R.ddl;
     A.sph = dsph;
+    A.log_prim_cut = ex.log_prim_cut;
     A.sphv = dsphv;
     A.sphvf = dsphvf;
     fill_lattice(L, A.a, A.bq, A.nk);
@@ -736,6 +738,9 @@ static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, uns
         if (ex.mlp->F != SR_NFEAT) return fail(RSGDF_EINVAL, "network input width does not match the SR features");
         ex.log10_cut = std::log10(opts->eps_screen) - 1.0;
     }
+    // a primitive combination whose bound stays below 1e-3 eps over every
+    // candidate translation of an item is not evaluated for that item
+    ex.log_prim_cut = (float)std::log(1e-3 * opts->eps_screen);
     RC(sr_setup(P.sr, S, L, P.plan, P.dao, P.dax, ao, ax, omega, P.X, P.nlt > 1 ? (long long)Nk * m : 0, m,
                 (long long)nao * nao, nao, 1, P.pfunc0, dcnt, ex));
     return RSGDF_OK;
@@ -1876,6 +1881,7 @@ int rsgdf_last_stats(rsgdf_stats *out)
         }
         t_stats.sr_integrals = (long long)t_count_host[LTOT_MAX + 1];
         t_stats.sr_items_pruned = (long long)t_count_host[2 * LTOT_MAX + 4];
+        t_stats.sr_prim_terms_skipped = (long long)t_count_host[2 * LTOT_MAX + 5];
         double ms[PH_N];
         t_timer.totals(ms, t_stats.sr_ms_by_L);
         for (int L = 0; L <= LTOT_MAX; L++) {

@@ -55,6 +55,7 @@ struct SRArgs {
     int warp_bytes;
     int ncomp_max, w_max, list_max;
     int combo_max;                    // primitive combinations of the largest triple of the launch (<= 64)
+    float log_prim_cut;               // drop a primitive combination of an item whose bound is below e^this (-1e30: never)
     unsigned long long *term_count;   // [LTOT_MAX+2] or NULL
     const double *ec_tab;             // [aux primitive][(LMAX+1)^2] single-centre Hermite coefficients
     const double *ptab;               // pair entries of the SR d list

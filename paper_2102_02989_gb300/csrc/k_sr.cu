@@ -205,6 +205,32 @@ size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int 
     return sr_smem(L, bc, ncomp_max, w_max, list_max, combo_max).total;
 }
 
+// Coulomb bound of one primitive SR term, natural log, in FP32 (a bound only
+// needs its order of magnitude).  The aux primitive c x^a y^b z^c e^{-g r^2},
+// |x^a y^b z^c| <= r^lP, has a potential no larger than at its centre,
+// |c| 2 pi Gamma(lP/2 + 1) / g^{lP/2 + 1} (the potential of a non-negative
+// radial density decreases outwards); erfc(w r)/r <= 1/r; and the pair
+// density c_i c_j |r-A|^lm |r-B|^ln e^{-a|r-A|^2 - b|r-B|^2} integrates to at
+// most |c_i c_j| e^{-ab/p R12^2} sum_{i',j'} C(lm,i') C(ln,j') |PA|^{lm-i'}
+// |PB|^{ln-j'} 2 pi Gamma((i'+j'+3)/2) / p^{(i'+j'+3)/2}.
+__constant__ float c_gamma_half[11] = {0.0f, 1.7724539f, 1.0f, 0.88622693f, 1.0f, 1.3293404f,
+                                       2.0f, 3.3233509f, 6.0f, 11.631728f, 24.0f};   // Gamma(n/2)
+__constant__ float c_binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+__device__ __forceinline__ float prim_combo_log_bound(int lP, float g, float cg, int lm, float a, float ca, int ln,
+                                                      float b, float cb, float R12)
+{
+    const float twopi = 6.2831853f;
+    const float p = a + b;
+    const float lq = __logf(fabsf(cg)) + __logf(twopi * c_gamma_half[lP + 2]) - 0.5f * (lP + 2) * __logf(g);
+    const float PA = b / p * R12, PB = a / p * R12;
+    float S = 0.0f;
+    for (int i = 0; i <= lm; i++)
+        for (int j = 0; j <= ln; j++)
+            S += c_binom[lm][i] * c_binom[ln][j] * powf(PA, (float)(lm - i)) * powf(PB, (float)(ln - j)) * twopi *
+                 c_gamma_half[i + j + 3] * __expf(-0.5f * (i + j + 3) * __logf(p));
+    return lq + __logf(fabsf(ca * cb)) - a * b / p * R12 * R12 + __logf(S);
+}
+
 // (t, u, v) of a packed index p = ridx(t, u, v)
 __device__ __forceinline__ void tuv_of(int p, int &t, int &u, int &v)
 {
@@ -297,27 +323,50 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const double omega2 = A.omega * A.omega;
 
     // constants of every primitive combination (k; i, j), one lane each:
-    // alpha, s = w^2/(w^2+alpha), sqrt(s), prefactor, product centre - C
+    // alpha, s = w^2/(w^2+alpha), sqrt(s), prefactor, product centre - C,
+    // and the combination's index.  A combination whose Coulomb bound (below)
+    // shows that it adds less than A.log_prim_cut over every candidate
+    // translation of the item is dropped here, and the kept ones are packed.
     const int npp = A.ao.nprim[mu] * A.ao.nprim[nu];
-    const int ncombo = A.ax.nprim[P] * npp;
-    for (int cb = lane; cb < ncombo; cb += 32) {
-        const int k = cb / npp, ij = cb - k * npp;
-        const int ok = A.ax.poff[P] + k;
-        const double g = A.ax.exps[ok];
-        const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
-        const double p = en[5];
-        const double ipg = 1.0 / (p + g);
-        const double alpha = p * g * ipg;
-        const double s = omega2 / (omega2 + alpha);
-        double *kc = Kc + 8 * cb;
-        kc[0] = alpha;
-        kc[1] = s;
-        kc[2] = sqrt(s);
-        kc[3] = 2.0 * KPI2_5 / (p * g) * sqrt(ipg) * A.ax.cn[ok] * en[6] * ((lP & 1) ? -1.0 : 1.0);
-        kc[4] = en[0] - Cx;
-        kc[5] = en[1] - Cy;
-        kc[6] = en[2] - Cz;
-        kc[7] = 0.0;
+    const int ncombo_all = A.ax.nprim[P] * npp;
+    int ncombo = 0;
+    for (int cb0 = 0; cb0 < ncombo_all; cb0 += 32) {
+        const int cb = cb0 + lane;
+        bool keep = false;
+        double kv[7];
+        if (cb < ncombo_all) {
+            const int k = cb / npp, ij = cb - k * npp;
+            const int ok = A.ax.poff[P] + k;
+            const double g = A.ax.exps[ok];
+            const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
+            const double p = en[5];
+            const double ipg = 1.0 / (p + g);
+            const double alpha = p * g * ipg;
+            const double s = omega2 / (omega2 + alpha);
+            kv[0] = alpha;
+            kv[1] = s;
+            kv[2] = sqrt(s);
+            kv[3] = 2.0 * KPI2_5 / (p * g) * sqrt(ipg) * A.ax.cn[ok] * en[6] * ((lP & 1) ? -1.0 : 1.0);
+            kv[4] = en[0] - Cx;
+            kv[5] = en[1] - Cy;
+            kv[6] = en[2] - Cz;
+            keep = true;
+            if (A.log_prim_cut > -1e30f) {
+                const int i = ij / A.ao.nprim[nu], j = ij - i * A.ao.nprim[nu];
+                const int oi = A.ao.poff[mu] + i, oj = A.ao.poff[nu] + j;
+                keep = prim_combo_log_bound(lP, (float)g, (float)A.ax.cn[ok], lm, (float)A.ao.exps[oi],
+                                            (float)A.ao.cn[oi], ln, (float)A.ao.exps[oj], (float)A.ao.cn[oj],
+                                            (float)R12) + __logf((float)max(tr.nsph, 1)) >= A.log_prim_cut;
+            }
+        }
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            double *kc = Kc + 8 * (ncombo + __popc(km & ((1u << lane) - 1u)));
+#pragma unroll
+            for (int x = 0; x < 7; x++) kc[x] = kv[x];
+            kc[7] = (double)cb;
+        }
+        ncombo += __popc(km);
     }
     __syncwarp();
 
@@ -480,7 +529,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                     __syncwarp();
                     // contractions, one combination after the other
                     for (int gg = 0; gg < G && cg + gg < ncombo; gg++) {
-                        const int cc = cg + gg, k = cc / npp, ij = cc - k * npp;
+                        const int cc = cg + gg, cb = (int)Kc[8 * cc + 7], k = cb / npp, ij = cb - k * npp;
                         const int ok = A.ax.poff[P] + k;
                         for (int e = lane; e < EC_SZ; e += 32) Ec[e] = A.ec_tab[ok * EC_SZ + e];
                         // Hermite coefficients of (d, primitive pair)
@@ -572,6 +621,8 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         atomicAdd(A.term_count + L, kept);
         atomicAdd(A.term_count + LTOT_MAX + 1, kept * (unsigned long long)ncomp);
         atomicAdd(A.term_count + LTOT_MAX + 2 + L, kept * (unsigned long long)ncombo);
+        if (ncombo < ncombo_all)
+            atomicAdd(A.term_count + 2 * LTOT_MAX + 5, kept * (unsigned long long)(ncombo_all - ncombo));
     }
 }
 

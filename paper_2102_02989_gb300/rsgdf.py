@@ -73,7 +73,8 @@ class Stats(C.Structure):
                 ("lr_gemm_ms", C.c_double), ("phase_ms", C.c_double), ("other_ms", C.c_double),
                 ("sr_terms_by_L", C.c_longlong * 10), ("sr_prim_terms", C.c_longlong),
                 ("sr_items", C.c_longlong), ("sr_items_pruned", C.c_longlong),
-                ("sr_ms_by_L", C.c_double * 10), ("sr_prim_terms_by_L", C.c_longlong * 10)]
+                ("sr_ms_by_L", C.c_double * 10), ("sr_prim_terms_by_L", C.c_longlong * 10),
+                ("sr_prim_terms_skipped", C.c_longlong)]
 
     def asdict(self):
         return {"sr_terms": self.sr_terms, "sr_integrals": self.sr_integrals,
@@ -83,7 +84,8 @@ class Stats(C.Structure):
                 "phase_ms": self.phase_ms, "other_ms": self.other_ms,
                 "sr_terms_by_L": list(self.sr_terms_by_L), "sr_prim_terms": self.sr_prim_terms,
                 "sr_items": self.sr_items, "sr_items_pruned": self.sr_items_pruned,
-                "sr_ms_by_L": list(self.sr_ms_by_L), "sr_prim_terms_by_L": list(self.sr_prim_terms_by_L)}
+                "sr_ms_by_L": list(self.sr_ms_by_L), "sr_prim_terms_by_L": list(self.sr_prim_terms_by_L),
+                "sr_prim_terms_skipped": self.sr_prim_terms_skipped}
 
 
 def library_path() -> str:
