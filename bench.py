@@ -753,7 +753,8 @@ def rocksalt_bench(rsgdf, inputs, paths, np, torch):
             if rep:
                 times.append(e0.elapsed_time(e1))
         res[name] = {"ms": statistics.median(times), "sr_ms": st["sr_ms"], "sr_terms": int(st["sr_terms"]),
-                     "sr_items": int(st["sr_items"]), "sr_items_pruned": int(st["sr_items_pruned"])}
+                     "sr_items": int(st["sr_items"]), "sr_items_pruned": int(st["sr_items_pruned"]),
+                     "sr_prim_terms": int(sum(st.get("sr_prim_terms_by_L", [])))}
         outs[name] = out
     res["speedup"] = res["fp64"]["ms"] / res["learned-mixed"]["ms"]
     res["sr_speedup"] = res["fp64"]["sr_ms"] / res["learned-mixed"]["sr_ms"]

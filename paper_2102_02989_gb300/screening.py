@@ -19,8 +19,9 @@ below cut = log10(eps) - 1 and, as a guard against extrapolation, the
 estimate itself plus its own calibrated margin for the item's class
 L = lP + lmu + lnu (the guard, the largest cut - estimate over all training
 items of that class with magnitude >= eps 10^-drop, plus ``safety``) is
-below the cut too; a class with training items but none at that level takes
-the largest calibrated guard, and a class absent from the training data is
+below the cut too; a class with training items but fewer than ``min_class``
+at that level takes the largest calibrated guard (a guard calibrated on a
+handful of items says little), and a class absent from the training data is
 never skipped.  The margin is calibrated on held-out items that
 must be kept (magnitude >= eps 10^-drop; many skipped items can land in one
 output element, so the per-item budget sits well below eps): the largest
@@ -53,7 +54,7 @@ BASE = 8
 
 
 def train_screen(X, t, epochs=40, batch=2048, lr=2e-3, tau=0.99, seed=0, holdout=0.2, safety=0.5, eps_screen=1e-8,
-                 drop=2.0):
+                 drop=2.0, min_class=50):
     """Train the network on (X, t) and calibrate its margin on a held-out part."""
     import torch
     # data preparation and calibration statistics on host copies (torch only moves memory)
@@ -86,11 +87,11 @@ def train_screen(X, t, epochs=40, batch=2048, lr=2e-3, tau=0.99, seed=0, holdout
     calibrated = []
     for L in range(10):
         kk = keep_all & (Lc == L)
-        if kk.any():
+        if kk.sum() >= min_class:
             guard[L] = float((cut - Xh[kk, BASE]).max()) + safety
             calibrated.append(guard[L])
-    # a class seen in training without any item at the keep level takes the most
-    # conservative calibrated guard; a class never seen is never skipped (inf)
+    # a class seen in training with too few items at the keep level takes the
+    # most conservative calibrated guard; a class never seen is never skipped (inf)
     for L in range(10):
         if not np.isfinite(guard[L]) and (Lc == L).any() and calibrated:
             guard[L] = max(calibrated)
