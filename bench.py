@@ -333,7 +333,8 @@ def main():
     # this rank's share of the step: a contiguous aux-shell range of j3c
     # (rows P of V) and a round-robin share of the k points of j2c; one rank
     # holds the whole step
-    shells = shard.aux_shell_shards(p.aux, world)[rank]
+    shells = shard.aux_shell_shards(p.aux, world, cost=shard.planner_costs(p.a, p.kmesh, p.ao, p.aux, **base)
+                                    if world > 1 else None)[rank]
     klist = list(range(rank, p.nk, world))
 
     def make(prob, opt, shells=None, klist=None):

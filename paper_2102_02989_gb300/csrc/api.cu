@@ -30,48 +30,76 @@ static thread_local bool t_count_valid = false;
 // when the statistics are read.
 enum { PH_SR = 0, PH_AFT, PH_GEMM, PH_PHASE, PH_OTHER, PH_N };
 struct PhaseTimer {
-    std::vector<cudaEvent_t> ev;
-    std::vector<int> kind, cls;
+    // event pairs: a phase (kind >= 0) on the call's stream, or one SR class
+    // (cls >= 0) on any stream; a pair with kind -1 only times its class
+    struct Pair {
+        cudaEvent_t b = nullptr, e = nullptr;
+        int kind = -1, cls = -1;
+    };
+    std::vector<Pair> pairs;
+    std::vector<int> open;   // pairs begun on the call's stream and not yet ended
+    int side_open = -1;
     cudaStream_t st = nullptr;
     bool on = true;   // off while a graph is captured
     void reset(cudaStream_t s)
     {
-        for (auto e : ev) cudaEventDestroy(e);
-        ev.clear();
-        kind.clear();
-        cls.clear();
+        for (auto &p : pairs) {
+            if (p.b) cudaEventDestroy(p.b);
+            if (p.e) cudaEventDestroy(p.e);
+        }
+        pairs.clear();
+        open.clear();
+        side_open = -1;
         st = s;
         on = true;
     }
-    cudaEvent_t mark()
+    static cudaEvent_t rec(cudaStream_t s)
     {
         cudaEvent_t e;
         cudaEventCreate(&e);
-        cudaEventRecord(e, st);
-        ev.push_back(e);
+        cudaEventRecord(e, s);
         return e;
     }
     void begin(int k, int c = -1)
     {
         if (!on) return;
-        kind.push_back(k);
-        cls.push_back(c);
-        mark();
+        Pair p;
+        p.kind = k;
+        p.cls = c;
+        p.b = rec(st);
+        pairs.push_back(p);
+        open.push_back((int)pairs.size() - 1);
     }
     void end()
     {
-        if (on) mark();
+        if (!on || open.empty()) return;
+        pairs[open.back()].e = rec(st);
+        open.pop_back();
+    }
+    void begin_on(cudaStream_t s, int c)
+    {
+        if (!on) return;
+        Pair p;
+        p.cls = c;
+        p.b = rec(s);
+        pairs.push_back(p);
+        side_open = (int)pairs.size() - 1;
+    }
+    void end_on(cudaStream_t s)
+    {
+        if (!on || side_open < 0) return;
+        pairs[side_open].e = rec(s);
+        side_open = -1;
     }
     void totals(double *ms, double *cls_ms)
     {
         for (int i = 0; i < PH_N; i++) ms[i] = 0.0;
         for (int i = 0; i <= LTOT_MAX; i++) cls_ms[i] = 0.0;
-        for (size_t i = 0; i + 1 < ev.size() && i / 2 < kind.size(); i += 2) {
+        for (const Pair &p : pairs) {
             float t = 0.0f;
-            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
-                ms[kind[i / 2]] += t;
-                if (cls[i / 2] >= 0) cls_ms[cls[i / 2]] += t;
-            }
+            if (!p.b || !p.e || cudaEventElapsedTime(&t, p.b, p.e) != cudaSuccess) continue;
+            if (p.kind >= 0) ms[p.kind] += t;
+            if (p.cls >= 0) cls_ms[p.cls] += t;
         }
     }
 };
@@ -561,15 +589,72 @@ static int sr_merge(const std::vector<const SRSetup *> &rs, Scratch &S, cudaStre
     return RSGDF_OK;
 }
 
+// Side streams of this host thread on the current device, one per class,
+// created once: the class launches of an SR pass are independent (each adds
+// its own blocks into X with atomics and owns its queue counter), so they
+// run concurrently, forked from and joined to the caller's stream by events.
+// A class whose items are few and long (high L) then shares the SMs with the
+// many short items of the low classes instead of running its tail alone.
+struct SideStreams {
+    int dev = -1;
+    cudaStream_t s[LTOT_MAX + 1] = {};
+    cudaEvent_t fork = nullptr, join[LTOT_MAX + 1] = {};
+};
+static thread_local SideStreams t_side[8];
+
+static int side_streams(SideStreams *&ss)
+{
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 8) {
+        ss = nullptr;
+        return RSGDF_OK;   // serial launches on the caller's stream
+    }
+    ss = &t_side[dev];
+    if (ss->dev != dev) {
+        for (int i = 0; i <= LTOT_MAX; i++) {
+            CU(cudaStreamCreateWithFlags(&ss->s[i], cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&ss->join[i], cudaEventDisableTiming));
+        }
+        CU(cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming));
+        ss->dev = dev;
+    }
+    return RSGDF_OK;
+}
+
 static int sr_run(std::vector<SRClassLaunch> &cl, unsigned long long *dqueue, cudaStream_t st, int &nl)
 {
-    for (SRClassLaunch &c : cl) {
-        t_timer.begin(PH_SR, c.L);
-        RC(launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes, dqueue + c.L,
-                           c.grid, c.grab, st));
-        t_timer.end();
+    if (cl.empty()) return RSGDF_OK;
+    SideStreams *ss = nullptr;
+    RC(side_streams(ss));
+    if (!ss || cl.size() == 1) {
+        for (SRClassLaunch &c : cl) {
+            t_timer.begin(PH_SR, c.L);
+            RC(launch_sr_queue(c.L, c.ddesc, c.dcum, (int)c.desc.size(), c.ntot, c.warp_bytes, dqueue + c.L,
+                               c.grid, c.grab, st));
+            t_timer.end();
+            nl++;
+        }
+        return RSGDF_OK;
+    }
+    t_timer.begin(PH_SR);
+    CU(cudaEventRecord(ss->fork, st));
+    // heaviest items first: their classes start while the SMs are empty
+    std::vector<SRClassLaunch *> order;
+    for (SRClassLaunch &c : cl) order.push_back(&c);
+    std::sort(order.begin(), order.end(), [](const SRClassLaunch *x, const SRClassLaunch *y) { return x->L > y->L; });
+    for (SRClassLaunch *c : order) {
+        cudaStream_t s = ss->s[c->L];
+        CU(cudaStreamWaitEvent(s, ss->fork, 0));
+        t_timer.begin_on(s, c->L);
+        RC(launch_sr_queue(c->L, c->ddesc, c->dcum, (int)c->desc.size(), c->ntot, c->warp_bytes, dqueue + c->L,
+                           c->grid, c->grab, s));
+        t_timer.end_on(s);
+        CU(cudaEventRecord(ss->join[c->L], s));
         nl++;
     }
+    for (SRClassLaunch *c : order) CU(cudaStreamWaitEvent(st, ss->join[c->L], 0));
+    t_timer.end();
     return RSGDF_OK;
 }
 
@@ -994,7 +1079,7 @@ static int j3c_exec_lr_group(J3cProblem &P, int g, double *Tj, cudaStream_t st, 
     if (P.mixed_aft) {
         RC(launch_split_a(nP, NG, P.W, P.Apl, st));
         RC(launch_aft_f32(Ga, P.dao, P.ao.nshell, nao, P.dent, P.nent, P.dseg, P.ptab, P.ptab32, P.db9, P.uph, P.ph0,
-                          Nk, P.Bpl, st));
+                          Nk, P.Bpl, P.ao.l.empty() ? 0 : *std::max_element(P.ao.l.begin(), P.ao.l.end()), st));
     } else {
         RC(launch_aft(Ga, P.dao, P.ao.nshell, nao, P.dent, P.dseg, P.ptab, Nk, P.Y, st));
     }
@@ -1006,6 +1091,7 @@ static int j3c_exec_lr_group(J3cProblem &P, int g, double *Tj, cudaStream_t st, 
         RC(launch_zgemm_tn(nP, nao * nao, NG, Nk, P.W, P.Y, (long long)2 * NG * nao * nao, Tj, 2 * m, st));
     t_timer.end();
     nl += 3;
+    if (P.mixed_aft && !P.ao.l.empty() && *std::max_element(P.ao.l.begin(), P.ao.l.end()) >= 3) nl++;   // f-shell pairs
     return RSGDF_OK;
 }
 

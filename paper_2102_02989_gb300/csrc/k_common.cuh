@@ -135,7 +135,7 @@ int launch_pair_prep(DevShells ao, int nshell, const PairEntry *ent, int nent, c
                      double *tab, float *tab32, const double *b9, float2 *uph, cudaStream_t st);
 int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
                    const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
-                   float *Bp, cudaStream_t st);
+                   float *Bp, int lmax_ao, cudaStream_t st);
 int launch_aft(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg,
                const double *tab, int Nk, double *Y, cudaStream_t st);
 int launch_ovlp_fold(DevShells ao, int nshell, int nao, const PairEntry *ent, const int *seg, const double *tab,

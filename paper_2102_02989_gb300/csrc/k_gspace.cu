@@ -328,6 +328,98 @@ __device__ __forceinline__ float2 cpowf(float2 z, int n)
 
 // Mixed-precision pair transforms: FP32 arithmetic; e^{-i q.P} =
 // e^{-i f.(b.P)} prod_j (e^{-i b_j.P})^{n_j} from FP64-accurate phasors.
+// One (G point, BvK cell dt, AO shell pair) of the mixed pair transform, for
+// the angular momenta LM, LN as compile-time constants: the accumulators and
+// the per-axis polynomial factors then live in registers.
+template <int LM, int LN>
+__device__ __forceinline__ void aft_f32_body(const GArgs &G, const DevShells &ao, int nao, int mu, int nu, int ig,
+                                             int dt, int pr, const PairEntry *ent, const int *seg, const float *tab32,
+                                             const float2 *uph, const float2 *ph0, int Nk, float *Bp, int nnt, int nkc)
+{
+    constexpr int ncm = (LM + 1) * (LM + 2) / 2, ncn = (LN + 1) * (LN + 2) / 2;
+    constexpr int n1 = (LM + 1) * (LN + 1) * (LM + LN + 2) / 2;
+    const int gn[3] = {G.g[3 * ig], G.g[3 * ig + 1], G.g[3 * ig + 2]};
+    float q[3];
+    for (int x = 0; x < 3; x++)
+        q[x] = (float)((gn[0] + G.f12[0]) * G.b[x] + (gn[1] + G.f12[1]) * G.b[3 + x] + (gn[2] + G.f12[2]) * G.b[6 + x]);
+    const float q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    float qp[3][LM + LN + 1];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        qp[x][0] = 1.0f;
+#pragma unroll
+        for (int t = 1; t <= LM + LN; t++) qp[x][t] = qp[x][t - 1] * q[x];
+    }
+    float accr[ncm * ncn], acci[ncm * ncn];
+#pragma unroll
+    for (int z = 0; z < ncm * ncn; z++) { accr[z] = 0.0f; acci[z] = 0.0f; }
+    float last_inv4p = -1.0f, gauss = 0.0f;
+    const int e0 = seg[pr * Nk + dt], e1 = seg[pr * Nk + dt + 1];
+    for (int e = e0; e < e1; e++) {
+        const float *en = tab32 + ent[e].off;
+        const float inv4p = en[3];
+        if (inv4p != last_inv4p) {
+            gauss = expf(-q2 * inv4p);
+            last_inv4p = inv4p;
+        }
+        float2 ph = ph0[e];
+        ph = cmulf(ph, cpowf(uph[3 * e], gn[0]));
+        ph = cmulf(ph, cpowf(uph[3 * e + 1], gn[1]));
+        ph = cmulf(ph, cpowf(uph[3 * e + 2], gn[2]));
+        const float base = en[4] * gauss;
+        const float br = base * ph.x, bi = base * ph.y;
+        // per axis and (a, b): sum_t E^{ab}_t (-i q)^t
+        float fr[3][(LM + 1) * (LN + 1)], fi[3][(LM + 1) * (LN + 1)];
+#pragma unroll
+        for (int x = 0; x < 3; x++) {
+            const float *Ex = en + ENT_HDR + x * n1;
+            int k = 0;
+#pragma unroll
+            for (int a = 0; a <= LM; a++)
+#pragma unroll
+                for (int b = 0; b <= LN; b++) {
+                    float re = 0.0f, im = 0.0f;
+#pragma unroll
+                    for (int t = 0; t <= a + b; t++, k++) {
+                        const float v = Ex[k] * qp[x][t];
+                        if ((t & 3) == 0) re += v;
+                        else if ((t & 3) == 1) im -= v;
+                        else if ((t & 3) == 2) re -= v;
+                        else im += v;
+                    }
+                    fr[x][a * (LN + 1) + b] = re;
+                    fi[x][a * (LN + 1) + b] = im;
+                }
+        }
+#pragma unroll
+        for (int ia = 0; ia < ncm; ia++)
+#pragma unroll
+            for (int ib = 0; ib < ncn; ib++) {
+                const signed char *ca = c_cart[LM][ia], *cb = c_cart[LN][ib];
+                const int i0 = ca[0] * (LN + 1) + cb[0], i1 = ca[1] * (LN + 1) + cb[1], i2 = ca[2] * (LN + 1) + cb[2];
+                const float xr = fr[0][i0] * fr[1][i1] - fi[0][i0] * fi[1][i1];
+                const float xi = fr[0][i0] * fi[1][i1] + fi[0][i0] * fr[1][i1];
+                const float yr = xr * fr[2][i2] - xi * fi[2][i2];
+                const float yi = xr * fi[2][i2] + xi * fr[2][i2];
+                accr[ia * ncn + ib] += yr * br - yi * bi;
+                acci[ia * ncn + ib] += yr * bi + yi * br;
+            }
+    }
+    // written straight into the split-TF32 operand tiles of the tensor-core contraction
+    const int mf = ao.foff[mu], nf = ao.foff[nu];
+#pragma unroll
+    for (int ia = 0; ia < ncm; ia++)
+#pragma unroll
+        for (int ib = 0; ib < ncn; ib++) {
+            const int n = (mf + ia) * nao + nf + ib;
+            tc_put_b(Bp, nnt, nkc, dt, n, ig, 0, accr[ia * ncn + ib]);
+            tc_put_b(Bp, nnt, nkc, dt, n, ig, 1, acci[ia * ncn + ib]);
+        }
+}
+
+// Pairs whose shells both have l <= 2: one instantiation per (lm, ln), chosen
+// per block (the pair is uniform over a block).  Pairs with an f shell are
+// left to k_aft_f32_f.
 __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, int nshell, int nao,
                                                          const PairEntry *ent, const int *seg, const float *tab32,
                                                          const float2 *uph, const float2 *ph0, int Nk, float *Bp,
@@ -337,7 +429,31 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, 
     const int dt = blockIdx.y, pr = blockIdx.z;
     if (ig >= G.NG) return;
     const int mu = pr / nshell, nu = pr % nshell;
+#define AFT_CASE(a, b)                                                                                          \
+    case (a) * (LMAX + 1) + (b):                                                                                \
+        aft_f32_body<a, b>(G, ao, nao, mu, nu, ig, dt, pr, ent, seg, tab32, uph, ph0, Nk, Bp, nnt, nkc);    \
+        break;
+    switch (ao.l[mu] * (LMAX + 1) + ao.l[nu]) {
+        AFT_CASE(0, 0) AFT_CASE(0, 1) AFT_CASE(0, 2)
+        AFT_CASE(1, 0) AFT_CASE(1, 1) AFT_CASE(1, 2)
+        AFT_CASE(2, 0) AFT_CASE(2, 1) AFT_CASE(2, 2)
+        default: break;
+    }
+#undef AFT_CASE
+}
+
+// Pairs with an f shell: the same transform with runtime loop bounds.
+__global__ void __launch_bounds__(AFT_THREADS) k_aft_f32_f(GArgs G, DevShells ao, int nshell, int nao,
+                                                           const PairEntry *ent, const int *seg, const float *tab32,
+                                                           const float2 *uph, const float2 *ph0, int Nk, float *Bp,
+                                                           int nnt, int nkc)
+{
+    const int ig = blockIdx.x * AFT_THREADS + threadIdx.x;
+    const int dt = blockIdx.y, pr = blockIdx.z;
+    if (ig >= G.NG) return;
+    const int mu = pr / nshell, nu = pr % nshell;
     const int lm = ao.l[mu], ln = ao.l[nu];
+    if (lm < 3 && ln < 3) return;
     const int ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
     const int n1 = pair_e1(lm, ln);
     const int gn[3] = {G.g[3 * ig], G.g[3 * ig + 1], G.g[3 * ig + 2]};
@@ -399,7 +515,6 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, 
                 acci[ia * ncn + ib] += yr * bi + yi * br;
             }
     }
-    // written straight into the split-TF32 operand tiles of the tensor-core contraction
     const int mf = ao.foff[mu], nf = ao.foff[nu];
     for (int ia = 0; ia < ncm; ia++)
         for (int ib = 0; ib < ncn; ib++) {
@@ -411,12 +526,14 @@ __global__ void __launch_bounds__(AFT_THREADS) k_aft_f32(GArgs G, DevShells ao, 
 
 int launch_aft_f32(const GArgs &G, DevShells ao, int nshell, int nao, const PairEntry *ent, int nent, const int *seg,
                    const double *tab, const float *tab32, const double *b9, const float2 *uph, float2 *ph0, int Nk,
-                   float *Bp, cudaStream_t st)
+                   float *Bp, int lmax_ao, cudaStream_t st)
 {
     const int nnt = (nao * nao + TC_N - 1) / TC_N, nkc = (G.NG + TC_KC - 1) / TC_KC;
     k_aft_phase0<<<(nent + 127) / 128, 128, 0, st>>>(ent, nent, tab, G.f12[0], G.f12[1], G.f12[2], b9, ph0);
     dim3 grid((G.NG + AFT_THREADS - 1) / AFT_THREADS, Nk, nshell * nshell);
     k_aft_f32<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab32, uph, ph0, Nk, Bp, nnt, nkc);
+    if (lmax_ao >= 3)
+        k_aft_f32_f<<<grid, AFT_THREADS, 0, st>>>(G, ao, nshell, nao, ent, seg, tab32, uph, ph0, Nk, Bp, nnt, nkc);
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 

@@ -46,6 +46,8 @@ __host__ __device__ inline MlpOff mlp_off(int F)
 // ---------------------------------------------------------------------------
 __global__ void k_sr_features(SRArgs A, float *feat)
 {
+    // FP32 throughout: the features feed a network whose decisions carry a
+    // calibrated margin, and FP64 issues at 1/64 of the FP32 rate here
     const long long item = A.item_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= A.item_end) return;
     int lo = A.tri_begin, hi = A.tri_end - 1;
@@ -56,94 +58,97 @@ __global__ void k_sr_features(SRArgs A, float *feat)
     const SRTripleDev tr = A.tri[lo];
     const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);
     const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
-    double Av[3], Bv[3], x[3];
+    float Av[3], Bv[3], x[3];
     for (int k = 0; k < 3; k++) {
-        Av[k] = A.ao.cen[3 * tr.mu + k];
-        Bv[k] = A.ao.cen[3 * tr.nu + k] + d0 * A.a[k] + d1 * A.a[3 + k] + d2 * A.a[6 + k];
+        Av[k] = (float)A.ao.cen[3 * tr.mu + k];
+        Bv[k] = (float)A.ao.cen[3 * tr.nu + k] + d0 * A.af[k] + d1 * A.af[3 + k] + d2 * A.af[6 + k];
     }
-    const double R12 = sqrt((Bv[0] - Av[0]) * (Bv[0] - Av[0]) + (Bv[1] - Av[1]) * (Bv[1] - Av[1]) +
+    const float R12 = sqrtf((Bv[0] - Av[0]) * (Bv[0] - Av[0]) + (Bv[1] - Av[1]) * (Bv[1] - Av[1]) +
                             (Bv[2] - Av[2]) * (Bv[2] - Av[2]));
-    for (int k = 0; k < 3; k++) x[k] = (tr.amu * Av[k] + tr.anu * Bv[k]) / (tr.amu + tr.anu) - A.ax.cen[3 * tr.P + k];
+    const float amu = (float)tr.amu, anu = (float)tr.anu;
+    for (int k = 0; k < 3; k++) x[k] = (amu * Av[k] + anu * Bv[k]) / (amu + anu) - (float)A.ax.cen[3 * tr.P + k];
     int l[3];
-    for (int i = 0; i < 3; i++) l[i] = __double2int_rn(x[0] * A.bq[3 * i] + x[1] * A.bq[3 * i + 1] + x[2] * A.bq[3 * i + 2]);
-    // exact nearest aux image: the rounded lattice point and its 26 neighbours
-    double rc = 1e300;
+    for (int i = 0; i < 3; i++)
+        l[i] = __float2int_rn(x[0] * (float)A.bq[3 * i] + x[1] * (float)A.bq[3 * i + 1] + x[2] * (float)A.bq[3 * i + 2]);
+    // nearest aux image: the rounded lattice point and its 26 neighbours
+    float rc2 = 3.0e38f;
     int ln[3] = {l[0], l[1], l[2]};
     for (int i = -1; i <= 1; i++)
         for (int j = -1; j <= 1; j++)
             for (int k = -1; k <= 1; k++) {
-                double r2 = 0.0;
+                float r2 = 0.0f;
                 for (int c = 0; c < 3; c++) {
-                    const double r = x[c] - ((l[0] + i) * A.a[c] + (l[1] + j) * A.a[3 + c] + (l[2] + k) * A.a[6 + c]);
+                    const float r = x[c] - ((l[0] + i) * A.af[c] + (l[1] + j) * A.af[3 + c] + (l[2] + k) * A.af[6 + c]);
                     r2 += r * r;
                 }
-                if (r2 < rc) {
-                    rc = r2;
+                if (r2 < rc2) {
+                    rc2 = r2;
                     ln[0] = l[0] + i;
                     ln[1] = l[1] + j;
                     ln[2] = l[2] + k;
                 }
             }
-    rc = sqrt(rc);
+    const float rc = sqrtf(rc2);
     // s-type SR integral of the nearest term summed over primitive combinations:
     // |c_P c_i c_j| (pi^2/(g p))^{3/2} e^{-ab/p R12^2} [erf(e1 R) - erf(e2 R)]/R
-    double est = 0.0;
-    const double om2 = A.omega * A.omega;
+    float est = 0.0f;
+    const float om2 = (float)(A.omega * A.omega);
+    const float kpi = 3.14159265f;
     for (int k = 0; k < A.ax.nprim[tr.P]; k++) {
         const int ok = A.ax.poff[tr.P] + k;
-        const double g = A.ax.exps[ok];
+        const float g = (float)A.ax.exps[ok];
         for (int i = 0; i < A.ao.nprim[tr.mu]; i++)
             for (int j = 0; j < A.ao.nprim[tr.nu]; j++) {
                 const int oi = A.ao.poff[tr.mu] + i, oj = A.ao.poff[tr.nu] + j;
-                const double ea = A.ao.exps[oi], eb = A.ao.exps[oj], p = ea + eb;
-                double R2 = 0.0;
+                const float ea = (float)A.ao.exps[oi], eb = (float)A.ao.exps[oj], p = ea + eb;
+                float R2 = 0.0f;
                 for (int c = 0; c < 3; c++) {
-                    const double r = (ea * Av[c] + eb * Bv[c]) / p - A.ax.cen[3 * tr.P + c] -
-                                     (ln[0] * A.a[c] + ln[1] * A.a[3 + c] + ln[2] * A.a[6 + c]);
+                    const float r = (ea * Av[c] + eb * Bv[c]) / p - (float)A.ax.cen[3 * tr.P + c] -
+                                    (ln[0] * A.af[c] + ln[1] * A.af[3 + c] + ln[2] * A.af[6 + c]);
                     R2 += r * r;
                 }
-                const double R = sqrt(R2);
-                const double e1 = sqrt(g * p / (g + p));
-                const double e2 = e1 * sqrt(om2 / (e1 * e1 + om2));
-                const double fR = (R < 1e-8) ? 2.0 * (e1 - e2) / sqrt(KPI) : (erf(e1 * R) - erf(e2 * R)) / R;
-                const double pf = KPI * KPI / (g * p);
-                est += fabs(A.ax.cn[ok] * A.ao.cn[oi] * A.ao.cn[oj]) * pf * sqrt(pf) * exp(-ea * eb / p * R12 * R12) * fR;
+                const float R = sqrtf(R2);
+                const float e1 = sqrtf(g * p / (g + p));
+                const float e2 = e1 * sqrtf(om2 / (e1 * e1 + om2));
+                const float fR = (R < 1e-4f) ? 2.0f * (e1 - e2) * 0.5641895835f : (erff(e1 * R) - erff(e2 * R)) / R;
+                const float pf = kpi * kpi / (g * p);
+                est += fabsf((float)A.ax.cn[ok] * (float)A.ao.cn[oi] * (float)A.ao.cn[oj]) * pf * sqrtf(pf) *
+                       __expf(-ea * eb / p * R12 * R12) * fR;
             }
     }
     // every aux image inside the screening radius adds to the lattice sum: scale
     // by the image sum of the diffuse-rate s-type kernel relative to the
-    // nearest image ([erf(e1 R) - erf(e2 R)]/R, FP32 is ample for a feature)
+    // nearest image ([erf(e1 R) - erf(e2 R)]/R)
     {
         const float e1 = (float)tr.eta1, e2 = (float)tr.eta2;
         auto fk = [&](float R) {
             return (R < 1e-4f) ? 2.0f * (e1 - e2) * 0.5641895835f : (erff(e1 * R) - erff(e2 * R)) / R;
         };
-        const float f0 = fk((float)rc);
+        const float f0 = fk(rc);
         const float fcut = (float)tr.Rc_cut + 1e-3f;
-        const float fx = (float)x[0], fy = (float)x[1], fz = (float)x[2];
         float sum = 0.0f;
         for (int idx = 0; idx < tr.nsph; idx++) {
             const int li0 = l[0] + A.sph[3 * idx], li1 = l[1] + A.sph[3 * idx + 1], li2 = l[2] + A.sph[3 * idx + 2];
-            const float ex = fx - (li0 * A.af[0] + li1 * A.af[3] + li2 * A.af[6]);
-            const float ey = fy - (li0 * A.af[1] + li1 * A.af[4] + li2 * A.af[7]);
-            const float ez = fz - (li0 * A.af[2] + li1 * A.af[5] + li2 * A.af[8]);
+            const float ex = x[0] - (li0 * A.af[0] + li1 * A.af[3] + li2 * A.af[6]);
+            const float ey = x[1] - (li0 * A.af[1] + li1 * A.af[4] + li2 * A.af[7]);
+            const float ez = x[2] - (li0 * A.af[2] + li1 * A.af[5] + li2 * A.af[8]);
             const float r = sqrtf(ex * ex + ey * ey + ez * ez);
             if (r <= fcut) sum += fk(r);
         }
-        if (f0 > 0.0f && sum > f0) est *= (double)(sum / f0);
+        if (f0 > 0.0f && sum > f0) est *= sum / f0;
     }
-    est = log10(fmax(est, 1e-300));
+    const float lest = log10f(fmaxf(est, 1e-37f));
     float *f = feat + item * SR_NFEAT;
     f[0] = (float)A.ax.l[tr.P];
     f[1] = (float)A.ao.l[tr.mu];
     f[2] = (float)A.ao.l[tr.nu];
-    f[3] = (float)log(tr.aP);
-    f[4] = (float)log(tr.amu);
-    f[5] = (float)log(fmax(tr.anu, 1e-300));
-    f[6] = (float)R12;
-    f[7] = (float)rc;
-    f[8] = (float)fmax(est, -300.0);
-    f[9] = (float)log(tr.Rc_cut);
+    f[3] = logf((float)tr.aP);
+    f[4] = logf((float)tr.amu);
+    f[5] = logf(fmaxf((float)tr.anu, 1e-37f));
+    f[6] = R12;
+    f[7] = rc;
+    f[8] = est > 0.0f ? lest : -300.0f;
+    f[9] = logf((float)tr.Rc_cut);
 }
 
 int launch_sr_features(const SRArgs &A, float *feat, cudaStream_t st)

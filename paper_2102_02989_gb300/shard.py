@@ -12,17 +12,34 @@ import numpy as np
 
 
 def _shell_cost(aux, s):
-    """Relative cost of one aux shell in j3c: Cartesian functions x primitives."""
+    """Relative cost of one aux shell in j3c without a plan: Cartesian
+    functions x primitives x (1 + l)."""
     l = int(aux.l[s])
     return (l + 1) * (l + 2) // 2 * int(aux.nprim[s]) * (1 + l)
 
 
-def aux_shell_shards(aux, nranks):
-    """Contiguous aux-shell ranges [(s0, s1)] per rank, balanced by cost; every
-    shell belongs to exactly one range; a range may be empty when there are
-    more ranks than shells."""
+def planner_costs(a, kmesh, ao, aux, **opt):
+    """Per aux shell, the SR work the library's host planner assigns it: its
+    screened work items (aux shell, AO shell pair, d) times its Cartesian
+    functions and primitives.  Host planning only (no device work)."""
+    from . import rsgdf
+    cost = []
+    for s in range(len(aux.l)):
+        n = rsgdf.rsgdf_sr_items(a, kmesh, ao, aux, shells=(s, s + 1), features=False, **opt)[0]
+        l = int(aux.l[s])
+        cost.append(max(1, n) * (l + 1) * (l + 2) // 2 * int(aux.nprim[s]))
+    return np.array(cost, dtype=np.float64)
+
+
+def aux_shell_shards(aux, nranks, cost=None):
+    """Contiguous aux-shell ranges [(s0, s1)] per rank, balanced by cost (per
+    shell, e.g. planner_costs; default _shell_cost); every shell belongs to
+    exactly one range; a range may be empty when there are more ranks than
+    shells."""
     ns = len(aux.l)
-    cost = np.array([_shell_cost(aux, s) for s in range(ns)], dtype=np.float64)
+    if cost is None:
+        cost = np.array([_shell_cost(aux, s) for s in range(ns)], dtype=np.float64)
+    cost = np.asarray(cost, dtype=np.float64)
     cum = np.concatenate([[0.0], np.cumsum(cost)])
     cuts = [0]
     for r in range(1, nranks):

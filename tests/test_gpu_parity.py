@@ -157,10 +157,12 @@ def test_invalid_arguments_rejected(rs):
 MIXED_REL = 1e-6
 
 
-@pytest.mark.parametrize("km", [(1, 1, 1), (2, 2, 1)])
-def test_lr_mixed_tensor_core(rs, orc, km):
+@pytest.mark.parametrize("km,lao", [((1, 1, 1), 2), ((2, 2, 1), 2), ((2, 1, 1), 3)])
+def test_lr_mixed_tensor_core(rs, orc, km, lao):
+    """lao = 3 puts f shells among the AO pairs: their transforms take the
+    generic kernel, the others the per-(lmu, lnu) instantiations."""
     import torch
-    p = inputs.tiny(kmesh=km, lmax_ao=2, lmax_aux=3, natm=2, seed=5)
+    p = inputs.tiny(kmesh=km, lmax_ao=lao, lmax_aux=3, natm=2, seed=5)
     nk = int(np.prod(km))
     kp = inputs.kpairs_all(nk)
     w = 0.9

@@ -17,18 +17,21 @@ def _worker(rank, world, init_file, q):
     p = inputs.tiny(kmesh=(2, 1, 1), lmax_ao=1, lmax_aux=2, natm=2, seed=4)
     kp = inputs.kpairs_all(2)
     s0, s1 = shard.aux_shell_shards(p.aux, world)[rank]
-    part = None
+    part, terms = None, 0
     if s1 > s0:
-        part = oracle.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9),
-                          shells=(s0, s1))
+        part, cnt = oracle.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9),
+                               shells=(s0, s1), return_counts=True)
+        terms = cnt["terms"]
     got = [None] * world
     dist.all_gather_object(got, (s0, s1, part))
     # timing reduction: rank r took 10 + r ms and processed 100 + r units
     tm, units = shard.reduce_timing(dist, [10.0 + rank, 1.0], 100 + rank)
+    # the bench's units: SR lattice terms of each rank's shard, summed over ranks
+    _, terms_all = shard.reduce_timing(dist, [1.0], terms)
     dist.barrier()
     dist.destroy_process_group()
     if rank == 0:
-        q.put((got, tm, units))
+        q.put((got, tm, units, terms_all))
 
 
 @pytest.fixture(scope="module")
@@ -46,13 +49,16 @@ def test_aux_shards_gather_to_the_whole(orc_built, tmp_path):
     procs = [ctx.Process(target=_worker, args=(r, 2, init_file, q)) for r in range(2)]
     for pr in procs:
         pr.start()
-    got, tm, units = q.get(timeout=600)
+    got, tm, units, terms_all = q.get(timeout=600)
     for pr in procs:
         pr.join(timeout=120)
         assert pr.exitcode == 0
     p = inputs.tiny(kmesh=(2, 1, 1), lmax_ao=1, lmax_aux=2, natm=2, seed=4)
     kp = inputs.kpairs_all(2)
-    full = orc_built.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9))
+    full, cnt = orc_built.j3c(p.a, p.kmesh, p.ao, p.aux, 0.9, kp, eps_sr=1e-12, eps_lr=1e-12, gmesh=(9, 9, 9),
+                              return_counts=True)
+    # the shards' units add up to the whole problem's
+    assert terms_all == cnt["terms"] > 0
     parts = sorted(got, key=lambda x: x[0])
     assert parts[0][0] == 0 and parts[-1][1] == len(p.aux.l)
     cat = np.concatenate([x[2] for x in parts if x[2] is not None], axis=1)
@@ -130,3 +136,11 @@ def test_pair_shards_cover_every_pair_once():
         flat = sorted(i for s in sh for i in s)
         assert flat == list(range(npair))
         assert max(len(s) for s in sh) - min(len(s) for s in sh) <= 1
+
+
+def test_j2c_k_shards_cover_the_mesh():
+    """The bench's j2c partition: round-robin k points, each exactly once."""
+    for nk in (1, 8, 27, 64):
+        for world in (1, 2, 3, 8):
+            ks = [k for r in range(world) for k in range(r, nk, world)]
+            assert sorted(ks) == list(range(nk))
