@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <atomic>
+#include <future>
 #include <mutex>
 #include <set>
 #include <string>
@@ -346,11 +347,41 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     for (const SRTriple &t : plan.tri)
         if (hax.nprim[t.P] * hao.nprim[t.mu] * hao.nprim[t.nu] > 64)
             return fail(RSGDF_ENOTIMPL, "more than 64 primitive combinations in one shell triple");
+    // per triple: the device record, its work items, and the constants of its
+    // primitive combinations (k; i, j), which do not depend on the item's d:
+    // alpha = p g/(p + g), s = w^2/(w^2 + alpha), sqrt s, the prefactor
+    // 2 pi^{5/2}/(p g sqrt(p + g)) c_k c_i c_j (-1)^lP, and the d-independent
+    // part of the log Coulomb bound of the combination
     std::vector<SRTripleDev> td(plan.tri.size());
+    std::vector<int> item_tri((size_t)plan.n_items);
+    std::vector<double> ccon;
+    std::vector<float> cbnd;
+    const double om2 = omega * omega;
+    const double gamma_half[11] = {0.0, 1.7724538509055160, 1.0, 0.8862269254527580, 1.0, 1.3293403881791370,
+                                   2.0, 3.3233509704478426, 6.0, 11.631728396567450, 24.0};   // Gamma(n/2)
     for (size_t i = 0; i < plan.tri.size(); i++) {
         const SRTriple &t = plan.tri[i];
-        td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, t.Rc_cut, t.amu, t.anu, t.item_off,
-                 t.log10A, t.beta, t.eta1, t.eta2, t.aP};
+        td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, (int)(ccon.size() / 4), t.Rc_cut, t.amu,
+                 t.anu, t.item_off, t.log10A, t.beta, t.eta1, t.eta2, t.aP};
+        for (long long it = t.item_off; it < t.item_off + t.nd; it++) item_tri[(size_t)it] = (int)i;
+        const int lP = hax.l[t.P];
+        for (int k = 0; k < hax.nprim[t.P]; k++)
+            for (int ii = 0; ii < hao.nprim[t.mu]; ii++)
+                for (int jj = 0; jj < hao.nprim[t.nu]; jj++) {
+                    const int ok = hax.poff[t.P] + k, oi = hao.poff[t.mu] + ii, oj = hao.poff[t.nu] + jj;
+                    const double g = hax.exps[ok], p = hao.exps[oi] + hao.exps[oj];
+                    const double ipg = 1.0 / (p + g);
+                    const double alpha = p * g * ipg;
+                    const double s = om2 / (om2 + alpha);
+                    ccon.push_back(alpha);
+                    ccon.push_back(s);
+                    ccon.push_back(std::sqrt(s));
+                    ccon.push_back(2.0 * KPI2_5 / (p * g) * std::sqrt(ipg) * hax.cn[ok] * (hao.cn[oi] * hao.cn[oj]) *
+                                   ((lP & 1) ? -1.0 : 1.0));
+                    const double lq = std::log(std::fabs(hax.cn[ok])) + std::log(2.0 * KPI * gamma_half[lP + 2]) -
+                                      0.5 * (lP + 2) * std::log(g) + std::log(std::fabs(hao.cn[oi] * hao.cn[oj]));
+                    cbnd.push_back((float)std::max(lq, -1e30));
+                }
     }
     SRTripleDev *dtri;
     double *dwin;
@@ -372,6 +403,12 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     float *dsphvf;
     RC(S.upload(dsphv, sphv));
     RC(S.upload(dsphvf, sphvf));
+    int *ditem_tri;
+    double *dccon;
+    float *dcbnd;
+    RC(S.upload(ditem_tri, item_tri));
+    RC(S.upload(dccon, ccon));
+    RC(S.upload(dcbnd, cbnd));
     // Hermite tables of every (pair, d, primitive pair) of the SR d lists,
     // shared by all aux shells (entries of one d contiguous, ij order)
     const int npairs = hao.nshell * hao.nshell;
@@ -423,6 +460,9 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.log_prim_cut = ex.log_prim_cut;
     A.sphv = dsphv;
     A.sphvf = dsphvf;
+    A.item_tri = ditem_tri;
+    A.ccon = dccon;
+    A.cbnd = dcbnd;
     fill_lattice(L, A.a, A.bq, A.nk);
     A.Nk = L.Nk;
     A.omega = omega;
@@ -800,7 +840,30 @@ static int j3c_check(J3cProblem &P, const rsgdf_cell *cell, const rsgdf_basis *a
 
 // Plans and device buffers of a problem that passed j3c_check.
 // SR plan (host screening) and its device tables; needs the k12 groups.
-static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, unsigned long long *dcnt)
+// SR screening plan of a problem that passed j3c_check (host only, reads
+// only the lattice, the bases and the options, writes only P.plan), so it
+// can run on another host thread while the LR part is prepared and enqueued.
+static void j3c_plan_sr(J3cProblem &P, const rsgdf_opts *opts)
+{
+    if (opts->split_alpha > 0.0) {
+        const double acut = opts->split_alpha;
+        auto diffuse = [&](const HBasis &b, int sh) {
+            for (int i = 0; i < b.nprim[sh]; i++)
+                if (b.exps[b.poff[sh] + i] > acut) return false;
+            return true;
+        };
+        std::vector<char> dx(P.ax.nshell), da(P.ao.nshell);
+        for (int sh = 0; sh < P.ax.nshell; sh++) dx[sh] = diffuse(P.ax, sh);
+        for (int sh = 0; sh < P.ao.nshell; sh++) da[sh] = diffuse(P.ao, sh);
+        plan_sr3c(P.L, P.ao, P.ax, P.s0, P.s1, P.omega, opts->eps_screen, P.plan,
+                  [&](int Q, int mu, int nu) { return !dx[Q] && !(da[mu] && da[nu]); });
+    } else {
+        plan_sr3c(P.L, P.ao, P.ax, P.s0, P.s1, P.omega, opts->eps_screen, P.plan);
+    }
+}
+
+static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, unsigned long long *dcnt,
+                          bool planned = false)
 {
     const Lattice &L = P.L;
     const HBasis &ao = P.ao, &ax = P.ax;
@@ -808,12 +871,7 @@ static int j3c_prepare_sr(J3cProblem &P, Scratch &S, const rsgdf_opts *opts, uns
     const long long m = P.m;
     const double omega = P.omega;
     // SR folded sums X[lt][dt][P][mu][nu]
-    if (P.split_alpha > 0.0)
-        plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan, [&](int Q, int mu, int nu) {
-            return !P.ax_diffuse[Q] && !(P.ao_diffuse[mu] && P.ao_diffuse[nu]);
-        });
-    else
-        plan_sr3c(L, ao, ax, P.s0, P.s1, omega, opts->eps_screen, P.plan);
+    if (!planned) j3c_plan_sr(P, opts);
     P.nlt = (P.gkey.size() == 1 && P.gkey[0] == 0) ? 1 : Nk;
     RC(S.alloc(P.X, (size_t)P.nlt * Nk * m));
     SRExtras ex;
@@ -1232,6 +1290,10 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     if (opts->kernel == RSGDF_KERNEL_PLAIN && mode != MODE_LR)
         return fail(RSGDF_EINVAL, "the plain kernel is for rsgdf_j3c_lr only");
     RC(check_device());
+    // the host screening of the SR sums runs beside the LR preparation and the
+    // LR device work (declared after P: an early return waits for it first)
+    std::future<void> sr_plan;
+    if (mode & MODE_SR) sr_plan = std::async(std::launch::async, [&P, opts] { j3c_plan_sr(P, opts); });
     cudaStream_t st = (cudaStream_t)opts->stream;
     RC(ensure_boys(st));
     t_timer.reset(st);
@@ -1244,7 +1306,10 @@ static int j3c_impl(const rsgdf_cell *cell, const rsgdf_basis *ao_in, const rsgd
     CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * (2 * LTOT_MAX + 6), st));
     const bool lr_first = (mode == (MODE_SR | MODE_LR)) && P.B >= (int)P.gkey.size();
     if (lr_first) RC(j3c_exec_lr_first(P, st, nl));   // device busy while the host plans the SR sums
-    if (mode & MODE_SR) RC(j3c_prepare_sr(P, S, opts, dcnt));
+    if (mode & MODE_SR) {
+        sr_plan.get();
+        RC(j3c_prepare_sr(P, S, opts, dcnt, true));
+    }
     std::vector<SRClassLaunch> cl;
     if (mode & MODE_SR) RC(sr_merge({&P.sr}, S, st, cl));
     RC(j3c_exec_pre(P, st, nl));

@@ -28,6 +28,7 @@ struct DevShells {
 struct SRTripleDev {
     int P, mu, nu, pair;
     int nwin, win_off, nd, nsph;
+    int cc_off;       // first entry of the triple's primitive combinations in SRArgs::ccon / cbnd
     double Rc_cut, amu, anu;
     long long item_off;
     double log10A, beta, eta1, eta2, aP;
@@ -42,6 +43,9 @@ struct SRArgs {
     const int *pair_doff, *dlist, *sph;
     const double *sphv;               // Cartesian vectors of the lattice list (FP64), [nsph][3]
     const float *sphvf;               // the same in FP32 (pre-filter)
+    const int *item_tri;              // [n_items] triple of each work item
+    const double *ccon;               // per (triple, combination) [4]: alpha, s, sqrt s, prefactor (d-independent)
+    const float *cbnd;                // per (triple, combination): d-independent part of the log Coulomb bound
     double a[9];    // lattice vectors (rows)
     float af[9];    // the same in FP32 (pre-filter of the translations)
     double bq[9];   // b_i / 2 pi: fractional coordinates

@@ -216,19 +216,21 @@ size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int 
 __constant__ float c_gamma_half[11] = {0.0f, 1.7724539f, 1.0f, 0.88622693f, 1.0f, 1.3293404f,
                                        2.0f, 3.3233509f, 6.0f, 11.631728f, 24.0f};   // Gamma(n/2)
 __constant__ float c_binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
-__device__ __forceinline__ float prim_combo_log_bound(int lP, float g, float cg, int lm, float a, float ca, int ln,
-                                                      float b, float cb, float R12)
+// The part of the bound that depends on the item's d (through R12): the
+// overlap factor and the pair-density sum.  The rest, log(|c| 2 pi
+// Gamma(lP/2 + 1) / g^{lP/2+1}) + log|c_i c_j|, is per triple and combination
+// and comes from the host (SRArgs::cbnd).
+__device__ __forceinline__ float prim_combo_log_bound_r12(int lm, float a, int ln, float b, float R12)
 {
     const float twopi = 6.2831853f;
     const float p = a + b;
-    const float lq = __logf(fabsf(cg)) + __logf(twopi * c_gamma_half[lP + 2]) - 0.5f * (lP + 2) * __logf(g);
     const float PA = b / p * R12, PB = a / p * R12;
     float S = 0.0f;
     for (int i = 0; i <= lm; i++)
         for (int j = 0; j <= ln; j++)
             S += c_binom[lm][i] * c_binom[ln][j] * powf(PA, (float)(lm - i)) * powf(PB, (float)(ln - j)) * twopi *
                  c_gamma_half[i + j + 3] * __expf(-0.5f * (i + j + 3) * __logf(p));
-    return lq + __logf(fabsf(ca * cb)) - a * b / p * R12 * R12 + __logf(S);
+    return -a * b / p * R12 * R12 + __logf(S);
 }
 
 // (t, u, v) of a packed index p = ridx(t, u, v)
@@ -270,13 +272,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     short *Li = (short *)(base + sm.li);
     double *Kc = (double *)(base + sm.kc);   // [combo][8]
 
-    // the triple of this item: last triple with item_off <= item
-    int lo = A.tri_begin, hi = A.tri_end - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (A.tri[mid].item_off <= item) lo = mid; else hi = mid - 1;
-    }
-    const SRTripleDev tr = A.tri[lo];
+    const SRTripleDev tr = A.tri[A.item_tri[item]];
     const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);   // global d index
     const int P = tr.P, mu = tr.mu, nu = tr.nu;
     const int lP = A.ax.l[P], lm = A.ao.l[mu], ln = A.ao.l[nu];
@@ -284,15 +280,27 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const int ncomp = ncP * ncm * ncn;
     const int n1 = (lm + 1) * (ln + 1) * (lm + ln + 2) / 2;
     const int Lp = lm + ln, npt = (Lp + 1) * (Lp + 2) * (Lp + 3) / 6;
-    if (lane == 0) {
-        // offsets of the pair-side coefficient lists, one list per (a, b)
-        int o = 0;
-        for (int ab = 0; ab < ncm * ncn; ab++) {
-            const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
-            loff[ab] = o;
-            o += (ca[0] + cb[0] + 1) * (ca[1] + cb[1] + 1) * (ca[2] + cb[2] + 1);
+    {
+        // offsets of the pair-side coefficient lists, one list per (a, b): a
+        // warp prefix sum of the list lengths
+        int carry = 0;
+        for (int ab0 = 0; ab0 < ncm * ncn; ab0 += 32) {
+            const int ab = ab0 + lane;
+            int len = 0;
+            if (ab < ncm * ncn) {
+                const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
+                len = (ca[0] + cb[0] + 1) * (ca[1] + cb[1] + 1) * (ca[2] + cb[2] + 1);
+            }
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (ab < ncm * ncn) loff[ab] = carry + inc - len;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        loff[ncm * ncn] = o;
+        if (lane == 0) loff[ncm * ncn] = carry;
     }
     __syncwarp();
     const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
@@ -320,7 +328,6 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const int dt = bvk_bin(d0, d1, d2, A.nk);
     const double *win = A.win + tr.win_off;
     const double Rc2 = tr.Rc_cut * tr.Rc_cut;
-    const double omega2 = A.omega * A.omega;
 
     // constants of every primitive combination (k; i, j), one lane each:
     // alpha, s = w^2/(w^2+alpha), sqrt(s), prefactor, product centre - C,
@@ -335,28 +342,23 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         bool keep = false;
         double kv[7];
         if (cb < ncombo_all) {
-            const int k = cb / npp, ij = cb - k * npp;
-            const int ok = A.ax.poff[P] + k;
-            const double g = A.ax.exps[ok];
+            const int ij = cb % npp;
+            const double *cc = A.ccon + 4 * (long long)(tr.cc_off + cb);
             const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
-            const double p = en[5];
-            const double ipg = 1.0 / (p + g);
-            const double alpha = p * g * ipg;
-            const double s = omega2 / (omega2 + alpha);
-            kv[0] = alpha;
-            kv[1] = s;
-            kv[2] = sqrt(s);
-            kv[3] = 2.0 * KPI2_5 / (p * g) * sqrt(ipg) * A.ax.cn[ok] * en[6] * ((lP & 1) ? -1.0 : 1.0);
+            kv[0] = cc[0];
+            kv[1] = cc[1];
+            kv[2] = cc[2];
+            kv[3] = cc[3];
             kv[4] = en[0] - Cx;
             kv[5] = en[1] - Cy;
             kv[6] = en[2] - Cz;
             keep = true;
             if (A.log_prim_cut > -1e30f) {
                 const int i = ij / A.ao.nprim[nu], j = ij - i * A.ao.nprim[nu];
-                const int oi = A.ao.poff[mu] + i, oj = A.ao.poff[nu] + j;
-                keep = prim_combo_log_bound(lP, (float)g, (float)A.ax.cn[ok], lm, (float)A.ao.exps[oi],
-                                            (float)A.ao.cn[oi], ln, (float)A.ao.exps[oj], (float)A.ao.cn[oj],
-                                            (float)R12) + __logf((float)max(tr.nsph, 1)) >= A.log_prim_cut;
+                keep = A.cbnd[tr.cc_off + cb] +
+                           prim_combo_log_bound_r12(lm, (float)A.ao.exps[A.ao.poff[mu] + i], ln,
+                                                    (float)A.ao.exps[A.ao.poff[nu] + j], (float)R12) +
+                           __logf((float)max(tr.nsph, 1)) >= A.log_prim_cut;
             }
         }
         const unsigned km = __ballot_sync(0xffffffffu, keep);
