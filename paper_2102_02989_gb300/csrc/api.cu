@@ -403,6 +403,9 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     float *dsphvf;
     RC(S.upload(dsphv, sphv));
     RC(S.upload(dsphvf, sphvf));
+    std::vector<float> sphlen(plan.sph_len.begin(), plan.sph_len.end());
+    float *dsphlen;
+    RC(S.upload(dsphlen, sphlen));
     int *ditem_tri;
     double *dccon;
     float *dcbnd;
@@ -460,6 +463,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.log_prim_cut = ex.log_prim_cut;
     A.sphv = dsphv;
     A.sphvf = dsphvf;
+    A.sphlen = dsphlen;
     A.item_tri = ditem_tri;
     A.ccon = dccon;
     A.cbnd = dcbnd;

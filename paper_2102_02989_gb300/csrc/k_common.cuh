@@ -43,6 +43,7 @@ struct SRArgs {
     const int *pair_doff, *dlist, *sph;
     const double *sphv;               // Cartesian vectors of the lattice list (FP64), [nsph][3]
     const float *sphvf;               // the same in FP32 (pre-filter)
+    const float *sphlen;              // their lengths (ascending), FP32
     const int *item_tri;              // [n_items] triple of each work item
     const double *ccon;               // per (triple, combination) [4]: alpha, s, sqrt s, prefactor (d-independent)
     const float *cbnd;                // per (triple, combination): d-independent part of the log Coulomb bound

@@ -1098,17 +1098,25 @@ __global__ void __launch_bounds__(256) k_phase2_df(const double2 *__restrict__ T
 // ---------------------------------------------------------------------------
 constexpr int DFT_NMAX = 16;
 
-__global__ void __launch_bounds__(256) k_dft_axis(double2 *__restrict__ T, long long S, long long nouter, int N,
+// NT > 0: the line length as a compile-time constant (the line stays in
+// registers); NT = 0: any length up to DFT_NMAX, given at run time.
+template <int NT>
+__global__ void __launch_bounds__(256) k_dft_axis(double2 *__restrict__ T, long long S, long long nouter, int Nrt,
                                                   const double2 *__restrict__ tw, int conj)
 {
+    const int N = NT > 0 ? NT : Nrt;
+    constexpr int NV = NT > 0 ? NT : DFT_NMAX;
     const long long nl = nouter * S;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nl; id += (long long)gridDim.x * blockDim.x) {
         const long long outer = id / S, inner = id - outer * S;
         double2 *line = T + outer * N * S + inner;
-        double2 v[DFT_NMAX];
+        double2 v[NV];
+#pragma unroll
         for (int n = 0; n < N; n++) v[n] = line[n * S];
+#pragma unroll
         for (int q = 0; q < N; q++) {
             double re = 0.0, im = 0.0;
+#pragma unroll
             for (int n = 0; n < N; n++) {
                 const double2 w = __ldg(&tw[q * N + n]);
                 const double wy = conj ? -w.y : w.y;
@@ -1167,8 +1175,13 @@ int launch_dft_mesh(double *T, const int nk[3], long long slab, long long nrep, 
         for (int e = 0; e < d; e++) outer *= nk[e];
         if (N > 1) {
             const long long nl = outer * inner;
-            k_dft_axis<<<grid_for(nl), 256, 0, st>>>((double2 *)T, inner, outer, N,
-                                                     (const double2 *)tw + d * DFT_NMAX * DFT_NMAX, conj);
+            const double2 *twd = (const double2 *)tw + d * DFT_NMAX * DFT_NMAX;
+            switch (N) {
+#define DFT_CASE(n) case n: k_dft_axis<n><<<grid_for(nl), 256, 0, st>>>((double2 *)T, inner, outer, N, twd, conj); break;
+                DFT_CASE(2) DFT_CASE(3) DFT_CASE(4) DFT_CASE(5) DFT_CASE(6) DFT_CASE(7) DFT_CASE(8)
+#undef DFT_CASE
+                default: k_dft_axis<0><<<grid_for(nl), 256, 0, st>>>((double2 *)T, inner, outer, N, twd, conj);
+            }
             if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
         }
         inner *= N;
@@ -1206,17 +1219,23 @@ __device__ __forceinline__ float4 df4_from(double2 v)
     return make_float4(r.h, r.l, i.h, i.l);
 }
 
-__global__ void __launch_bounds__(256) k_dft_axis_df(float4 *__restrict__ T, long long S, long long nouter, int N,
+template <int NT>
+__global__ void __launch_bounds__(256) k_dft_axis_df(float4 *__restrict__ T, long long S, long long nouter, int Nrt,
                                                      const float4 *__restrict__ tw, int conj)
 {
+    const int N = NT > 0 ? NT : Nrt;
+    constexpr int NV = NT > 0 ? NT : DFT_NMAX;
     const long long nl = nouter * S;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nl; id += (long long)gridDim.x * blockDim.x) {
         const long long outer = id / S, inner = id - outer * S;
         float4 *line = T + outer * N * S + inner;
-        float4 v[DFT_NMAX];
+        float4 v[NV];
+#pragma unroll
         for (int n = 0; n < N; n++) v[n] = line[n * S];
+#pragma unroll
         for (int q = 0; q < N; q++) {
             dflt re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+#pragma unroll
             for (int n = 0; n < N; n++) {
                 const float4 w = __ldg(&tw[q * N + n]);
                 const dflt c = {w.x, w.y};
@@ -1290,8 +1309,13 @@ int launch_dft_mesh_df(double *T, const int nk[3], long long slab, long long nre
         for (int e = 0; e < d; e++) outer *= nk[e];
         if (N > 1) {
             const long long nl = outer * inner;
-            k_dft_axis_df<<<grid_for(nl), 256, 0, st>>>((float4 *)T, inner, outer, N,
-                                                        (const float4 *)tw4 + d * DFT_NMAX * DFT_NMAX, conj);
+            const float4 *twd = (const float4 *)tw4 + d * DFT_NMAX * DFT_NMAX;
+            switch (N) {
+#define DFT_CASE(n) case n: k_dft_axis_df<n><<<grid_for(nl), 256, 0, st>>>((float4 *)T, inner, outer, N, twd, conj); break;
+                DFT_CASE(2) DFT_CASE(3) DFT_CASE(4) DFT_CASE(5) DFT_CASE(6) DFT_CASE(7) DFT_CASE(8)
+#undef DFT_CASE
+                default: k_dft_axis_df<0><<<grid_for(nl), 256, 0, st>>>((float4 *)T, inner, outer, N, twd, conj);
+            }
             if (cudaGetLastError() != cudaSuccess) return RSGDF_EDEVICE;
         }
         inner *= N;

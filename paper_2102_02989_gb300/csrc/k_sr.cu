@@ -325,6 +325,19 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const double hx = xr0 - L0x, hy = xr1 - L0y, hz = xr2 - L0z;
     const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
     const float fcut = (float)tr.Rc_cut + 1e-3f;
+    // a lattice-list entry l' can pass |h - l'| <= Rc_cut only if |l'| <= Rc_cut +
+    // |h|: the candidates of this item are a prefix of the length-sorted list,
+    // usually shorter than the triple's (which assumes the largest |h|)
+    int nsph = tr.nsph;
+    {
+        const float lim = fcut + sqrtf(fx * fx + fy * fy + fz * fz) + 1e-3f;
+        int lo = 0, hi = tr.nsph;   // first entry longer than lim in [lo, hi]
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A.sphlen[mid] <= lim) lo = mid + 1; else hi = mid;
+        }
+        nsph = lo;
+    }
     const int dt = bvk_bin(d0, d1, d2, A.nk);
     const double *win = A.win + tr.win_off;
     const double Rc2 = tr.Rc_cut * tr.Rc_cut;
@@ -376,10 +389,10 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     unsigned long long kept = 0;
     float magmax = 0.0f;   // largest |block| the item adds (magnitude mode)
     int nq = 0;   // FP32 survivors waiting for the exact FP64 test (smem queue Qd)
-    for (int b0 = 0; b0 < tr.nsph; b0 += 32) {
+    for (int b0 = 0; b0 < nsph; b0 += 32) {
         const int idx = b0 + lane;
         bool pass = false;
-        if (idx < tr.nsph) {
+        if (idx < nsph) {
             // FP32 pre-filter with a margin far above its rounding error
             const float ex = fx - A.sphvf[3 * idx], ey = fy - A.sphvf[3 * idx + 1], ez = fz - A.sphvf[3 * idx + 2];
             pass = (ex * ex + ey * ey + ez * ez <= fcut * fcut);
@@ -388,7 +401,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         if (pass) Qd[nq + __popc(pm & ((1u << lane) - 1u))] = idx;
         nq += __popc(pm);
         __syncwarp();
-        const bool lastround = (b0 + 32 >= tr.nsph);
+        const bool lastround = (b0 + 32 >= nsph);
         if (nq < 32 && !lastround) continue;
         // exact FP64 test of up to 64 queued candidates, 32 at a time
         for (int q0 = 0; q0 < nq; q0 += 32) {
