@@ -53,51 +53,83 @@ __device__ __forceinline__ float top_float(double T)
     return __int_as_float(max(hi - (896 << 20), 0) << 3);
 }
 
-// F_m(T), m = 0..L.  Below BOYS_TMAX: Taylor series about the nearest
-// tabulated point T_i (D = T_i - T, |D| <= h/2 up to the float rounding of
-// the index); classes L <= 1 sum one series per order, classes L >= 2 sum
-// the series of F_L and of e^{-T} = e^{-T_i} e^{D} and recur downward,
-// F_m = (2T F_{m+1} + e^{-T})/(2m+1).  Above it: F_0 = sqrt(pi/T)/2 and the
-// upward recursion without e^{-T} (below 1e-43 there).  The branch and the
-// index use integer and FP32 arithmetic; the FP64 work is one subtraction,
-// the Horner steps and the recursion.
+// The table row of class L nearest to T (T_i = i h, the index from integer
+// and FP32 arithmetic only) and D = T_i - T, |D| <= h/2 up to the float
+// rounding of the index.
 template <int L>
-__device__ __forceinline__ void boys_f64(double T, double *F)
+__device__ __forceinline__ const double *boys_row(double T, float Tf, double &D)
+{
+    const int i = min(__float2int_rn(Tf * (float)(1.0 / BOYS_H)), BOYS_NT - 1);
+    const double *row = g_boys_table + ((size_t)L * BOYS_NT + i) * BOYS_W;
+    D = row[0] - T;
+    return row;
+}
+
+// sum_k c_k D^k, k < BOYS_TAYLOR (Horner)
+__device__ __forceinline__ double boys_taylor(const double *c, double D)
+{
+    double f = c[BOYS_TAYLOR - 1];
+#pragma unroll
+    for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
+    return f;
+}
+
+// F_L(T) = c_L T^{-L-1/2} where e^{-T} is negligible: c_L = (sqrt(pi)/2) prod_{m<L} (m + 1/2)
+__host__ __device__ constexpr double boys_asym(int L)
+{
+    double c = 0.5 * 1.772453850905516027298167483341;   // sqrt(pi)/2
+    for (int m = 0; m < L; m++) c *= m + 0.5;
+    return c;
+}
+
+// Classes L <= 1: F_m(T), m = 0..L, one Taylor series per order below
+// BOYS_TMAX; above it F_0 = sqrt(pi/T)/2 and the upward recursion without
+// e^{-T} (below 1e-43 there).
+template <int L>
+__device__ __forceinline__ void boys_low(double T, double *F)
 {
     const float Tf = top_float(T);
     if (Tf < (float)BOYS_TMAX) {
-        const int i = min(__float2int_rn(Tf * (float)(1.0 / BOYS_H)), BOYS_NT - 1);
-        const double *row = g_boys_table + ((size_t)L * BOYS_NT + i) * BOYS_W;
-        const double D = row[0] - T;
-        if (L <= 1) {
+        double D;
+        const double *row = boys_row<L>(T, Tf, D);
 #pragma unroll
-            for (int m = 0; m <= L; m++) {
-                const double *c = row + 1 + m * BOYS_TAYLOR;
-                double f = c[BOYS_TAYLOR - 1];
-#pragma unroll
-                for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
-                F[m] = f;
-            }
-        } else {
-            const double *c = row + 1;
-            double f = c[BOYS_TAYLOR - 1];
-#pragma unroll
-            for (int k = BOYS_TAYLOR - 2; k >= 0; k--) f = fma(f, D, c[k]);
-            F[L] = f;
-            const double *ce = row + 1 + BOYS_TAYLOR;
-            double e = ce[BOYS_TAYLOR - 1];
-#pragma unroll
-            for (int k = BOYS_TAYLOR - 2; k >= 0; k--) e = fma(e, D, ce[k]);
-            const double T2 = T + T;
-#pragma unroll
-            for (int m = L - 1; m >= 0; m--) F[m] = fma(T2, F[m + 1], e) * (1.0 / (2 * m + 1));
-        }
+        for (int m = 0; m <= L; m++) F[m] = boys_taylor(row + 1 + m * BOYS_TAYLOR, D);
     } else {
         const double rs = rsqrt(T);
         const double it = rs * rs;
-        F[0] = 0.5 * sqrt(KPI) * rs;
+        F[0] = boys_asym(0) * rs;
 #pragma unroll
         for (int m = 0; m < L; m++) F[m + 1] = F[m] * ((m + 0.5) * it);
+    }
+}
+
+// Classes L >= 2: F_L(T) and e^{-T} = e^{-T_i} e^{D}, each one Taylor series
+// about T_i (T < BOYS_TMAX; the caller guarantees it for the attenuated
+// argument sT < 70).
+template <int L>
+__device__ __forceinline__ void boys_seed_table(double T, float Tf, double &FL, double &eT)
+{
+    double D;
+    const double *row = boys_row<L>(T, Tf, D);
+    FL = boys_taylor(row + 1, D);
+    eT = boys_taylor(row + 1 + BOYS_TAYLOR, D);
+}
+
+// The same for any T >= 0: above BOYS_TMAX the power law and e^{-T} = 0.
+template <int L>
+__device__ __forceinline__ void boys_seed(double T, double &FL, double &eT)
+{
+    const float Tf = top_float(T);
+    if (Tf < (float)BOYS_TMAX) {
+        boys_seed_table<L>(T, Tf, FL, eT);
+    } else {
+        const double rs = rsqrt(T);
+        const double it = rs * rs;
+        double f = boys_asym(L) * rs;
+#pragma unroll
+        for (int m = 0; m < L; m++) f *= it;
+        FL = f;
+        eT = 0.0;
     }
 }
 
@@ -107,18 +139,67 @@ __host__ __device__ constexpr int ridx(int t, int u, int v)
     return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
 }
 
-// Hermite integrals R_tuv, t+u+v <= L, of the erfc kernel, in place: level n
-// from L down to 0, totals from high to low so that every read still sees
-// level n+1.  sw[n] = s^{n+1/2}, fw[n] = (-2 alpha)^n (per primitive
-// combination), s = omega^2/(omega^2 + alpha).
+// Per-combination constants of the erfc auxiliary integrals, 2L+2 doubles
+// (s = omega^2/(omega^2 + alpha), sw_n = s^{n+1/2}, fw_n = (-2 alpha)^n):
+// classes L >= 2: [0] fw_L, [1] sw_L, then for n < L the pair
+// fw_n/(2n+1), -fw_n sw_n/(2n+1); classes L <= 1: the pairs fw_n, sw_n.
 template <int L>
-__device__ __forceinline__ void hermite_R(double T, double sT, const double *sw, const double *fw, double X, double Y,
-                                          double Z, double *r)
+__device__ __forceinline__ void erfc_consts(double alpha, double s, double sqrt_s, double *cw)
 {
-    double F[L + 1], Fs[L + 1];
-    boys_f64<L>(T, F);
-    boys_f64<L>(sT, Fs);
-    r[0] = fw[L] * fma(-sw[L], Fs[L], F[L]);
+    double sw = sqrt_s, fw = 1.0;
+#pragma unroll
+    for (int n = 0; n <= L; n++) {
+        if constexpr (L >= 2) {
+            if (n < L) {
+                cw[2 + 2 * n] = fw * (1.0 / (2 * n + 1));
+                cw[3 + 2 * n] = -(fw * sw) * (1.0 / (2 * n + 1));
+            } else {
+                cw[0] = fw;
+                cw[1] = sw;
+            }
+        } else {
+            cw[2 * n] = fw;
+            cw[2 * n + 1] = sw;
+        }
+        sw *= s;
+        fw *= -2.0 * alpha;
+    }
+}
+
+// Hermite integrals R_tuv, t+u+v <= L, of the erfc kernel at one
+// translation, added to acc.  The auxiliary integrals
+// G_n = (-2 alpha)^n H_n, H_n = F_n(T) - s^{n+1/2} F_n(sT), obey a downward
+// recursion of their own: H_n is the integral of t^{2n} e^{-T t^2} over
+// [sqrt s, 1], and integrating (t^{2n+1} e^{-T t^2})' over that interval gives
+// (2n+1) H_n = 2T H_{n+1} + e^{-T} - s^{n+1/2} e^{-sT}, that is
+// G_n = (-R^2 G_{n+1} + fw_n e^{-T} - fw_n sw_n e^{-sT}) / (2n+1), R^2 = T/alpha.
+// Rounding errors stay at the scale eps E_n, E_n = F_n(T) + s^{n+1/2} F_n(sT),
+// of the difference that this replaces: F's own recursion gives
+// F_n(x)/F_{n+1}(x) >= 2x/(2n+1), so the factor 2T/(2n+1) carried by an error
+// in G_{n+1} maps eps E_{n+1} to at most eps E_n.  Classes L >= 2 seed G_L from F_L(T) and
+// F_L(sT) and recur; classes L <= 1 form each G_n from its own series.
+// Levels n = L-1 .. 1 of R_tuv are built in place in r (totals from high to
+// low so that every read still sees level n+1); level 0 goes straight into
+// acc.  Requires sT < 70.
+template <int L>
+__device__ __forceinline__ void hermite_acc(double T, double sT, double R2, const double *cw, double X, double Y,
+                                            double Z, double *acc)
+{
+    constexpr int NR1 = L >= 1 ? (L * (L + 1) * (L + 2)) / 6 : 1;   // entries of totals <= L-1
+    double r[NR1];
+    double eT = 0.0, esT = 0.0, G0 = 0.0;
+    if constexpr (L >= 2) {
+        double FL, FsL;
+        boys_seed<L>(T, FL, eT);
+        boys_seed_table<L>(sT, top_float(sT), FsL, esT);
+        r[0] = cw[0] * fma(-cw[1], FsL, FL);
+    } else {
+        double F[L + 1], Fs[L + 1];
+        boys_low<L>(T, F);
+        boys_low<L>(sT, Fs);
+        G0 = cw[0] * fma(-cw[1], Fs[0], F[0]);
+        if constexpr (L == 1) r[0] = cw[2] * fma(-cw[3], Fs[L], F[L]);
+    }
 #pragma unroll
     for (int n = L - 1; n >= 0; n--) {
 #pragma unroll
@@ -128,23 +209,30 @@ __device__ __forceinline__ void hermite_R(double T, double sT, const double *sw,
 #pragma unroll
                 for (int u = S - t; u >= 0; u--) {
                     const int v = S - t - u;
-                    double val;
+                    double val = n == 0 ? acc[ridx(t, u, v)] : 0.0;
                     if (t > 0) {
-                        val = X * r[ridx(t - 1, u, v)];
+                        val = n == 0 ? fma(X, r[ridx(t - 1, u, v)], val) : X * r[ridx(t - 1, u, v)];
                         if (t > 1) val = fma((double)(t - 1), r[ridx(t - 2, u, v)], val);
                     } else if (u > 0) {
-                        val = Y * r[ridx(t, u - 1, v)];
+                        val = n == 0 ? fma(Y, r[ridx(t, u - 1, v)], val) : Y * r[ridx(t, u - 1, v)];
                         if (u > 1) val = fma((double)(u - 1), r[ridx(t, u - 2, v)], val);
                     } else {
-                        val = Z * r[ridx(t, u, v - 1)];
+                        val = n == 0 ? fma(Z, r[ridx(t, u, v - 1)], val) : Z * r[ridx(t, u, v - 1)];
                         if (v > 1) val = fma((double)(v - 1), r[ridx(t, u, v - 2)], val);
                     }
-                    r[ridx(t, u, v)] = val;
+                    if (n == 0) acc[ridx(t, u, v)] = val;
+                    else r[ridx(t, u, v)] = val;
                 }
             }
         }
-        r[0] = fw[n] * fma(-sw[n], Fs[n], F[n]);
+        if constexpr (L >= 2) {
+            const double b = fma(cw[2 + 2 * n], eT, cw[3 + 2 * n] * esT);
+            const double g = fma(-R2 * (1.0 / (2 * n + 1)), r[0], b);
+            if (n == 0) G0 = g;
+            else r[0] = g;
+        }
     }
+    acc[0] += G0;
 }
 
 // compact Hermite-coefficient layout of a pair entry: E^{ab}_t at eoff(a,b) + t
@@ -495,14 +583,8 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                     if (cmy < ncombo) {
                         const double *kc = Kc + 8 * cmy;
                         const double alpha = kc[0], s = kc[1];
-                        double sw[L + 1], fw[L + 1];
-                        sw[0] = kc[2];
-                        fw[0] = 1.0;
-#pragma unroll
-                        for (int n = 1; n <= L; n++) {
-                            sw[n] = sw[n - 1] * s;
-                            fw[n] = fw[n - 1] * (-2.0 * alpha);
-                        }
+                        double cw[2 * L + 2];
+                        erfc_consts<L>(alpha, s, kc[2], cw);
                         const double Px = kc[4], Py = kc[5], Pz = kc[6];
                         double *Rg = Rb + grp * nb * NR;
                         // contiguous slice of the sorted translations per lane of the group
@@ -525,16 +607,14 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                 cur = bn;
                             }
                             const double X = Px - Sx[tt], Y = Py - Sy[tt], Z = Pz - Sz[tt];
-                            const double T = alpha * (X * X + Y * Y + Z * Z);
+                            const double R2 = X * X + Y * Y + Z * Z;
+                            const double T = alpha * R2;
                             // F_n(T) and s^{n+1/2} F_n(sT) share their power-law part; for sT >= 70
                             // they differ by O(e^{-sT}) < 1e-30: the erfc term vanishes (the test
                             // compares the top words of the FP64 encodings as integers)
                             const double sT = s * T;
                             if (__double2hiint(sT) >= SR_SKIP_ST_HI) continue;
-                            double r[NR];
-                            hermite_R<L>(T, sT, sw, fw, X, Y, Z, r);
-#pragma unroll
-                            for (int q = 0; q < NR; q++) accR[q] += r[q];
+                            hermite_acc<L>(T, sT, R2, cw, X, Y, Z, accR);
                         }
                         if (cur >= 0) {
 #pragma unroll
