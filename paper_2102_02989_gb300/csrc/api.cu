@@ -529,6 +529,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
         Ac.w_max = wmax;
         Ac.list_max = lmax_list;
         Ac.combo_max = cmax;
+        Ac.nbin_max = A.Nk;
         R.cls.push_back(Ac);
         R.cls_L.push_back(c);
     }
@@ -579,7 +580,7 @@ static int g_num_sms = 0;
 static int sr_set_bc(SRClassLaunch &c, int bc, cudaStream_t st)
 {
     c.bc = bc;
-    c.warp_bytes = sr_warp_bytes(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax);
+    c.warp_bytes = sr_warp_bytes(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax, c.nkmax);
     for (SRArgs &a : c.desc) {
         a.bc = bc;
         a.warp_bytes = (int)c.warp_bytes;
@@ -587,9 +588,10 @@ static int sr_set_bc(SRClassLaunch &c, int bc, cudaStream_t st)
         a.w_max = c.wmax;
         a.list_max = c.lmax;
         a.combo_max = c.cmax;
+        a.nbin_max = c.nkmax;
     }
     CU(cudaMemcpyAsync(c.ddesc, c.desc.data(), sizeof(SRArgs) * c.desc.size(), cudaMemcpyHostToDevice, st));
-    const int occ = sr_occupancy(c.L, sr_launch_smem(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax));
+    const int occ = sr_occupancy(c.L, sr_launch_smem(c.L, bc, c.ncmax, c.wmax, c.lmax, c.cmax, c.nkmax));
     if (occ < 1) return fail(RSGDF_EDEVICE, "SR kernel does not fit on an SM");
     if (!g_num_sms) {
         int dev = 0;

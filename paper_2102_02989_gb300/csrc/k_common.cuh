@@ -60,6 +60,7 @@ struct SRArgs {
     int warp_bytes;
     int ncomp_max, w_max, list_max;
     int combo_max;                    // primitive combinations of the largest triple of the launch (<= 64)
+    int nbin_max;                     // BvK cells of the largest k mesh of the launch (<= NBIN_MAX): bin counters per warp
     float log_prim_cut;               // drop a primitive combination of an item whose bound is below e^this (-1e30: never)
     unsigned long long *term_count;   // [LTOT_MAX+2] or NULL
     const double *ec_tab;             // [aux primitive][(LMAX+1)^2] single-centre Hermite coefficients
@@ -95,8 +96,8 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
 // rows (BvK cell x primitive combination) of Hermite sums a warp holds for a bin chunk bc:
 // room for up to 4 combinations at once when the chunk is small
 __host__ __device__ constexpr int sr_rb_rows(int bc) { return 4 * bc < 32 ? 4 * bc : (bc > 32 ? bc : 32); }
-size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max);
-size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max);
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);
 int sr_occupancy(int L, size_t smem);
 int launch_sr_queue(int L, const SRArgs *ddesc, const long long *dcum, int ndesc, long long ntot,
                     size_t warp_bytes, unsigned long long *queue, int grid, int grab, cudaStream_t st);

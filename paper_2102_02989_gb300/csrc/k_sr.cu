@@ -262,7 +262,7 @@ constexpr int SR_SKIP_ST_HI = 0x40518000;   // top word of 70.0: erfc terms with
 struct SRSmem {
     unsigned sx, sb, tq, tb, cnt, fill, loff, qd, eab, ec, rb, o, wb, lc, li, kc, total;
 };
-__host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
+__host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin)
 {
     SRSmem s;
     unsigned b = 0;
@@ -270,8 +270,8 @@ __host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_ma
     s.sb = b; b += SR_NT * 4u;
     s.tq = b; b += SR_NT * 4u;
     s.tb = b; b += SR_NT * 4u;
-    s.cnt = b; b += (NBIN_MAX + 4) * 4u;
-    s.fill = b; b += (NBIN_MAX + 4) * 4u;
+    s.cnt = b; b += (unsigned)(nbin + 4) * 4u;
+    s.fill = b; b += (unsigned)(nbin + 4) * 4u;
     s.loff = b; b += (NC_MAX * NC_MAX + 4) * 4u;
     s.qd = b; b += 64u * 4u;
     b = (b + 15u) & ~15u;
@@ -288,9 +288,9 @@ __host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_ma
     return s;
 }
 
-size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
+size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin)
 {
-    return sr_smem(L, bc, ncomp_max, w_max, list_max, combo_max).total;
+    return sr_smem(L, bc, ncomp_max, w_max, list_max, combo_max, nbin).total;
 }
 
 // Coulomb bound of one primitive SR term, natural log, in FP32 (a bound only
@@ -342,7 +342,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
 {
     if (A.item_skip && A.item_skip[item]) return;   // pruned by the learned screen (warp-uniform)
     constexpr int NR = ntuv(L);
-    const SRSmem sm = sr_smem(L, A.bc, A.ncomp_max, A.w_max, A.list_max, A.combo_max);
+    const SRSmem sm = sr_smem(L, A.bc, A.ncomp_max, A.w_max, A.list_max, A.combo_max, A.nbin_max);
     double *Sx = (double *)(base + sm.sx), *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
     int *Sb = (int *)(base + sm.sb);
     int *Tq = (int *)(base + sm.tq);   // collected: index into the lattice list
@@ -727,8 +727,14 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
 // item_begin) are drawn by warps from one queue, grab items per atomic.
 // Descriptors of one launch share bc, ncomp_max, w_max and list_max, so all
 // warps carve shared memory alike.
+// Registers per thread of the class-L kernel: classes L <= 2 fit in 168 and
+// L = 3 in 200 without spilling, so 6 and 5 CTAs of 2 warps can share an SM
+// (latency of the collection and contraction phases is then hidden by more
+// warps); the higher classes keep 255 (their shared memory admits few CTAs).
+__host__ __device__ constexpr int sr_max_regs(int L) { return L <= 2 ? 168 : (L == 3 ? 200 : 255); }
+
 template <int L>
-__global__ void __launch_bounds__(SR_WARPS * 32, 1) k_sr3c(const SRArgs *__restrict__ desc, const long long *__restrict__ cum,
+__global__ void __maxnreg__(sr_max_regs(L)) k_sr3c(const SRArgs *__restrict__ desc, const long long *__restrict__ cum,
                                                         int ndesc, int warp_bytes, unsigned long long *queue, int grab)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -768,9 +774,9 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max)
     return bc > nk_max ? (nk_max < 1 ? 1 : nk_max) : bc;
 }
 
-size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max)
+size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin)
 {
-    return sr_warp_bytes(L, bc, ncomp_max, w_max, list_max, combo_max) * SR_WARPS;
+    return sr_warp_bytes(L, bc, ncomp_max, w_max, list_max, combo_max, nbin) * SR_WARPS;
 }
 
 // Resident CTAs per SM of the class-L kernel with the given dynamic shared memory.
