@@ -281,7 +281,7 @@ __host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_ma
     s.o = b; b += (unsigned)(bc * ncomp_max) * 8u;
     s.wb = b; b += (unsigned)(bc * w_max) * 8u;
     s.lc = b; b += (unsigned)list_max * 8u;
-    s.li = b; b += (unsigned)list_max * 2u;
+    s.li = b; b += (unsigned)list_max * 4u;
     b = (b + 15u) & ~15u;
     s.kc = b; b += (unsigned)combo_max * 8u * 8u;
     s.total = (b + 15u) & ~15u;
@@ -357,7 +357,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     double *O = (double *)(base + sm.o);
     double *Wb = (double *)(base + sm.wb);
     double *Lc = (double *)(base + sm.lc);
-    short *Li = (short *)(base + sm.li);
+    int *Lx = (int *)(base + sm.li);   // packed layout of the coefficient lists (per item)
     double *Kc = (double *)(base + sm.kc);   // [combo][8]
 
     const SRTripleDev tr = A.tri[A.item_tri[item]];
@@ -389,6 +389,20 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
             carry += __shfl_sync(0xffffffffu, inc, 31);
         }
         if (lane == 0) loff[ncm * ncn] = carry;
+    }
+    __syncwarp();
+    // the layout of the coefficient lists is fixed per item: entry kk of the
+    // list of (a, b) is E^x_t E^y_u E^z_v with Hermite index ridx(t, u, v);
+    // packed as ridx | (x offset) << 8 | (y offset) << 16 | (z offset) << 24,
+    // offsets into the x, y, z blocks of a primitive pair's coefficients
+    for (int ab = lane; ab < ncm * ncn; ab += 32) {
+        const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
+        const int ox = eoff_sr(ca[0], cb[0], ln), oy = eoff_sr(ca[1], cb[1], ln), oz = eoff_sr(ca[2], cb[2], ln);
+        int kk = loff[ab];
+        for (int t = 0; t <= ca[0] + cb[0]; t++)
+            for (int u = 0; u <= ca[1] + cb[1]; u++)
+                for (int v = 0; v <= ca[2] + cb[2]; v++, kk++)
+                    Lx[kk] = ridx(t, u, v) | (ox + t) << 8 | (oy + u) << 16 | (oz + v) << 24;
     }
     __syncwarp();
     const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
@@ -637,41 +651,34 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                         const double *Wsrc = Rg;
                         int wstride = NR, cstride = 0;
                         if (lP > 0) {
-                            for (int w = lane; w < nb * ncP * npt; w += 32) {
-                                const int bb = w / (ncP * npt), rem = w - bb * (ncP * npt);
-                                const int ic = rem / npt, pq = rem - ic * npt;
+                            // lanes over (cell, pair-side tuv), the aux components in a
+                            // warp-uniform loop (uniform trip counts and table reads)
+                            for (int w = lane; w < nb * npt; w += 32) {
+                                const int bb = w / npt, pq = w - bb * npt;
                                 int t, u, v;
                                 tuv_of(pq, t, u, v);
-                                const signed char *cc3 = c_cart[lP][ic];
                                 const double *rb = Rg + bb * NR;
-                                double sum = 0.0;
-                                for (int ta2 = cc3[0] & 1; ta2 <= cc3[0]; ta2 += 2)
-                                    for (int ua = cc3[1] & 1; ua <= cc3[1]; ua += 2) {
-                                        const double e2 = Ec[cc3[0] * (LMAX + 1) + ta2] * Ec[cc3[1] * (LMAX + 1) + ua];
-                                        for (int va = cc3[2] & 1; va <= cc3[2]; va += 2)
-                                            sum = fma(e2 * Ec[cc3[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
-                                    }
-                                Wb[w] = sum;
+                                double *wd = Wb + bb * (ncP * npt) + pq;
+                                for (int ic = 0; ic < ncP; ic++) {
+                                    const signed char *cc3 = c_cart[lP][ic];
+                                    double sum = 0.0;
+                                    for (int ta2 = cc3[0] & 1; ta2 <= cc3[0]; ta2 += 2)
+                                        for (int ua = cc3[1] & 1; ua <= cc3[1]; ua += 2) {
+                                            const double e2 = Ec[cc3[0] * (LMAX + 1) + ta2] * Ec[cc3[1] * (LMAX + 1) + ua];
+                                            for (int va = cc3[2] & 1; va <= cc3[2]; va += 2)
+                                                sum = fma(e2 * Ec[cc3[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
+                                        }
+                                    wd[ic * npt] = sum;
+                                }
                             }
                             Wsrc = Wb;
                             wstride = ncP * npt;
                             cstride = npt;
                         }
-                        // (B) pair side: one coefficient list E^x_t E^y_u E^z_v per (a, b)
-                        for (int ab = lane; ab < ncm * ncn; ab += 32) {
-                            const signed char *ca = c_cart[lm][ab / ncn], *cb = c_cart[ln][ab % ncn];
-                            const double *ex0 = Eab + eoff_sr(ca[0], cb[0], ln);
-                            const double *ey0 = Eab + n1 + eoff_sr(ca[1], cb[1], ln);
-                            const double *ez0 = Eab + 2 * n1 + eoff_sr(ca[2], cb[2], ln);
-                            int kk = loff[ab];
-                            for (int t = 0; t <= ca[0] + cb[0]; t++)
-                                for (int u = 0; u <= ca[1] + cb[1]; u++) {
-                                    const double exy = ex0[t] * ey0[u];
-                                    for (int v = 0; v <= ca[2] + cb[2]; v++, kk++) {
-                                        Lc[kk] = exy * ez0[v];
-                                        Li[kk] = (short)ridx(t, u, v);
-                                    }
-                                }
+                        // (B) pair side: the coefficient lists E^x_t E^y_u E^z_v of all (a, b), one entry per lane
+                        for (int kk = lane; kk < loff[ncm * ncn]; kk += 32) {
+                            const int q = Lx[kk];
+                            Lc[kk] = Eab[(q >> 8) & 255] * Eab[n1 + ((q >> 16) & 255)] * Eab[2 * n1 + (q >> 24)];
                         }
                         __syncwarp();
                         // outputs ordered with (a, b) slowest so that neighbouring lanes share list lengths
@@ -683,10 +690,10 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             int kk = loff[ab];
                             const int ke = loff[ab + 1];
                             for (; kk + 1 < ke; kk += 2) {
-                                s0 = fma(Lc[kk], w[Li[kk]], s0);
-                                s1 = fma(Lc[kk + 1], w[Li[kk + 1]], s1);
+                                s0 = fma(Lc[kk], w[Lx[kk] & 255], s0);
+                                s1 = fma(Lc[kk + 1], w[Lx[kk + 1] & 255], s1);
                             }
-                            if (kk < ke) s0 = fma(Lc[kk], w[Li[kk]], s0);
+                            if (kk < ke) s0 = fma(Lc[kk], w[Lx[kk] & 255], s0);
                             const int oo = bb * ncomp + ic * ncm * ncn + ab;
                             O[oo] = fma(pref, s0 + s1, O[oo]);
                         }
