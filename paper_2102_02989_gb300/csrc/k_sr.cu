@@ -426,12 +426,25 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const double L0z = l00 * A.a[2] + l01 * A.a[5] + l02 * A.a[8];
     const double hx = xr0 - L0x, hy = xr1 - L0y, hz = xr2 - L0z;
     const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
-    const float fcut = (float)tr.Rc_cut + 1e-3f;
-    // a lattice-list entry l' can pass |h - l'| <= Rc_cut only if |l'| <= Rc_cut +
-    // |h|: the candidates of this item are a prefix of the length-sorted list,
-    // usually shorter than the triple's (which assumes the largest |h|)
-    int nsph = tr.nsph;
-    {
+    const double *win = A.win + tr.win_off;
+    // the exact test below keeps a translation at distance Rc only if the
+    // cutoff win[min(floor(Rc / DR), nwin - 1)] of its window admits this
+    // pair's R12: beyond the last window that does (wlast), nothing is kept,
+    // so unless that is the open-ended last window the candidates need only
+    // reach (wlast + 1) DR (none at all when no window admits R12)
+    int wlast = -1;
+    for (int w0 = ((tr.nwin - 1) >> 5) << 5; w0 >= 0 && wlast < 0; w0 -= 32) {
+        const int w = w0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, w < tr.nwin && R12 <= win[min(w, tr.nwin - 1)]);
+        if (m) wlast = w0 + 31 - __clz(m);
+    }
+    const double rcut = wlast == tr.nwin - 1 ? tr.Rc_cut : min(tr.Rc_cut, (wlast + 1) * SCREEN_DR);
+    const float fcut = (float)rcut + 1e-3f;
+    // a lattice-list entry l' can pass |h - l'| <= Rc only if |l'| <= Rc + |h|:
+    // the candidates of this item are a prefix of the length-sorted list,
+    // usually shorter than the triple's (which assumes the largest |h| and R12)
+    int nsph = 0;
+    if (wlast >= 0) {
         const float lim = fcut + sqrtf(fx * fx + fy * fy + fz * fz) + 1e-3f;
         int lo = 0, hi = tr.nsph;   // first entry longer than lim in [lo, hi]
         while (lo < hi) {
@@ -441,7 +454,6 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         nsph = lo;
     }
     const int dt = bvk_bin(d0, d1, d2, A.nk);
-    const double *win = A.win + tr.win_off;
     const double Rc2 = tr.Rc_cut * tr.Rc_cut;
 
     // constants of every primitive combination (k; i, j), one lane each:
@@ -452,7 +464,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     const int npp = A.ao.nprim[mu] * A.ao.nprim[nu];
     const int ncombo_all = A.ax.nprim[P] * npp;
     int ncombo = 0;
-    for (int cb0 = 0; cb0 < ncombo_all; cb0 += 32) {
+    for (int cb0 = 0; nsph > 0 && cb0 < ncombo_all; cb0 += 32) {   // (no candidates: no combinations)
         const int cb = cb0 + lane;
         bool keep = false;
         double kv[7];
