@@ -326,6 +326,7 @@ struct SRSetup {
     float *feat = nullptr, *pred = nullptr;
     unsigned char *skip = nullptr;
     unsigned long long *counts = nullptr;
+    SRItemGeom *geom = nullptr;      // per-item geometry, written by sr_pre
     long long n_items = 0;
     int ntri = 0;
     bool skip_sr = false;
@@ -410,6 +411,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     double *dccon;
     float *dcbnd;
     RC(S.upload(ditem_tri, item_tri));
+    RC(S.alloc(R.geom, (size_t)std::max(plan.n_items, 1LL)));
     RC(S.upload(dccon, ccon));
     RC(S.upload(dcbnd, cbnd));
     // Hermite tables of every (pair, d, primitive pair) of the SR d lists,
@@ -465,6 +467,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.sphvf = dsphvf;
     A.sphlen = dsphlen;
     A.item_tri = ditem_tri;
+    A.geom = R.geom;
     A.ccon = dccon;
     A.cbnd = dcbnd;
     fill_lattice(L, A.a, A.bq, A.nk);
@@ -542,8 +545,9 @@ static int sr_pre(const SRSetup &R, cudaStream_t st, int &nl)
     if (R.ntri == 0) return RSGDF_OK;
     t_timer.begin(PH_SR);
     RC(launch_pair_prep(R.ao, R.nshell, R.dent, R.nent, R.ddl, R.da9, R.ptab, nullptr, nullptr, nullptr, st));
+    RC(launch_sr_item_geom(R.A, R.n_items, R.geom, st));
     t_timer.end();
-    nl++;
+    nl += 2;
     if (R.feat && R.n_items > 0) {
         t_timer.begin(PH_OTHER);
         RC(launch_sr_features(R.A, R.feat, st));

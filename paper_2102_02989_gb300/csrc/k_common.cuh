@@ -34,6 +34,21 @@ struct SRTripleDev {
     double log10A, beta, eta1, eta2, aP;
 };
 
+// Geometry of one SR work item (aux shell P, AO shell pair, lattice vector d),
+// one record per item, computed before the SR launches by one thread per item:
+// L0 is the lattice vector nearest to (pair centre - C_P) and h the rest, R12
+// the pair separation; the candidates of the item are the first nsph entries
+// of the length-sorted lattice list, pre-filtered at the FP32 radius fcut.
+struct SRItemGeom {
+    double h[3], L0[3], R12;
+    float fcut;
+    int nsph;
+    int l0[3];       // L0 in lattice coordinates
+    int gd, dt;      // global d index, BvK cell of d
+    int pad[3];
+};
+static_assert(sizeof(SRItemGeom) == 96, "SRItemGeom is six 16-byte words");
+
 struct SRArgs {
     DevShells ao, ax;
     const SRTripleDev *tri;
@@ -45,6 +60,7 @@ struct SRArgs {
     const float *sphvf;               // the same in FP32 (pre-filter)
     const float *sphlen;              // their lengths (ascending), FP32
     const int *item_tri;              // [n_items] triple of each work item
+    const SRItemGeom *geom;           // [n_items] geometry of each work item
     const double *ccon;               // per (triple, combination) [4]: alpha, s, sqrt s, prefactor (d-independent)
     const float *cbnd;                // per (triple, combination): d-independent part of the log Coulomb bound
     double a[9];    // lattice vectors (rows)
@@ -96,6 +112,7 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
 // rows (BvK cell x primitive combination) of Hermite sums a warp holds for a bin chunk bc:
 // room for up to 4 combinations at once when the chunk is small
 __host__ __device__ constexpr int sr_rb_rows(int bc) { return 4 * bc < 32 ? 4 * bc : (bc > 32 ? bc : 32); }
+int launch_sr_item_geom(const SRArgs &A, long long n_items, SRItemGeom *out, cudaStream_t st);
 size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);
 size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);
 int sr_occupancy(int L, size_t smem);

@@ -250,7 +250,8 @@ constexpr int SR_WARPS = 2;
 constexpr int SR_NT = 256;   // translations buffered per segment (flush above SR_NT - 64)
 constexpr int SR_MAXCOMBO = 64;
 constexpr int SR_GMAX = 4;   // primitive combinations summed at once in the term loop
-constexpr int SR_SKIP_ST_HI = 0x40518000;   // top word of 70.0: erfc terms with s T >= 70 vanish
+constexpr int SR_SKIP_ST_HI = 0x40518000;
+constexpr float FLT_U = 5.9604645e-8f;       // 2^-24, unit roundoff of FP32   // top word of 70.0: erfc terms with s T >= 70 vanish
 
 // Per-warp shared memory of the SR kernel, one layout for the host (sizes)
 // and the device (carving); offsets in bytes from the warp's base:
@@ -334,6 +335,72 @@ __device__ __forceinline__ void tuv_of(int p, int &t, int &u, int &v)
     t = S - w;
 }
 
+// Geometry of the work items, one thread per item (SRItemGeom).  The exact
+// test of a translation at distance Rc keeps it only if the cutoff
+// win[min(floor(Rc / DR), nwin - 1)] of its window admits the pair's R12:
+// beyond the last window that does (wlast) nothing is kept, so unless that is
+// the open-ended last window the candidates need only reach (wlast + 1) DR
+// (none at all when no window admits R12).  A lattice-list entry l' can pass
+// |h - l'| <= Rc only if |l'| <= Rc + |h|: the candidates are a prefix of the
+// length-sorted list, usually shorter than the triple's (which assumes the
+// largest |h| and R12).
+__global__ void k_sr_item_geom(const SRArgs A, long long n_items, SRItemGeom *__restrict__ out)
+{
+    const long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (item >= n_items) return;
+    const SRTripleDev &tr = A.tri[A.item_tri[item]];
+    const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);
+    const int P = tr.P, mu = tr.mu, nu = tr.nu;
+    const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
+    const double Ax = A.ao.cen[3 * mu], Ay = A.ao.cen[3 * mu + 1], Az = A.ao.cen[3 * mu + 2];
+    const double Bx = A.ao.cen[3 * nu] + d0 * A.a[0] + d1 * A.a[3] + d2 * A.a[6];
+    const double By = A.ao.cen[3 * nu + 1] + d0 * A.a[1] + d1 * A.a[4] + d2 * A.a[7];
+    const double Bz = A.ao.cen[3 * nu + 2] + d0 * A.a[2] + d1 * A.a[5] + d2 * A.a[8];
+    const double Cx = A.ax.cen[3 * P], Cy = A.ax.cen[3 * P + 1], Cz = A.ax.cen[3 * P + 2];
+    const double R12 = sqrt((Bx - Ax) * (Bx - Ax) + (By - Ay) * (By - Ay) + (Bz - Az) * (Bz - Az));
+    const double iw = 1.0 / (tr.amu + tr.anu);
+    const double xr0 = (tr.amu * Ax + tr.anu * Bx) * iw - Cx;
+    const double xr1 = (tr.amu * Ay + tr.anu * By) * iw - Cy;
+    const double xr2 = (tr.amu * Az + tr.anu * Bz) * iw - Cz;
+    SRItemGeom g;
+    g.l0[0] = __double2int_rn(xr0 * A.bq[0] + xr1 * A.bq[1] + xr2 * A.bq[2]);
+    g.l0[1] = __double2int_rn(xr0 * A.bq[3] + xr1 * A.bq[4] + xr2 * A.bq[5]);
+    g.l0[2] = __double2int_rn(xr0 * A.bq[6] + xr1 * A.bq[7] + xr2 * A.bq[8]);
+    for (int x = 0; x < 3; x++) g.L0[x] = g.l0[0] * A.a[x] + g.l0[1] * A.a[3 + x] + g.l0[2] * A.a[6 + x];
+    g.h[0] = xr0 - g.L0[0];
+    g.h[1] = xr1 - g.L0[1];
+    g.h[2] = xr2 - g.L0[2];
+    g.R12 = R12;
+    const double *win = A.win + tr.win_off;
+    int wlast = tr.nwin - 1;
+    while (wlast >= 0 && !(R12 <= win[wlast])) wlast--;
+    const double rcut = wlast == tr.nwin - 1 ? tr.Rc_cut : min(tr.Rc_cut, (wlast + 1) * SCREEN_DR);
+    g.fcut = (float)rcut + 1e-3f;
+    int nsph = 0;
+    if (wlast >= 0) {
+        const float fx = (float)g.h[0], fy = (float)g.h[1], fz = (float)g.h[2];
+        const float lim = g.fcut + sqrtf(fx * fx + fy * fy + fz * fz) + 1e-3f;
+        int lo = 0, hi = tr.nsph;   // first entry longer than lim in [lo, hi]
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A.sphlen[mid] <= lim) lo = mid + 1; else hi = mid;
+        }
+        nsph = lo;
+    }
+    g.nsph = nsph;
+    g.gd = gd;
+    g.dt = bvk_bin(d0, d1, d2, A.nk);
+    g.pad[0] = g.pad[1] = g.pad[2] = 0;
+    out[item] = g;
+}
+
+int launch_sr_item_geom(const SRArgs &A, long long n_items, SRItemGeom *out, cudaStream_t st)
+{
+    if (n_items <= 0) return RSGDF_OK;
+    k_sr_item_geom<<<(unsigned)((n_items + 127) / 128), 128, 0, st>>>(A, n_items, out);
+    return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
+}
+
 // One SR work item (aux shell, AO shell pair, d) by one warp; base is the
 // warp's shared-memory region (laid out from A's bc, ncomp_max, w_max and
 // list_max).  Every branch on the item is warp-uniform.
@@ -360,8 +427,9 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     int *Lx = (int *)(base + sm.li);   // packed layout of the coefficient lists (per item)
     double *Kc = (double *)(base + sm.kc);   // [combo][8]
 
+    const SRItemGeom G = A.geom[item];
     const SRTripleDev tr = A.tri[A.item_tri[item]];
-    const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);   // global d index
+    const int gd = G.gd;   // global d index
     const int P = tr.P, mu = tr.mu, nu = tr.nu;
     const int lP = A.ax.l[P], lm = A.ao.l[mu], ln = A.ao.l[nu];
     const int ncP = (lP + 1) * (lP + 2) / 2, ncm = (lm + 1) * (lm + 2) / 2, ncn = (ln + 1) * (ln + 2) / 2;
@@ -405,56 +473,27 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                     Lx[kk] = ridx(t, u, v) | (ox + t) << 8 | (oy + u) << 16 | (oz + v) << 24;
     }
     __syncwarp();
-    const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
-    const double Ax = A.ao.cen[3 * mu], Ay = A.ao.cen[3 * mu + 1], Az = A.ao.cen[3 * mu + 2];
-    const double Bx = A.ao.cen[3 * nu] + d0 * A.a[0] + d1 * A.a[3] + d2 * A.a[6];
-    const double By = A.ao.cen[3 * nu + 1] + d0 * A.a[1] + d1 * A.a[4] + d2 * A.a[7];
-    const double Bz = A.ao.cen[3 * nu + 2] + d0 * A.a[2] + d1 * A.a[5] + d2 * A.a[8];
     const double Cx = A.ax.cen[3 * P], Cy = A.ax.cen[3 * P + 1], Cz = A.ax.cen[3 * P + 2];
-    const double R12 = sqrt((Bx - Ax) * (Bx - Ax) + (By - Ay) * (By - Ay) + (Bz - Az) * (Bz - Az));
-    const double iw = 1.0 / (tr.amu + tr.anu);
-    const double xr0 = (tr.amu * Ax + tr.anu * Bx) * iw - Cx;
-    const double xr1 = (tr.amu * Ay + tr.anu * By) * iw - Cy;
-    const double xr2 = (tr.amu * Az + tr.anu * Bz) * iw - Cz;
-    const int l00 = __double2int_rn(xr0 * A.bq[0] + xr1 * A.bq[1] + xr2 * A.bq[2]);
-    const int l01 = __double2int_rn(xr0 * A.bq[3] + xr1 * A.bq[4] + xr2 * A.bq[5]);
-    const int l02 = __double2int_rn(xr0 * A.bq[6] + xr1 * A.bq[7] + xr2 * A.bq[8]);
+    const double R12 = G.R12;
+    const int l00 = G.l0[0], l01 = G.l0[1], l02 = G.l0[2];
     // candidate translations l = L0 + (an entry of the length-sorted lattice
     // list): h = (pair centre - C) - L0 once per item, then h - l' per entry
-    const double L0x = l00 * A.a[0] + l01 * A.a[3] + l02 * A.a[6];
-    const double L0y = l00 * A.a[1] + l01 * A.a[4] + l02 * A.a[7];
-    const double L0z = l00 * A.a[2] + l01 * A.a[5] + l02 * A.a[8];
-    const double hx = xr0 - L0x, hy = xr1 - L0y, hz = xr2 - L0z;
+    const double L0x = G.L0[0], L0y = G.L0[1], L0z = G.L0[2];
+    const double hx = G.h[0], hy = G.h[1], hz = G.h[2];
     const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
     const double *win = A.win + tr.win_off;
-    // the exact test below keeps a translation at distance Rc only if the
-    // cutoff win[min(floor(Rc / DR), nwin - 1)] of its window admits this
-    // pair's R12: beyond the last window that does (wlast), nothing is kept,
-    // so unless that is the open-ended last window the candidates need only
-    // reach (wlast + 1) DR (none at all when no window admits R12)
-    int wlast = -1;
-    for (int w0 = ((tr.nwin - 1) >> 5) << 5; w0 >= 0 && wlast < 0; w0 -= 32) {
-        const int w = w0 + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, w < tr.nwin && R12 <= win[min(w, tr.nwin - 1)]);
-        if (m) wlast = w0 + 31 - __clz(m);
-    }
-    const double rcut = wlast == tr.nwin - 1 ? tr.Rc_cut : min(tr.Rc_cut, (wlast + 1) * SCREEN_DR);
-    const float fcut = (float)rcut + 1e-3f;
-    // a lattice-list entry l' can pass |h - l'| <= Rc only if |l'| <= Rc + |h|:
-    // the candidates of this item are a prefix of the length-sorted list,
-    // usually shorter than the triple's (which assumes the largest |h| and R12)
-    int nsph = 0;
-    if (wlast >= 0) {
-        const float lim = fcut + sqrtf(fx * fx + fy * fy + fz * fz) + 1e-3f;
-        int lo = 0, hi = tr.nsph;   // first entry longer than lim in [lo, hi]
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (A.sphlen[mid] <= lim) lo = mid + 1; else hi = mid;
-        }
-        nsph = lo;
-    }
-    const int dt = bvk_bin(d0, d1, d2, A.nk);
+    const float fcut = G.fcut;
+    const int nsph = G.nsph;
+    const int dt = G.dt;
     const double Rc2 = tr.Rc_cut * tr.Rc_cut;
+    // FP32 squared distances |h - l'|^2 of candidates (|h - l'| <= fcut, |l'| <= lim):
+    // each component carries at most 2u(|h_x| + |l'_x|)(1 + u) of error from the
+    // roundings of h, l' and the difference (u = 2^-24), so the sum of squares is
+    // off by at most 4u fcut (|h| + lim) + 3u fcut^2 plus O(u^2); e2f doubles that
+    const float hf = sqrtf(fx * fx + fy * fy + fz * fz);
+    const float e2f = 8.0f * FLT_U * fcut * (hf + fcut + 1e-3f + hf + fcut);
+    const float rc2f = (float)Rc2;
+    const float rc2f_lo = rc2f * (1.0f - 4.0f * FLT_U), rc2f_hi = rc2f * (1.0f + 4.0f * FLT_U);
 
     // constants of every primitive combination (k; i, j), one lane each:
     // alpha, s = w^2/(w^2+alpha), sqrt(s), prefactor, product centre - C,
@@ -517,25 +556,34 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
         __syncwarp();
         const bool lastround = (b0 + 32 >= nsph);
         if (nq < 32 && !lastround) continue;
-        // exact FP64 test of up to 64 queued candidates, 32 at a time
+        // exact test of up to 64 queued candidates, 32 at a time: Rc <= Rc_cut and
+        // the window floor(Rc / DR), decided from the FP32 distance wherever its
+        // error bound e2f leaves no doubt, else from the FP64 distance
         for (int q0 = 0; q0 < nq; q0 += 32) {
         const int qi = q0 + lane;
         bool acc = false;
         int ci = 0;
         if (qi < nq) {
             ci = Qd[qi];
-            const double r0 = hx - A.sphv[3 * ci], r1 = hy - A.sphv[3 * ci + 1], r2 = hz - A.sphv[3 * ci + 2];
-            const double rc2 = r0 * r0 + r1 * r1 + r2 * r2;
-            if (rc2 <= Rc2) {
-                // window floor(Rc / DR) from a float square root; in FP64 only
-                // where the float value lies within 1e-4 of a window boundary
-                const float q = sqrtf(top_float(rc2)) * (float)(1.0 / SCREEN_DR);
-                int w = (int)q;
-                const float fr = q - (float)w;
-                if (fr < 1e-4f || fr > 1.0f - 1e-4f) w = (int)floor(sqrt(rc2) * (1.0 / SCREEN_DR));
-                if (w >= tr.nwin) w = tr.nwin - 1;
-                acc = (R12 <= win[w]);
+            const float ex = fx - A.sphvf[3 * ci], ey = fy - A.sphvf[3 * ci + 1], ez = fz - A.sphvf[3 * ci + 2];
+            const float r2f = ex * ex + ey * ey + ez * ez;
+            const float lo = fmaxf(r2f - e2f, 0.0f), hi = r2f + e2f;
+            int w = -1;   // window of the translation, -1 beyond Rc_cut
+            bool known = lo > rc2f_hi;   // surely beyond Rc_cut
+            if (!known && hi <= rc2f_lo) {   // surely within: the window unless an edge lies in [lo, hi]
+                const int wl = (int)(sqrtf(lo) * (float)(1.0 / SCREEN_DR) * (1.0f - 4.0f * FLT_U));
+                const int wh = (int)(sqrtf(hi) * (float)(1.0 / SCREEN_DR) * (1.0f + 4.0f * FLT_U));
+                if (wl == wh) {
+                    w = wl;
+                    known = true;
+                }
             }
+            if (!known) {
+                const double r0 = hx - A.sphv[3 * ci], r1 = hy - A.sphv[3 * ci + 1], r2 = hz - A.sphv[3 * ci + 2];
+                const double rc2 = r0 * r0 + r1 * r1 + r2 * r2;
+                if (rc2 <= Rc2) w = (int)floor(sqrt(rc2) * (1.0 / SCREEN_DR));
+            }
+            if (w >= 0) acc = (R12 <= win[min(w, tr.nwin - 1)]);
         }
         const unsigned m = __ballot_sync(0xffffffffu, acc);
         if (acc) {
