@@ -111,7 +111,8 @@ int upload_boys_table(const double *tab, cudaStream_t st);
 int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max);
 // rows (BvK cell x primitive combination) of Hermite sums a warp holds for a bin chunk bc:
 // room for up to 4 combinations at once when the chunk is small
-__host__ __device__ constexpr int sr_rb_rows(int bc) { return 4 * bc < 32 ? 4 * bc : (bc > 32 ? bc : 32); }
+// rows of Hermite sums per warp in the SR kernel: one per lane and the zero row of empty cells
+__host__ __device__ constexpr int sr_rb_rows(int) { return 33; }
 int launch_sr_item_geom(const SRArgs &A, long long n_items, SRItemGeom *out, cudaStream_t st);
 size_t sr_warp_bytes(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);
 size_t sr_launch_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin);

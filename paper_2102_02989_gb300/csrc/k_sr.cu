@@ -255,20 +255,20 @@ constexpr float FLT_U = 5.9604645e-8f;       // 2^-24, unit roundoff of FP32   /
 
 // Per-warp shared memory of the SR kernel, one layout for the host (sizes)
 // and the device (carving); offsets in bytes from the warp's base:
-// translations sorted by BvK cell (positions and cells), the collected
-// translations (index into the lattice list and cell), bin counters,
-// coefficient-list offsets, the FP32 survivor queue, the Hermite
-// coefficients of the current primitive combination, Hermite sums per cell,
-// contracted blocks, coefficient lists, and the per-combination constants.
+// translation positions sorted by BvK cell, the collected translations
+// (index into the lattice list and cell), bin counters (then the row table
+// of the cells), coefficient-list offsets, the FP32 survivor queue, the
+// Hermite coefficients of the current primitive combination, Hermite sums
+// (a row per lane and a zero row), contracted blocks, coefficient lists, and
+// the per-combination constants.
 struct SRSmem {
-    unsigned sx, sb, tq, tb, cnt, fill, loff, qd, eab, ec, rb, o, wb, lc, li, kc, total;
+    unsigned sx, tq, tb, cnt, fill, loff, qd, eab, ec, rb, o, wb, lc, li, kc, total;
 };
 __host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_max, int list_max, int combo_max, int nbin)
 {
     SRSmem s;
     unsigned b = 0;
     s.sx = b; b += 3u * SR_NT * 8u;
-    s.sb = b; b += SR_NT * 4u;
     s.tq = b; b += SR_NT * 4u;
     s.tb = b; b += SR_NT * 4u;
     s.cnt = b; b += (unsigned)(nbin + 4) * 4u;
@@ -333,6 +333,13 @@ __device__ __forceinline__ void tuv_of(int p, int &t, int &u, int &v)
     v = q - w * (w + 1) / 2;
     u = w - v;
     t = S - w;
+}
+
+// Row of the Hermite sums of cell bb for group g of Lg lanes, from the cell's
+// row-table entry (first lane | lanes << 8, or -1 for an empty cell: the zero row 32).
+__device__ __forceinline__ int sr_cell_row(int rt, int g, int Lg)
+{
+    return rt < 0 ? 32 : g * Lg + (rt & 255);
 }
 
 // Geometry of the work items, one thread per item (SRItemGeom).  The exact
@@ -411,7 +418,6 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     constexpr int NR = ntuv(L);
     const SRSmem sm = sr_smem(L, A.bc, A.ncomp_max, A.w_max, A.list_max, A.combo_max, A.nbin_max);
     double *Sx = (double *)(base + sm.sx), *Sy = Sx + SR_NT, *Sz = Sy + SR_NT;   // sorted by BvK cell
-    int *Sb = (int *)(base + sm.sb);
     int *Tq = (int *)(base + sm.tq);   // collected: index into the lattice list
     int *Tb = (int *)(base + sm.tb);   // collected: BvK cell
     int *cnt = (int *)(base + sm.cnt);
@@ -619,7 +625,6 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                     Sx[dst] = L0x + A.sphv[3 * ci];
                     Sy[dst] = L0y + A.sphv[3 * ci + 1];
                     Sz[dst] = L0z + A.sphv[3 * ci + 2];
-                    Sb[dst] = bin;
                 }
                 __syncwarp();
                 if (t < nT && (peers & act & ((1u << lane) - 1u)) == 0) fill[bin] += __popc(peers & act);
@@ -631,55 +636,71 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                 const int r0 = cnt[c0], r1 = cnt[c0 + nb];
                 if (r0 == r1) continue;
                 for (int o = lane; o < nb * ncomp; o += 32) O[o] = 0.0;
-                // G primitive combinations at a time, each on 32/G lanes with its
-                // own rows of Hermite sums: G minimises the warp rounds of the
-                // term loop (a chunk holds ~tens of translations, fewer than 32
-                // lanes per combination would leave idle)
-                const int nTc = r1 - r0;
-                int G = 1;
+                // G primitive combinations at a time, each on Lg = 32/G lanes.  The
+                // lanes of a combination are spread over the cells of the chunk:
+                // cell b (n_b translations) gets k_b = ceil(n_b / R) lanes, R the
+                // fewest rounds with sum_b k_b <= Lg, and a lane strides through
+                // the translations of its own cell.  Every lane leaves its Hermite
+                // sums in a row of its own (row = lane); the rows of one cell are
+                // then added into its first.  G minimises ceil(ncombo / G) R.
+                const int nbv = lane < nb ? cnt[c0 + lane + 1] - cnt[c0 + lane] : 0;
+                const int nz = __popc(__ballot_sync(0xffffffffu, nbv > 0));
+                const int nmax = __reduce_max_sync(0xffffffffu, nbv);
+                int G = 1, Rr = nmax;
                 {
-                    long long best = (long long)ncombo * ((nTc + 31) >> 5);
-                    for (int g2 = 2; g2 <= SR_GMAX && g2 * nb <= sr_rb_rows(A.bc); g2 *= 2) {
+                    long long best = -1;
+                    for (int g2 = 1; g2 <= SR_GMAX; g2 *= 2) {
                         const int lg = 32 / g2;
-                        const long long rounds = (long long)((ncombo + g2 - 1) / g2) * ((nTc + lg - 1) / lg);
-                        if (rounds < best) {
+                        if (nz > lg) continue;   // every non-empty cell needs a lane
+                        int lo = 1, hi = nmax;   // sum_b ceil(n_b / hi) = nz <= lg
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (__reduce_add_sync(0xffffffffu, (nbv + mid - 1) / mid) <= lg) hi = mid; else lo = mid + 1;
+                        }
+                        const long long rounds = (long long)((ncombo + g2 - 1) / g2) * lo;
+                        if (best < 0 || rounds < best) {
                             best = rounds;
                             G = g2;
+                            Rr = lo;
                         }
                     }
                 }
                 const int Lg = 32 / G;
                 const int grp = lane / Lg, sub = lane - grp * Lg;
+                const int kb = (nbv + Rr - 1) / Rr;   // lanes of cell `lane` (lane < nb)
+                int ls = kb;                          // -> first lane of cell `lane`
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, ls, o);
+                    if (lane >= o) ls += y;
+                }
+                ls -= kb;
+                // row table of the cells: first lane | lanes << 8, or -1 (empty cell)
+                if (lane < nb) fill[lane] = kb > 0 ? (ls | kb << 8) : -1;
+                int mybin = -1, myj = 0, myk = 0;   // this lane's cell, rank among its lanes, their count
+                for (int b2 = 0; b2 < nb; b2++) {
+                    const int kbb = __shfl_sync(0xffffffffu, kb, b2), lsb = __shfl_sync(0xffffffffu, ls, b2);
+                    if (sub >= lsb && sub < lsb + kbb) {
+                        mybin = b2;
+                        myj = sub - lsb;
+                        myk = kbb;
+                    }
+                }
+                for (int q = lane; q < NR; q += 32) Rb[32 * NR + q] = 0.0;   // the row of an empty cell
+                __syncwarp();
                 for (int cg = 0; cg < ncombo; cg += G) {
-                    for (int o = lane; o < G * nb * NR; o += 32) Rb[o] = 0.0;
-                    __syncwarp();
                     const int cmy = cg + grp;
-                    if (cmy < ncombo) {
+                    if (cmy < ncombo && mybin >= 0) {
                         const double *kc = Kc + 8 * cmy;
                         const double alpha = kc[0], s = kc[1];
                         double cw[2 * L + 2];
                         erfc_consts<L>(alpha, s, kc[2], cw);
                         const double Px = kc[4], Py = kc[5], Pz = kc[6];
-                        double *Rg = Rb + grp * nb * NR;
-                        // contiguous slice of the sorted translations per lane of the group
-                        const int per = (nTc + Lg - 1) / Lg;
-                        const int ta = r0 + sub * per, tb = min(ta + per, r1);
                         double accR[NR];
 #pragma unroll
                         for (int q = 0; q < NR; q++) accR[q] = 0.0;
-                        int cur = -1;
-                        for (int tt = ta; tt < tb; tt++) {
-                            const int bn = Sb[tt];
-                            if (bn != cur) {
-                                if (cur >= 0) {
-#pragma unroll
-                                    for (int q = 0; q < NR; q++) {
-                                        atomicAdd(&Rg[(cur - c0) * NR + q], accR[q]);
-                                        accR[q] = 0.0;
-                                    }
-                                }
-                                cur = bn;
-                            }
+                        const int te = cnt[c0 + mybin + 1];
+                        for (int tt = cnt[c0 + mybin] + myj; tt < te; tt += myk) {
                             const double X = Px - Sx[tt], Y = Py - Sy[tt], Z = Pz - Sz[tt];
                             const double R2 = X * X + Y * Y + Z * Z;
                             const double T = alpha * R2;
@@ -690,9 +711,19 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                             if (__double2hiint(sT) >= SR_SKIP_ST_HI) continue;
                             hermite_acc<L>(T, sT, R2, cw, X, Y, Z, accR);
                         }
-                        if (cur >= 0) {
+                        double *row = Rb + lane * NR;
 #pragma unroll
-                            for (int q = 0; q < NR; q++) atomicAdd(&Rg[(cur - c0) * NR + q], accR[q]);
+                        for (int q = 0; q < NR; q++) row[q] = accR[q];
+                    }
+                    __syncwarp();
+                    for (int o = lane; o < G * nb * NR; o += 32) {
+                        const int g = o / (nb * NR), rem = o - g * (nb * NR), bb = rem / NR, q = rem - bb * NR;
+                        const int rt = fill[bb];
+                        if (cg + g < ncombo && rt >= 0 && (rt >> 8) > 1) {
+                            double *r0p = Rb + (g * Lg + (rt & 255)) * NR + q;
+                            double sum = r0p[0];
+                            for (int i = 1; i < (rt >> 8); i++) sum += r0p[i * NR];
+                            r0p[0] = sum;
                         }
                     }
                     __syncwarp();
@@ -706,10 +737,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                         for (int e = lane; e < 3 * n1; e += 32) Eab[e] = en[ENT_HDR + e];
                         __syncwarp();
                         const double pref = Kc[8 * cc + 3];
-                        const double *Rg = Rb + gg * nb * NR;
                         // (A) aux side: W[bb][c][tuv] = sum E^c_tau E^c_upsilon E^c_phi R[t+tau, u+upsilon, v+phi]
-                        const double *Wsrc = Rg;
-                        int wstride = NR, cstride = 0;
                         if (lP > 0) {
                             // lanes over (cell, pair-side tuv), the aux components in a
                             // warp-uniform loop (uniform trip counts and table reads)
@@ -717,7 +745,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                 const int bb = w / npt, pq = w - bb * npt;
                                 int t, u, v;
                                 tuv_of(pq, t, u, v);
-                                const double *rb = Rg + bb * NR;
+                                const double *rb = Rb + sr_cell_row(fill[bb], gg, Lg) * NR;
                                 double *wd = Wb + bb * (ncP * npt) + pq;
                                 for (int ic = 0; ic < ncP; ic++) {
                                     const signed char *cc3 = c_cart[lP][ic];
@@ -731,9 +759,6 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                     wd[ic * npt] = sum;
                                 }
                             }
-                            Wsrc = Wb;
-                            wstride = ncP * npt;
-                            cstride = npt;
                         }
                         // (B) pair side: the coefficient lists E^x_t E^y_u E^z_v of all (a, b), one entry per lane
                         for (int kk = lane; kk < loff[ncm * ncn]; kk += 32) {
@@ -745,7 +770,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                         for (int o = lane; o < nb * ncomp; o += 32) {
                             const int ab = o / (nb * ncP), rem = o - ab * (nb * ncP);
                             const int bb = rem / ncP, ic = rem - bb * ncP;
-                            const double *w = Wsrc + bb * wstride + ic * cstride;
+                            const double *w = lP > 0 ? Wb + (bb * ncP + ic) * npt : Rb + sr_cell_row(fill[bb], gg, Lg) * NR;
                             double s0 = 0.0, s1 = 0.0;
                             int kk = loff[ab];
                             const int ke = loff[ab + 1];
