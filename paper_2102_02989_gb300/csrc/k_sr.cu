@@ -246,6 +246,9 @@ __device__ __forceinline__ int eoff_sr(int a, int b, int ln)
 
 constexpr int EAB_SZ = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 2) / 2 * 1;   // >= pair_e1(LMAX, LMAX) = 64
 constexpr int EC_SZ = (LMAX + 1) * (LMAX + 1);
+// products E^c_tau E^c_upsilon E^c_phi over the aux components c of one shell
+// (tau, upsilon, phi of the parities of c): at most 19 for l <= 3
+constexpr int SR_E3_MAX = 32;
 constexpr int SR_WARPS = 2;
 constexpr int SR_NT = 256;   // translations buffered per segment (flush above SR_NT - 64)
 constexpr int SR_MAXCOMBO = 64;
@@ -277,7 +280,7 @@ __host__ __device__ inline SRSmem sr_smem(int L, int bc, int ncomp_max, int w_ma
     s.qd = b; b += 64u * 4u;
     b = (b + 15u) & ~15u;
     s.eab = b; b += 3u * EAB_SZ * 8u;
-    s.ec = b; b += EC_SZ * 8u;
+    s.ec = b; b += SR_E3_MAX * 8u;
     s.rb = b; b += (unsigned)(sr_rb_rows(bc) * ntuv(L)) * 8u;
     s.o = b; b += (unsigned)(bc * ncomp_max) * 8u;
     s.wb = b; b += (unsigned)(bc * w_max) * 8u;
@@ -425,7 +428,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     int *loff = (int *)(base + sm.loff);
     int *Qd = (int *)(base + sm.qd);
     double *Eab = (double *)(base + sm.eab);
-    double *Ec = (double *)(base + sm.ec);
+    double *E3 = (double *)(base + sm.ec);   // aux-side coefficient products
     double *Rb = (double *)(base + sm.rb);
     double *O = (double *)(base + sm.o);
     double *Wb = (double *)(base + sm.wb);
@@ -731,7 +734,27 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                     for (int gg = 0; gg < G && cg + gg < ncombo; gg++) {
                         const int cc = cg + gg, cb = (int)Kc[8 * cc + 7], k = cb / npp, ij = cb - k * npp;
                         const int ok = A.ax.poff[P] + k;
-                        for (int e = lane; e < EC_SZ; e += 32) Ec[e] = A.ec_tab[ok * EC_SZ + e];
+                        if (lP > 0) {
+                            // E3: the products E^c_tau E^c_upsilon E^c_phi of every aux
+                            // component c, one component per lane, in the order in
+                            // which the sums of (A) use them
+                            const double *ect = A.ec_tab + ok * EC_SZ;
+                            const signed char *c3 = c_cart[lP][min(lane, ncP - 1)];
+                            const int nt3 = lane < ncP ? (c3[0] / 2 + 1) * (c3[1] / 2 + 1) * (c3[2] / 2 + 1) : 0;
+                            int e3 = nt3;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(0xffffffffu, e3, o);
+                                if (lane >= o) e3 += y;
+                            }
+                            e3 -= nt3;
+                            if (lane < ncP)
+                                for (int ta2 = c3[0] & 1; ta2 <= c3[0]; ta2 += 2)
+                                    for (int ua = c3[1] & 1; ua <= c3[1]; ua += 2) {
+                                        const double e2 = ect[c3[0] * (LMAX + 1) + ta2] * ect[c3[1] * (LMAX + 1) + ua];
+                                        for (int va = c3[2] & 1; va <= c3[2]; va += 2) E3[e3++] = e2 * ect[c3[2] * (LMAX + 1) + va];
+                                    }
+                        }
                         // Hermite coefficients of (d, primitive pair)
                         const double *en = A.ptab + A.sr_doff[gd] + (long long)ij * (ENT_HDR + 3 * n1);
                         for (int e = lane; e < 3 * n1; e += 32) Eab[e] = en[ENT_HDR + e];
@@ -747,15 +770,14 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
                                 tuv_of(pq, t, u, v);
                                 const double *rb = Rb + sr_cell_row(fill[bb], gg, Lg) * NR;
                                 double *wd = Wb + bb * (ncP * npt) + pq;
+                                int e3 = 0;
                                 for (int ic = 0; ic < ncP; ic++) {
                                     const signed char *cc3 = c_cart[lP][ic];
                                     double sum = 0.0;
                                     for (int ta2 = cc3[0] & 1; ta2 <= cc3[0]; ta2 += 2)
-                                        for (int ua = cc3[1] & 1; ua <= cc3[1]; ua += 2) {
-                                            const double e2 = Ec[cc3[0] * (LMAX + 1) + ta2] * Ec[cc3[1] * (LMAX + 1) + ua];
+                                        for (int ua = cc3[1] & 1; ua <= cc3[1]; ua += 2)
                                             for (int va = cc3[2] & 1; va <= cc3[2]; va += 2)
-                                                sum = fma(e2 * Ec[cc3[2] * (LMAX + 1) + va], rb[ridx(t + ta2, u + ua, v + va)], sum);
-                                        }
+                                                sum = fma(E3[e3++], rb[ridx(t + ta2, u + ua, v + va)], sum);
                                     wd[ic * npt] = sum;
                                 }
                             }
