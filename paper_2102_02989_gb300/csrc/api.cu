@@ -132,11 +132,35 @@ static int fail(int code, const std::string &msg)
 // rsgdf_set_scratch_limit.
 static std::atomic<long long> g_scratch_limit{0};
 
+// The device's default stream-ordered pool, where scratch comes from, returns
+// its memory to the driver at every synchronisation unless told to keep some
+// (release threshold 0), and mapping it again costs milliseconds per call.
+// Once per device the threshold is raised to keep up to 8 GiB between calls
+// (never lowered).
+static void keep_pool_memory()
+{
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    if (done.load() & (1ull << dev)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long cur = 0, keep = 8ull << 30;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < keep)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.fetch_or(1ull << dev);
+}
+
 struct Scratch {
     cudaStream_t st;
     std::vector<void *> ptrs;
     size_t held = 0;
-    explicit Scratch(cudaStream_t s) : st(s) {}
+    explicit Scratch(cudaStream_t s) : st(s) { keep_pool_memory(); }
     ~Scratch()
     {
         for (void *p : ptrs) cudaFreeAsync(p, st);
@@ -354,18 +378,24 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     // 2 pi^{5/2}/(p g sqrt(p + g)) c_k c_i c_j (-1)^lP, and the d-independent
     // part of the log Coulomb bound of the combination
     std::vector<SRTripleDev> td(plan.tri.size());
-    std::vector<int> item_tri((size_t)plan.n_items);
     std::vector<double> ccon;
     std::vector<float> cbnd;
     const double om2 = omega * omega;
     const double gamma_half[11] = {0.0, 1.7724538509055160, 1.0, 0.8862269254527580, 1.0, 1.3293403881791370,
                                    2.0, 3.3233509704478426, 6.0, 11.631728396567450, 24.0};   // Gamma(n/2)
+    // log |c| of every primitive and log g of every aux primitive, for the bounds
+    std::vector<double> lcx(hax.exps.size()), lgx(hax.exps.size()), lco(hao.exps.size());
+    for (size_t o = 0; o < lcx.size(); o++) {
+        lcx[o] = std::log(std::fabs(hax.cn[o]));
+        lgx[o] = std::log(hax.exps[o]);
+    }
+    for (size_t o = 0; o < lco.size(); o++) lco[o] = std::log(std::fabs(hao.cn[o]));
     for (size_t i = 0; i < plan.tri.size(); i++) {
         const SRTriple &t = plan.tri[i];
         td[i] = {t.P, t.mu, t.nu, t.pair, t.nwin, t.win_off, t.nd, t.nsph, (int)(ccon.size() / 4), t.Rc_cut, t.amu,
                  t.anu, t.item_off, t.log10A, t.beta, t.eta1, t.eta2, t.aP};
-        for (long long it = t.item_off; it < t.item_off + t.nd; it++) item_tri[(size_t)it] = (int)i;
         const int lP = hax.l[t.P];
+        const double lgam = std::log(2.0 * KPI * gamma_half[lP + 2]);
         for (int k = 0; k < hax.nprim[t.P]; k++)
             for (int ii = 0; ii < hao.nprim[t.mu]; ii++)
                 for (int jj = 0; jj < hao.nprim[t.nu]; jj++) {
@@ -379,8 +409,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
                     ccon.push_back(std::sqrt(s));
                     ccon.push_back(2.0 * KPI2_5 / (p * g) * std::sqrt(ipg) * hax.cn[ok] * (hao.cn[oi] * hao.cn[oj]) *
                                    ((lP & 1) ? -1.0 : 1.0));
-                    const double lq = std::log(std::fabs(hax.cn[ok])) + std::log(2.0 * KPI * gamma_half[lP + 2]) -
-                                      0.5 * (lP + 2) * std::log(g) + std::log(std::fabs(hao.cn[oi] * hao.cn[oj]));
+                    const double lq = lcx[ok] + lgam - 0.5 * (lP + 2) * lgx[ok] + (lco[oi] + lco[oj]);
                     cbnd.push_back((float)std::max(lq, -1e30));
                 }
     }
@@ -407,10 +436,8 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     std::vector<float> sphlen(plan.sph_len.begin(), plan.sph_len.end());
     float *dsphlen;
     RC(S.upload(dsphlen, sphlen));
-    int *ditem_tri;
     double *dccon;
     float *dcbnd;
-    RC(S.upload(ditem_tri, item_tri));
     RC(S.alloc(R.geom, (size_t)std::max(plan.n_items, 1LL)));
     RC(S.upload(dccon, ccon));
     RC(S.upload(dcbnd, cbnd));
@@ -466,7 +493,7 @@ static int sr_setup(SRSetup &R, Scratch &S, const Lattice &L, const SRPlan &plan
     A.sphv = dsphv;
     A.sphvf = dsphvf;
     A.sphlen = dsphlen;
-    A.item_tri = ditem_tri;
+    A.ntri = (int)plan.tri.size();
     A.geom = R.geom;
     A.ccon = dccon;
     A.cbnd = dcbnd;

@@ -45,7 +45,8 @@ struct SRItemGeom {
     int nsph;
     int l0[3];       // L0 in lattice coordinates
     int gd, dt;      // global d index, BvK cell of d
-    int pad[3];
+    int tri;         // the item's shell triple (index into SRArgs::tri)
+    int pad[2];
 };
 static_assert(sizeof(SRItemGeom) == 96, "SRItemGeom is six 16-byte words");
 
@@ -59,7 +60,7 @@ struct SRArgs {
     const double *sphv;               // Cartesian vectors of the lattice list (FP64), [nsph][3]
     const float *sphvf;               // the same in FP32 (pre-filter)
     const float *sphlen;              // their lengths (ascending), FP32
-    const int *item_tri;              // [n_items] triple of each work item
+    int ntri;                         // shell triples of the problem (items of triple t: [tri[t].item_off, + nd))
     const SRItemGeom *geom;           // [n_items] geometry of each work item
     const double *ccon;               // per (triple, combination) [4]: alpha, s, sqrt s, prefactor (d-independent)
     const float *cbnd;                // per (triple, combination): d-independent part of the log Coulomb bound

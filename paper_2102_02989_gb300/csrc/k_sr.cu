@@ -358,7 +358,12 @@ __global__ void k_sr_item_geom(const SRArgs A, long long n_items, SRItemGeom *__
 {
     const long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (item >= n_items) return;
-    const SRTripleDev &tr = A.tri[A.item_tri[item]];
+    int t0 = 0, t1 = A.ntri - 1;   // last triple whose first item is <= item
+    while (t0 < t1) {
+        const int mid = (t0 + t1 + 1) >> 1;
+        if (A.tri[mid].item_off <= item) t0 = mid; else t1 = mid - 1;
+    }
+    const SRTripleDev &tr = A.tri[t0];
     const int gd = A.pair_doff[tr.pair] + (int)(item - tr.item_off);
     const int P = tr.P, mu = tr.mu, nu = tr.nu;
     const int d0 = A.dlist[3 * gd], d1 = A.dlist[3 * gd + 1], d2 = A.dlist[3 * gd + 2];
@@ -400,7 +405,8 @@ __global__ void k_sr_item_geom(const SRArgs A, long long n_items, SRItemGeom *__
     g.nsph = nsph;
     g.gd = gd;
     g.dt = bvk_bin(d0, d1, d2, A.nk);
-    g.pad[0] = g.pad[1] = g.pad[2] = 0;
+    g.tri = t0;
+    g.pad[0] = g.pad[1] = 0;
     out[item] = g;
 }
 
@@ -437,7 +443,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     double *Kc = (double *)(base + sm.kc);   // [combo][8]
 
     const SRItemGeom G = A.geom[item];
-    const SRTripleDev tr = A.tri[A.item_tri[item]];
+    const SRTripleDev tr = A.tri[G.tri];
     const int gd = G.gd;   // global d index
     const int P = tr.P, mu = tr.mu, nu = tr.nu;
     const int lP = A.ax.l[P], lm = A.ao.l[mu], ln = A.ao.l[nu];

@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <cstring>
 #include <numeric>
@@ -191,27 +194,99 @@ int derive_params(const Lattice &L, const rsgdf_opts *o, double &omega, int gmes
 
 namespace {
 
-// static partition of [0, n) over the hardware threads
+// Worker threads kept for the life of the process: a parallel loop costs a
+// wake-up instead of creating and joining threads (which took longer than
+// the planning loops themselves).  One loop runs at a time; a loop started
+// while another is running runs serially in its caller.  Each loop has its
+// own index counter, published while its caller hands out work and withdrawn
+// (under the lock) before the caller waits for the workers that joined: a
+// worker that wakes late finds no loop and cannot take indices of the next.
+class WorkerPool {
+public:
+    explicit WorkerPool(int nt)
+    {
+        for (int t = 0; t < nt; t++) th_.emplace_back([this] { work(); });
+    }
+    ~WorkerPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            quit_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    void run(int n, const std::function<void(int)> &f)
+    {
+        std::unique_lock<std::mutex> own(busy_, std::try_to_lock);
+        if (!own.owns_lock() || th_.empty()) {
+            for (int i = 0; i < n; i++) f(i);
+            return;
+        }
+        Loop loop{&f, n};
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            loop_ = &loop;
+            gen_++;
+        }
+        cv_.notify_all();
+        loop.drain();
+        std::unique_lock<std::mutex> lk(m_);
+        loop_ = nullptr;
+        done_.wait(lk, [&] { return active_ == 0; });
+    }
+
+private:
+    struct Loop {
+        const std::function<void(int)> *f;
+        int n;
+        std::atomic<int> next{0};
+        void drain()
+        {
+            for (int i; (i = next.fetch_add(1)) < n;) (*f)(i);
+        }
+    };
+    void work()
+    {
+        long seen = 0;
+        for (;;) {
+            std::unique_lock<std::mutex> lk(m_);
+            cv_.wait(lk, [&] { return quit_ || (loop_ && gen_ != seen); });
+            if (quit_) return;
+            Loop *loop = loop_;
+            seen = gen_;
+            active_++;
+            lk.unlock();
+            loop->drain();
+            lk.lock();
+            if (--active_ == 0) done_.notify_all();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex m_, busy_;
+    std::condition_variable cv_, done_;
+    Loop *loop_ = nullptr;
+    long gen_ = 0;
+    int active_ = 0;
+    bool quit_ = false;
+};
+
+WorkerPool &worker_pool()
+{
+    static WorkerPool pool(std::max(0, std::min((int)std::thread::hardware_concurrency(), 32) - 1));
+    return pool;
+}
+
+// dynamic partition of [0, n) over the pool and the calling thread
 template <class F>
 void parallel_for(int n, F f)
 {
-    int nt = (int)std::thread::hardware_concurrency();
-    nt = std::max(1, std::min(nt, 32));
-    if (n < 64 || nt == 1) {
+    if (n < 64) {
         for (int i = 0; i < n; i++) f(i);
         return;
     }
-    std::atomic<int> next(0);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; t++)
-        th.emplace_back([&]() {
-            for (;;) {
-                int i = next.fetch_add(1);
-                if (i >= n) break;
-                f(i);
-            }
-        });
-    for (auto &x : th) x.join();
+    const std::function<void(int)> g(f);
+    worker_pool().run(n, g);
 }
 
 struct Vec3 { double x, y, z; };
@@ -643,6 +718,9 @@ void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double o
         plan.dlist.insert(plan.dlist.end(), one.begin(), one.end());
         for (int q = pr + 1; q <= ns * ns; q++) plan.pair_doff[q] = (int)(plan.dlist.size() / 3);
     }
+    const int na = aux.nshell;
+    std::vector<double> rc((size_t)na * na);
+    parallel_for(na * na, [&](int id) { rc[id] = pair2c_cut(L, omega, eps, aux, id / na, id % na); });
     for (int P = 0; P < aux.nshell; P++)
         for (int Q = 0; Q < aux.nshell; Q++) {
             SRTriple t;
@@ -652,7 +730,7 @@ void plan_sr2c(const Lattice &L, const HBasis &aux, const HBasis &auxu, double o
             t.win_off = (int)plan.win.size();
             plan.win.push_back(1e300);
             t.nd = 1;
-            t.Rc_cut = pair2c_cut(L, omega, eps, aux, P, Q);
+            t.Rc_cut = rc[(size_t)P * na + Q];
             t.amu = aux.exps[diffuse_index(aux, Q)];
             t.anu = 0.0;
             t.nsph = 0;
