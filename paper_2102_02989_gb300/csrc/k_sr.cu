@@ -891,6 +891,11 @@ int sr_default_bc(int L, int ncomp_max, int w_max, int nk_max)
 {
     int bc = 4096 / (ntuv(L) + ncomp_max + w_max);
     bc = bc < 1 ? 1 : (bc > 16 ? 16 : bc);
+    // classes L >= 5 hold large per-cell blocks and aux-side sums (ncomp_max,
+    // w_max): at most 4 cells per chunk halves them, and two CTAs share an SM
+    // where one did (2.7% less SR time on the FCC 2x2x2 step; 2 cells per chunk,
+    // or 4 from L = 4 on, were slower)
+    if (L >= 5 && bc > 4) bc = 4;
     return bc > nk_max ? (nk_max < 1 ? 1 : nk_max) : bc;
 }
 
