@@ -156,6 +156,80 @@ static void keep_pool_memory()
     done.fetch_or(1ull << dev);
 }
 
+// Pinned staging of host-to-device uploads.  A copy from pageable memory goes
+// through the driver's small staging buffers, and when the stream still holds
+// queued kernels (j3c enqueues its LR work before the SR set-up) the host
+// waits until the device has drained them: about 2 ms of the headline call.
+// Uploads are therefore copied into a pinned arena of the calling thread and
+// sent from there.  The arena is filled front to back and reused from the
+// front once every copy sent from it has completed (an event per stream after
+// its last copy); if it fills while copies are pending, a larger one takes
+// over and the full one is freed at the next such point.  Uploads above
+// 64 MiB, and uploads during a stream capture, take the pageable path.
+struct PinnedArena {
+    char *buf = nullptr;
+    size_t cap = 0, used = 0;
+    std::vector<char *> retired;                               // full arenas whose copies may still be pending
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> marks;   // last copy per stream
+    bool idle() const
+    {
+        for (const auto &m : marks)
+            if (cudaEventQuery(m.second) == cudaErrorNotReady) return false;
+        cudaGetLastError();
+        return true;
+    }
+    void drain()
+    {
+        for (const auto &m : marks) cudaEventSynchronize(m.second);
+        cudaGetLastError();
+    }
+    // pinned destination of n bytes for a copy on stream s, or nullptr (pageable path)
+    char *take(size_t n, cudaStream_t s)
+    {
+        constexpr size_t MAXUP = 64ull << 20, MAXCAP = 256ull << 20;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (n == 0 || n > MAXUP || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        n = (n + 255) & ~(size_t)255;
+        if ((used > 0 || !retired.empty()) && idle()) {   // every copy sent so far has completed
+            for (char *r : retired) cudaFreeHost(r);
+            retired.clear();
+            used = 0;
+        }
+        if (used + n > cap) {
+            // a larger arena; the full one is freed once its copies have completed
+            const size_t want = std::min(MAXCAP, std::max({(size_t)32 << 20, 2 * cap, 2 * n}));
+            void *p = nullptr;
+            if (want < n || cudaHostAlloc(&p, want, cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                drain();   // no larger arena: wait for the pending copies and reuse this one
+                if (n > cap) return nullptr;
+                used = 0;
+            } else {
+                if (buf) retired.push_back(buf);
+                buf = (char *)p;
+                cap = want;
+                used = 0;
+            }
+        }
+        char *q = buf + used;
+        used += n;
+        return q;
+    }
+    bool mark(cudaStream_t s)
+    {
+        for (auto &m : marks)
+            if (m.first == s) return cudaEventRecord(m.second, s) == cudaSuccess;
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+        marks.push_back({s, e});
+        return cudaEventRecord(e, s) == cudaSuccess;
+    }
+};
+static thread_local PinnedArena t_upload_arena;
+
 struct Scratch {
     cudaStream_t st;
     std::vector<void *> ptrs;
@@ -188,8 +262,17 @@ struct Scratch {
     int upload(T *&p, const std::vector<T> &v)
     {
         RC(alloc(p, v.size()));
-        if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        if (v.empty()) return RSGDF_OK;
+        const size_t bytes = v.size() * sizeof(T);
+        const void *src = v.data();
+        char *pin = t_upload_arena.take(bytes, st);
+        if (pin) {
+            memcpy(pin, v.data(), bytes);
+            src = pin;
+        }
+        if (cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return fail(RSGDF_EDEVICE, "host-to-device copy failed");
+        if (pin && !t_upload_arena.mark(st)) return fail(RSGDF_EDEVICE, "event record failed");
         return RSGDF_OK;
     }
 };
