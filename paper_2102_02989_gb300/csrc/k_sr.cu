@@ -10,14 +10,17 @@
 //   2. sorts them stably by BvK cell of l (deterministic order),
 //   3. for every primitive combination, accumulates the McMurchie-Davidson
 //      Hermite integrals R_tuv(erfc kernel) over the translations of each BvK
-//      cell -- the lattice sum acts on R only --, and contracts the sums once
-//      per cell with the Hermite expansion coefficients of the pair and of
-//      the aux function,
+//      cell -- the lattice sum acts on R only; the lanes are spread over the
+//      cells, each with a row of sums of its own --, and contracts the sums
+//      once per cell with the Hermite expansion coefficients of the pair and
+//      of the aux function,
 //   4. adds the contracted blocks to the folded array X[lt][dt][P][mu][nu].
-// Everything is FP64.
+// The item's geometry (nearest lattice vector of the pair centre, candidate
+// radius and prefix) comes from a record written by k_sr_item_geom.  The
+// integral arithmetic is FP64; table indices, branches and the screening
+// tests use integer and FP32 arithmetic where stated error bounds allow.
 #include <cuda_runtime.h>
 
-#include <cstdint>
 #include <cstdint>
 
 #include <algorithm>
@@ -417,9 +420,10 @@ int launch_sr_item_geom(const SRArgs &A, long long n_items, SRItemGeom *out, cud
     return cudaGetLastError() == cudaSuccess ? RSGDF_OK : RSGDF_EDEVICE;
 }
 
-// One SR work item (aux shell, AO shell pair, d) by one warp; base is the
-// warp's shared-memory region (laid out from A's bc, ncomp_max, w_max and
-// list_max).  Every branch on the item is warp-uniform.
+// One SR work item (aux shell, AO shell pair, d) by one warp, from its
+// geometry record; base is the warp's shared-memory region (laid out from A's
+// bc, ncomp_max, w_max, list_max, combo_max and nbin_max).  Every branch on
+// the item is warp-uniform.
 template <int L>
 __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item, const int lane, unsigned char *base)
 {
@@ -556,7 +560,7 @@ __device__ __forceinline__ void sr3c_item(const SRArgs &A, const long long item,
     int nT = 0;
     unsigned long long kept = 0;
     float magmax = 0.0f;   // largest |block| the item adds (magnitude mode)
-    int nq = 0;   // FP32 survivors waiting for the exact FP64 test (smem queue Qd)
+    int nq = 0;   // pre-filter survivors waiting for the exact test (smem queue Qd)
     for (int b0 = 0; b0 < nsph; b0 += 32) {
         const int idx = b0 + lane;
         bool pass = false;
